@@ -1,0 +1,150 @@
+/*
+ * ttn.h -- C ABI of the GB300 tree-tensor-network (TTN) sweep library.
+ *
+ * The library optimises a regular binary TTN (arXiv 1905.01331, Sec. II.C,
+ * Fig. 1d) for the ground state of a periodic chain of L effective sites, or of
+ * an Lx x Ly thin torus seen as a chain of Lx columns of dimension d^Ly
+ * (Sec. II.B).  The Hamiltonian is given as one-site and product terms,
+ *     H = sum_m [ o_m + sum_{k<K} A_k,m B_k,m+1 ],
+ * whose bond index has dimension K instead of chi (Fig. 2b), so that every
+ * contraction of the sweep costs O(chi^4) (Sec. III.A, Sec. V).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a ttn_status (0 on success, negative on error).  Nothing
+ *    aborts or throws across the ABI; ttn_last_error() describes the last
+ *    failure of a context.
+ *  - Host buffers belong to the caller; the library copies from/to them and
+ *    keeps no pointer to them after the call returns.
+ *  - Device memory: one caller-owned workspace (device pointer + size) given
+ *    to ttn_create; the library carves all its tensors out of it and never
+ *    allocates device memory itself.  The workspace must stay allocated and
+ *    unused by the caller until ttn_destroy.
+ *  - Stream: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that return host values
+ *    synchronise that stream only.
+ *  - Layouts are row-major C order.  An isometry of layer t is w[p][l][r]
+ *    with parent p < chi_{t+1} and children l, r < chi_t (Eq. (constraint)
+ *    reads sum_{l,r} w[p][l][r] w[p'][l][r] = delta_{p p'}); the top tensor is
+ *    v[a][b], chi_T x chi_T (Eq. (normalization)).
+ *  - Bond dimensions: chi_0 = d^Ly and chi_{t+1} = min(chi, chi_t^2) for
+ *    t = 0..T-1, T = log2(Lx) - 1; Lx must be a power of two >= 4.
+ */
+#ifndef TTN_H
+#define TTN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttn_ctx* ttn_t;
+
+typedef enum {
+  TTN_OK = 0,
+  TTN_EINVAL = -1,    /* bad argument or shape */
+  TTN_ENOMEM = -2,    /* workspace too small */
+  TTN_ECUDA = -3,     /* a CUDA call failed */
+  TTN_ENOCONV = -4,   /* top eigensolver or polar iteration did not converge */
+  TTN_ETIMEOUT = -5,  /* a bounded device wait expired */
+  TTN_ENAN = -6       /* NaN or Inf met in an input or a result */
+} ttn_status;
+
+/* Arithmetic of the O(chi^4) contractions (ascend, environment, descend).
+ * The polar update's final isometry condition, the top eigenproblem and all
+ * energies are FP64 in every mode. */
+typedef enum {
+  TTN_FP64 = 0,     /* plain FP64 on the CUDA cores */
+  TTN_TF32 = 1,     /* tcgen05 kind::tf32, FP32 accumulation */
+  TTN_TF32X3 = 2,   /* three TF32 products (hi*hi + hi*lo + lo*hi) */
+  TTN_BF16 = 3,     /* tcgen05 kind::f16 with bf16 operands */
+  TTN_BF16X3 = 4    /* three bf16 products */
+} ttn_precision;
+
+/* One Hamiltonian.  onesite: d0 x d0, A and B: K x d0 x d0, d0 = d^Ly, all
+ * host FP64, row-major; the library copies them in ttn_create. */
+typedef struct {
+  int Lx, Ly, d, chi, K;
+  int per_node;             /* 0: one isometry per layer (translation
+                               invariant, Sec. III); 1: one per node */
+  const double* onesite;
+  const double* A;
+  const double* B;
+} ttn_problem;
+
+typedef struct {
+  int prec;                 /* ttn_precision */
+  int top_mode;             /* 0: lowest eigenvector of the top Hamiltonian */
+  double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-12) */
+  int lanczos_max;          /* Krylov dimension per restart (default 48) */
+  int lanczos_restarts;     /* restarts per sweep (default 4) */
+  double shift;             /* bond shift c; NaN = lambda_max of the bond term */
+  double polar_damping;     /* proximal weight mu of the update (default 1e-10) */
+  int deterministic;        /* 1: fixed-order reductions (always on) */
+  int use_graph;            /* 1: capture a sweep as a CUDA graph and replay */
+} ttn_options;
+
+/* Fill *opt with the defaults above. */
+void ttn_default_options(ttn_options* opt);
+
+/* Bytes of device workspace that ttn_create needs for these problems. */
+size_t ttn_workspace_bytes(const ttn_problem* probs, int n_problems, const ttn_options* opt);
+
+/* Build a context for n_problems independent Hamiltonians advanced together
+ * (step a0: operators uploaded, shift c computed on the host from the
+ * d0^2 x d0^2 bond matrix).  Isometries start undefined: call
+ * ttn_set_isometries for every instance before the first sweep. */
+int ttn_create(ttn_t* out, const ttn_problem* probs, int n_problems, const ttn_options* opt,
+               void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Number of doubles of one instance's isometries (all layers, layer 0 first;
+ * per node: node-major within a layer) and of its top tensor. */
+int ttn_sizes(ttn_t h, int inst, size_t* n_w, size_t* n_v, int* n_layers);
+
+/* Bond dimensions chi_0..chi_T of one instance (host array of n_layers+1). */
+int ttn_chis(ttn_t h, int inst, int* chis);
+
+/* Copy host isometries (concatenated as ttn_sizes describes) and top tensor
+ * of one instance to the device.  No check of the isometric constraint. */
+int ttn_set_isometries(ttn_t h, int inst, const double* host_w_all, const double* host_v);
+
+/* Copy one instance's current isometries and top tensor to host buffers. */
+int ttn_get_isometries(ttn_t h, int inst, double* host_w_all, double* host_v);
+
+/* Run n_sweeps sweeps of every instance (Sec. III): ascend the Hamiltonian
+ * through all layers, solve the top tensor, then for t = T-1..0 form the
+ * environment of w_t, replace w_t by minus its polar factor and descend the
+ * density matrices through the new w_t.  host_energy (may be NULL) receives
+ * n_sweeps * n_problems doubles, sweep-major: the energy found by each top
+ * solve, shift restored. */
+int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy);
+
+/* Energy <psi|H|psi> of one instance's current tensors, in FP64 (ascend and
+ * top contraction, no re-optimisation). */
+int ttn_energy(ttn_t h, int inst, double* E_total);
+
+/* Reduced density matrix on one site of site layer `site_layer` (0..T) of the
+ * current tensors, chi_t x chi_t, to host (Sec. IV.B).  which = 0: average
+ * over the sites of that layer (R / N_t); which = 1: the leftmost site. */
+int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* host_out);
+
+/* Environment dE/dw of isometry layer `layer` at the current tensors, written
+ * to caller device memory d_out (FP64, the isometry's shape; per node, all
+ * nodes).  This is the backward of the energy with respect to w. */
+int ttn_env(ttn_t h, int inst, int layer, double* d_out);
+
+/* Serialise / restore all isometries, top tensors and sweep counters. */
+int ttn_get_state(ttn_t h, void* host_buf, size_t* bytes);
+int ttn_set_state(ttn_t h, const void* host_buf, size_t bytes);
+
+/* Kernel launches enqueued by the last ttn_sweep call (a count). */
+long long ttn_launch_count(ttn_t h);
+
+const char* ttn_last_error(ttn_t h);
+void ttn_destroy(ttn_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTN_H */

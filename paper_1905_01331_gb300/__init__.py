@@ -1,0 +1,177 @@
+"""GB300 tree-tensor-network sweep (arXiv 1905.01331) -- Python binding.
+
+A thin layer over the C ABI of ``libttn.so`` (include/ttn.h): it marshals
+arguments, and takes the library's device workspace from PyTorch's caching
+allocator.  Every step of the sweep runs in the library's CUDA kernels; there
+is no CPU implementation here, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _abi
+
+PRECISIONS = {"fp64": _abi.TTN_FP64, "tf32": _abi.TTN_TF32, "tf32x3": _abi.TTN_TF32X3,
+              "bf16": _abi.TTN_BF16, "bf16x3": _abi.TTN_BF16X3}
+
+
+class TTNError(RuntimeError):
+    pass
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Sweeper:
+    """One or more TTN instances advanced together on the current CUDA device.
+
+    ``models``: objects with ``Lx, Ly, o (d0 x d0), A, B (K x d0 x d0)`` (for
+    example ``ttn_inputs.Model``); ``chis``: bond-dimension caps (int or list).
+    """
+
+    def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
+                 lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
+                 polar_damping=1e-10, use_graph=True, shift=None):
+        import torch
+        self._torch = torch
+        self.lib = _abi.load()
+        if not isinstance(models, (list, tuple)):
+            models = [models]
+        if isinstance(chis, int):
+            chis = [chis] * len(models)
+        self.n = len(models)
+        self._keep = []
+        probs = (_abi.Problem * self.n)()
+        for i, (m, chi) in enumerate(zip(models, chis)):
+            o = np.ascontiguousarray(m.o, dtype=np.float64)
+            A = np.ascontiguousarray(m.A, dtype=np.float64)
+            B = np.ascontiguousarray(m.B, dtype=np.float64)
+            self._keep += [o, A, B]
+            d = 2
+            probs[i] = _abi.Problem(m.Lx, m.Ly, d, int(chi), A.shape[0], int(bool(per_node)),
+                                    _ptr(o), _ptr(A), _ptr(B))
+        opt = _abi.Options()
+        self.lib.ttn_default_options(ctypes.byref(opt))
+        opt.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        opt.lanczos_tol = lanczos_tol
+        opt.lanczos_max = lanczos_max
+        opt.lanczos_restarts = lanczos_restarts
+        opt.polar_damping = polar_damping
+        opt.use_graph = int(bool(use_graph))
+        if shift is not None:
+            opt.shift = float(shift)
+        self.opt = opt
+        nbytes = self.lib.ttn_workspace_bytes(probs, self.n, ctypes.byref(opt))
+        if nbytes == 0:
+            raise TTNError("ttn_workspace_bytes rejected the problems")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = self.lib.ttn_create(ctypes.byref(h), probs, self.n, ctypes.byref(opt),
+                                 ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        self.h = h
+        self._check(rc, "ttn_create")
+        self.per_node = bool(per_node)
+        self.models = list(models)
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.lib.ttn_last_error(self.h).decode() if self.h else ""
+            raise TTNError(f"{what}: {_abi.STATUS.get(rc, rc)} {msg}")
+
+    def chis(self, inst=0):
+        nw, nv, nl = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+        self._check(self.lib.ttn_sizes(self.h, inst, ctypes.byref(nw), ctypes.byref(nv), ctypes.byref(nl)), "sizes")
+        out = (ctypes.c_int * (nl.value + 1))()
+        self._check(self.lib.ttn_chis(self.h, inst, out), "chis")
+        return list(out)
+
+    def _shapes(self, inst):
+        chis = self.chis(inst)
+        L = self.models[inst].Lx
+        shapes = []
+        for t in range(len(chis) - 1):
+            s = (chis[t + 1], chis[t], chis[t])
+            shapes.append(((L >> (t + 1)),) + s if self.per_node else s)
+        return shapes, (chis[-1], chis[-1])
+
+    # -- API -----------------------------------------------------------------
+    def set_isometries(self, inst, ws, V):
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(w, np.float64).ravel() for w in ws]))
+        v = np.ascontiguousarray(np.asarray(V, np.float64))
+        self._check(self.lib.ttn_set_isometries(self.h, inst, _ptr(flat), _ptr(v)), "set_isometries")
+
+    def get_isometries(self, inst=0):
+        shapes, vs = self._shapes(inst)
+        n = sum(int(np.prod(s)) for s in shapes)
+        flat = np.empty(n)
+        V = np.empty(vs)
+        self._check(self.lib.ttn_get_isometries(self.h, inst, _ptr(flat), _ptr(V)), "get_isometries")
+        ws, off = [], 0
+        for s in shapes:
+            k = int(np.prod(s))
+            ws.append(flat[off:off + k].reshape(s))
+            off += k
+        return ws, V
+
+    def sweep(self, n_sweeps=1):
+        """Run sweeps; returns energies of shape (n_sweeps, n_instances)."""
+        E = np.empty((n_sweeps, self.n))
+        self._check(self.lib.ttn_sweep(self.h, n_sweeps, _ptr(E)), "sweep")
+        return E
+
+    def sweep_async(self, n_sweeps=1):
+        """Enqueue sweeps on the stream without reading energies back."""
+        self._check(self.lib.ttn_sweep(self.h, n_sweeps, None), "sweep")
+
+    def energy(self, inst=0):
+        E = ctypes.c_double()
+        self._check(self.lib.ttn_energy(self.h, inst, ctypes.byref(E)), "energy")
+        return E.value
+
+    def rdm(self, inst, site_layer, which=0):
+        n = self.chis(inst)[site_layer]
+        out = np.empty((n, n))
+        self._check(self.lib.ttn_rdm(self.h, inst, site_layer, which, _ptr(out)), "rdm")
+        return out
+
+    def env(self, inst, layer, out=None):
+        """dE/dw of one isometry layer as a CUDA float64 tensor."""
+        shapes, _ = self._shapes(inst)
+        torch = self._torch
+        if out is None:
+            out = torch.empty(shapes[layer], dtype=torch.float64, device="cuda")
+        self._check(self.lib.ttn_env(self.h, inst, layer, ctypes.c_void_p(out.data_ptr())), "env")
+        return out
+
+    def get_state(self):
+        n = ctypes.c_size_t()
+        self._check(self.lib.ttn_get_state(self.h, None, ctypes.byref(n)), "state size")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self.lib.ttn_get_state(self.h, buf, ctypes.byref(n)), "get_state")
+        return bytes(buf.raw)
+
+    def set_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(self.lib.ttn_set_state(self.h, buf, len(data)), "set_state")
+
+    @property
+    def launch_count(self):
+        return int(self.lib.ttn_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

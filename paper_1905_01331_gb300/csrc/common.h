@@ -1,0 +1,91 @@
+// Shared declarations of the TTN sweep kernels (device side and host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttn {
+
+// One operand of a grouped, batched, strided matrix product.  Element (i, k)
+// of batch (b0, b1) sits at p[i*s_mn + k0*s_k0 + k1*s_k1 + b0*s_b0 + b1*s_b1]
+// with k0 = k mod K0, k1 = k div K0 (K0 a power of two).  i is the row for A
+// and the column for B.  Two-level K and batch indices let one descriptor
+// express every contraction of the sweep on tensors w[p][l][r] without
+// materialising a permutation.
+struct Operand {
+  const double* p;
+  long long s_mn, s_k0, s_k1, s_b0, s_b1;
+};
+
+struct Group {
+  Operand a, b;
+  int K;        // K0 * K1
+  int k0_log2;  // log2 K0
+};
+
+constexpr int kMaxGroups = 20;
+
+// C[b] = alpha * sum_g A_g[b] B_g[b] + beta * C[b] for every batch b = (b0, b1).
+// The K ranges of the groups are concatenated into one reduction; `splits`
+// cuts it into contiguous tile ranges whose partial sums are added in a fixed
+// order by a second kernel (deterministic).
+struct GemmDesc {
+  int M, N, B0, B1;
+  int ngroups;
+  Group g[kMaxGroups];
+  double* C;
+  long long sc_m, sc_n, sc_b0, sc_b1;
+  double alpha, beta;
+  int splits;
+  double* partial;   // splits * B0 * B1 * M * N doubles when splits > 1
+  int prec;          // ttn_precision of the products
+  const int* skip;   // if non-null and *skip != 0 the launch does nothing
+};
+
+// Launch one grouped product on `stream` (FP64 CUDA-core kernel or tcgen05
+// kernel by desc.prec).  Returns the number of kernel launches.
+int gemm_launch(const GemmDesc& d, cudaStream_t stream);
+
+// Split count / partial-buffer size the launcher will use for a descriptor.
+int gemm_pick_splits(const GemmDesc& d);
+size_t gemm_partial_elems(const GemmDesc& d, int splits);
+
+// Tensor-core path (gemm_tc.cu).
+int gemm_tc_launch(const GemmDesc& d, cudaStream_t stream);
+bool gemm_tc_supported(const GemmDesc& d);
+
+// ---------------------------------------------------------------------------
+// Small kernels (misc.cu).  All reductions are two-pass with fixed order.
+// ---------------------------------------------------------------------------
+
+// out[b] = sum_i x[b*stride + i] * y[b*stride + i] for b < nb, i < n.
+// scratch: at least nb * kDotBlocks doubles.
+constexpr int kDotBlocks = 64;
+int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
+                double* out, double* scratch, cudaStream_t s);
+
+// Polar start: per batch b (P x N rows), with fro2 = |G|^2, gw = <G, W>:
+//   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
+int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
+                int P, double mu, const double* fro2, const double* gw, cudaStream_t s);
+
+// Pm[b] = a I - c A[b] (P x P), nb batches.
+int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
+                     cudaStream_t s);
+
+// F[b] = I (P x P).
+int set_identity(double* F, int P, int nb, cudaStream_t s);
+
+// y = alpha * x + beta * y over n elements.
+int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s);
+
+// Symmetrise P x P blocks in place: A = (A + A^T) / 2.
+int symmetrize(double* A, int P, int nb, cudaStream_t s);
+
+// Sum of `count` doubles in a fixed order into *out (single block).
+int ordered_sum(const double* x, int count, double* out, double scale, double add,
+                cudaStream_t s);
+
+// NaN/Inf scan: flag[0] |= 1 if any element is not finite.
+int finite_check(const double* x, long long n, int* flag, cudaStream_t s);
+
+}  // namespace ttn

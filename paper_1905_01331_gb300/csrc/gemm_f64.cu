@@ -1,0 +1,191 @@
+// Grouped, batched, strided FP64 matrix products on the CUDA cores.
+//
+// Every O(chi^4) contraction of the sweep (Sec. III.A: "a sequence of
+// tensor-tensor contractions ... matrix-matrix multiplications") is one
+// GemmDesc: a sum over groups of A_g B_g with two-level K and batch indices, so
+// that index permutations of the rank-3 tensors (Sec. V: "permuting indices of
+// rank-3 tensors") are folded into the address arithmetic and never stored.
+#include <algorithm>
+#include <cstdio>
+
+#include "common.h"
+
+namespace ttn {
+
+namespace {
+
+constexpr int kBK = 16;
+constexpr int kThreads = 256;
+
+struct TileRange {
+  int g_begin, t_begin;  // first group and k-tile inside it
+  int tiles;             // number of k-tiles of this split
+};
+
+__device__ __forceinline__ double ld_operand(const Operand& o, int k0_log2, long long base,
+                                             int i, int k) {
+  const int k0 = k & ((1 << k0_log2) - 1);
+  const int k1 = k >> k0_log2;
+  return o.p[base + i * o.s_mn + k0 * o.s_k0 + (long long)k1 * o.s_k1];
+}
+
+// BM x BN output tile per CTA, 256 threads, each thread TM x TN outputs.
+template <int BM, int BN>
+__global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, int total_tiles) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  if (d.skip && *d.skip) return;
+  __shared__ double As[kBK][BM + 1];
+  __shared__ double Bs[kBK][BN + 1];
+
+  const int tiles_n = (d.N + BN - 1) / BN;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  const int b = blockIdx.y;
+  const int b0 = b % d.B0, b1 = b / d.B0;
+  const int split = blockIdx.z;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+
+  // contiguous range of k-tiles for this split
+  const int t_lo = (int)((long long)total_tiles * split / d.splits);
+  const int t_hi = (int)((long long)total_tiles * (split + 1) / d.splits);
+
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  int t_global = 0;
+  for (int g = 0; g < d.ngroups && t_global < t_hi; ++g) {
+    const Group& G = d.g[g];
+    const int nt = (G.K + kBK - 1) / kBK;
+    if (t_global + nt <= t_lo) { t_global += nt; continue; }
+    const long long abase = b0 * G.a.s_b0 + (long long)b1 * G.a.s_b1;
+    const long long bbase = b0 * G.b.s_b0 + (long long)b1 * G.b.s_b1;
+    const int first = max(0, t_lo - t_global), last = min(nt, t_hi - t_global);
+    const bool a_kfast = (G.a.s_k0 == 1);
+    const bool b_kfast = (G.b.s_k0 == 1);
+    for (int t = first; t < last; ++t) {
+      const int kb = t * kBK;
+      // stage A tile (BM x kBK) and B tile (kBK x BN)
+      for (int e = threadIdx.x; e < BM * kBK; e += kThreads) {
+        int mi, ki;
+        if (a_kfast) { ki = e % kBK; mi = e / kBK; } else { mi = e % BM; ki = e / BM; }
+        const int m = m0 + mi, k = kb + ki;
+        As[ki][mi] = (m < d.M && k < G.K) ? ld_operand(G.a, G.k0_log2, abase, m, k) : 0.0;
+      }
+      for (int e = threadIdx.x; e < BN * kBK; e += kThreads) {
+        int ni, ki;
+        if (b_kfast) { ki = e % kBK; ni = e / kBK; } else { ni = e % BN; ki = e / BN; }
+        const int n = n0 + ni, k = kb + ki;
+        Bs[ki][ni] = (n < d.N && k < G.K) ? ld_operand(G.b, G.k0_log2, bbase, n, k) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kBK; ++kk) {
+        double av[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    t_global += nt;
+  }
+
+  if (d.splits == 1) {
+    double* C = d.C + b0 * d.sc_b0 + (long long)b1 * d.sc_b1;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < d.M && n < d.N) {
+          double* c = C + m * d.sc_m + n * d.sc_n;
+          *c = d.beta == 0.0 ? d.alpha * acc[i][j] : d.alpha * acc[i][j] + d.beta * *c;
+        }
+      }
+  } else {
+    const long long MN = (long long)d.M * d.N;
+    double* Pp = d.partial + ((long long)split * d.B0 * d.B1 + b) * MN;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < d.M && n < d.N) Pp[(long long)m * d.N + n] = acc[i][j];
+      }
+  }
+}
+
+// C = alpha * sum_s partial[s] + beta * C, summed in split order.
+__global__ void splitk_reduce_kernel(const GemmDesc d) {
+  if (d.skip && *d.skip) return;
+  const long long MN = (long long)d.M * d.N;
+  const long long total = MN * d.B0 * d.B1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / MN, r = e % MN;
+    const int m = (int)(r / d.N), n = (int)(r % d.N);
+    double s = 0.0;
+    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
+    const int b0 = (int)(b % d.B0), b1 = (int)(b / d.B0);
+    double* c = d.C + b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n;
+    *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
+  }
+}
+
+int total_k_tiles(const GemmDesc& d) {
+  int t = 0;
+  for (int g = 0; g < d.ngroups; ++g) t += (d.g[g].K + kBK - 1) / kBK;
+  return t;
+}
+
+template <int BM, int BN>
+int launch_tile(const GemmDesc& d, cudaStream_t s) {
+  const int tiles = ((d.M + BM - 1) / BM) * ((d.N + BN - 1) / BN);
+  dim3 grid(tiles, d.B0 * d.B1, d.splits);
+  gemm_f64_kernel<BM, BN><<<grid, kThreads, 0, s>>>(d, total_k_tiles(d));
+  return 1;
+}
+
+}  // namespace
+
+int gemm_pick_splits(const GemmDesc& d) {
+  const int bm = (d.M >= 64 && d.N >= 64) ? 64 : (d.M >= 32 && d.N >= 32) ? 32 : 16;
+  const int bn = bm;
+  const long long base = (long long)((d.M + bm - 1) / bm) * ((d.N + bn - 1) / bn) * d.B0 * d.B1;
+  const int kt = total_k_tiles(d);
+  if (base >= 296 || kt < 8) return 1;
+  int s = (int)std::min<long long>((296 + base - 1) / base, kt / 4);
+  s = std::max(1, std::min(s, 64));
+  return s;
+}
+
+size_t gemm_partial_elems(const GemmDesc& d, int splits) {
+  return splits > 1 ? (size_t)splits * d.B0 * d.B1 * d.M * d.N : 0;
+}
+
+int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
+  if (d0.prec != 0 && gemm_tc_supported(d0)) return gemm_tc_launch(d0, s);
+  GemmDesc d = d0;
+  if (d.M <= 0 || d.N <= 0 || d.B0 * d.B1 <= 0) return 0;
+  int n = 0;
+  if (d.M >= 64 && d.N >= 64) n += launch_tile<64, 64>(d, s);
+  else if (d.M >= 32 && d.N >= 32) n += launch_tile<32, 32>(d, s);
+  else n += launch_tile<16, 16>(d, s);
+  if (d.splits > 1) {
+    const long long total = (long long)d.M * d.N * d.B0 * d.B1;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(d);
+    ++n;
+  }
+  return n;
+}
+
+}  // namespace ttn

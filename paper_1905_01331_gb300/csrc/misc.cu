@@ -1,0 +1,408 @@
+// Reductions, elementwise steps and the Lanczos bookkeeping of the sweep.
+// Every reduction is two-pass with a fixed summation order (deterministic).
+#include <cmath>
+
+#include "common.h"
+
+namespace ttn {
+
+namespace {
+
+__device__ double block_sum(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
+// partial[b * kDotBlocks + blk] = sum over this block's slice of x*y
+__global__ void dot_partial_kernel(const double* x, const double* y, long long n,
+                                   long long stride, double* partial, const int* skip) {
+  if (skip && *skip) return;
+  const int b = blockIdx.y, blk = blockIdx.x;
+  const double* xb = x + b * stride;
+  const double* yb = y + b * stride;
+  double s = 0.0;
+  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s = fma(xb[i], yb[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[b * kDotBlocks + blk] = s;
+}
+
+__global__ void dot_final_kernel(const double* partial, int nb, double* out, const int* skip) {
+  if (skip && *skip) return;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0;
+  for (int i = 0; i < kDotBlocks; ++i) s += partial[b * kDotBlocks + i];
+  out[b] = s;
+}
+
+__global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
+                                   int P, double mu, const double* fro2, const double* gw) {
+  const int b = blockIdx.y;
+  const double f2 = fro2[b];
+  const double s = mu * sqrt(f2);
+  const double nrm2 = f2 - 2.0 * s * gw[b] + s * s * P;
+  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  const double* g = G + b * elems;
+  const double* w = W + b * elems;
+  double* x = X + b * elems;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (g[i] - s * w[i]) * inv;
+}
+
+__global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, double c) {
+  const int b = blockIdx.y;
+  const long long PP = (long long)P * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / P), j = (int)(e % P);
+    Pm[b * PP + e] = (i == j ? a : 0.0) - c * A[b * PP + e];
+  }
+}
+
+__global__ void identity_kernel(double* F, int P) {
+  const int b = blockIdx.y;
+  const long long PP = (long long)P * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
+       e += (long long)gridDim.x * blockDim.x)
+    F[b * PP + e] = (e / P == e % P) ? 1.0 : 0.0;
+}
+
+__global__ void axpby_kernel(const double* x, double* y, long long n, double alpha, double beta) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = alpha * x[i] + beta * y[i];
+}
+
+__global__ void symmetrize_kernel(double* A, int P) {
+  const int b = blockIdx.y;
+  double* a = A + (long long)b * P * P;
+  const long long PP = (long long)P * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / P), j = (int)(e % P);
+    if (i < j) {
+      const double v = 0.5 * (a[i * (long long)P + j] + a[j * (long long)P + i]);
+      a[i * (long long)P + j] = v;
+      a[j * (long long)P + i] = v;
+    }
+  }
+}
+
+// ---- Lanczos -------------------------------------------------------------
+
+// partial[i * kDotBlocks + blk] = <basis_i, w> over this block's slice
+__global__ void lz_dots_partial(const double* basis, long long n, int count, const double* w,
+                                double* partial, const int* skip) {
+  if (*skip) return;
+  const int i = blockIdx.y;
+  if (i >= count) return;
+  const double* v = basis + i * n;
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    s = fma(v[e], w[e], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[i * kDotBlocks + blockIdx.x] = s;
+}
+
+__global__ void lz_dots_final(const double* partial, int count, double* coef, const int* skip) {
+  if (*skip) return;
+  const int i = threadIdx.x;
+  if (i >= count) return;
+  double s = 0.0;
+  for (int b = 0; b < kDotBlocks; ++b) s += partial[i * kDotBlocks + b];
+  coef[i] = s;
+}
+
+__global__ void lz_sub_kernel(const double* basis, long long n, int count, double* w,
+                              const double* coef, const int* skip) {
+  if (*skip) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double s = w[e];
+    for (int i = 0; i < count; ++i) s = fma(-coef[i], basis[i * n + e], s);
+    w[e] = s;
+  }
+}
+
+// alpha_j from the two projection passes, beta_j = |w|; breakdown stops the run.
+__global__ void lz_step_scalars(const double* c1, const double* c2, int j, double* alpha,
+                                double* beta, const double* nrm2, int* skip, int* tdim) {
+  if (*skip) return;
+  const double a = c1[j] + c2[j];
+  alpha[j] = a;
+  const double b = sqrt(fmax(nrm2[0], 0.0));
+  beta[j] = b;
+  *tdim = j + 1;
+  if (!(b > 1e-12 * fmax(fabs(a), 1e-300))) { beta[j] = 0.0; *skip = 1; }
+}
+
+__global__ void lz_scale_into(double* dst, const double* w, long long n, const double* beta, int j,
+                              const int* skip) {
+  if (*skip) return;
+  const double inv = 1.0 / beta[j];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = w[e] * inv;
+}
+
+// Sturm count: number of eigenvalues of the tridiagonal T (size m) below x.
+__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = a[i] - x - b[i - 1] * b[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// Lowest eigenpair of the Lanczos tridiagonal by bisection and inverse
+// iteration (Gaussian elimination with partial pivoting on the band).
+__global__ void lz_ritz_kernel(const double* alpha, const double* beta, const int* tdim, int jmax,
+                               double* y, double* theta, double* res, int* conv, double tol,
+                               const int* skip_before) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*conv) return;
+  const int m = *tdim;
+  double lo = alpha[0], hi = alpha[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(beta[i]) : 0.0);
+    lo = fmin(lo, alpha[i] - r);
+    hi = fmax(hi, alpha[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(alpha, beta, m, mid) >= 1) hi = mid; else lo = mid;
+  }
+  const double th = 0.5 * (lo + hi);
+  // inverse iteration on (T - th I) x = x_prev, 3 rounds
+  double x[128], dd[128], du[128], du2[128], rhs[128];
+  for (int i = 0; i < m; ++i) x[i] = 1.0 / sqrt((double)m);
+  const double eps = fmax(fabs(th), 1.0) * 1e-15;
+  for (int round = 0; round < 3; ++round) {
+    for (int i = 0; i < m; ++i) { dd[i] = alpha[i] - th; du[i] = i + 1 < m ? beta[i] : 0.0; du2[i] = 0.0; rhs[i] = x[i]; }
+    double dl[128];
+    for (int i = 0; i + 1 < m; ++i) dl[i] = beta[i];
+    // LU with partial pivoting of the tridiagonal (LAPACK gttrf-style)
+    for (int i = 0; i + 1 < m; ++i) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = eps;
+        const double f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+        rhs[i + 1] -= f * rhs[i];
+      } else {
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const double t = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = t - f * dd[i + 1];
+        if (i + 2 < m) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+        const double r = rhs[i];
+        rhs[i] = rhs[i + 1];
+        rhs[i + 1] = r - f * rhs[i + 1];
+      }
+    }
+    if (dd[m - 1] == 0.0) dd[m - 1] = eps;
+    // back substitution
+    for (int i = m - 1; i >= 0; --i) {
+      double s = rhs[i];
+      if (i + 1 < m) s -= du[i] * x[i + 1];
+      if (i + 2 < m) s -= du2[i] * x[i + 2];
+      x[i] = s / (fabs(dd[i]) < eps ? (dd[i] < 0 ? -eps : eps) : dd[i]);
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < m; ++i) x[i] /= nrm;
+  }
+  for (int i = 0; i < jmax; ++i) y[i] = i < m ? x[i] : 0.0;
+  *theta = th;
+  const double r = fabs(beta[m - 1] * x[m - 1]);
+  *res = r;
+  if (r <= tol * fmax(fabs(th), 1e-300)) *conv = 1;
+}
+
+__global__ void lz_combine_kernel(const double* basis, long long n, const int* tdim, const double* y,
+                                  double* v) {
+  const int m = *tdim;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s = fma(y[i], basis[i * n + e], s);
+    v[e] = s;
+  }
+}
+
+__global__ void scale_by_inv_sqrt(double* v, long long n, const double* nrm2, double* dst0) {
+  const double inv = 1.0 / sqrt(nrm2[0]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double t = v[e] * inv;
+    v[e] = t;
+    if (dst0) dst0[e] = t;
+  }
+}
+
+__global__ void lz_reset_kernel(int* tdim, int* skip, const int* conv) {
+  *tdim = 1;
+  *skip = *conv;
+}
+
+__global__ void flip_if_negative(double* v, long long n, const double* dotv) {
+  if (dotv[0] >= 0.0) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    v[e] = -v[e];
+}
+
+__global__ void ordered_sum_kernel(const double* x, int count, double* out, double scale,
+                                   double add) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < count; ++i) s += x[i];
+  *out = scale * s + add;
+}
+
+__global__ void finite_kernel(const double* x, long long n, int* flag) {
+  int bad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[e])) bad = 1;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+int grid_for(long long n, int per = 256, int cap = 1184) {
+  long long g = (n + per - 1) / per;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
+                double* out, double* scratch, cudaStream_t s) {
+  dot_partial_kernel<<<dim3(kDotBlocks, nb), 256, 0, s>>>(x, y, n, stride, scratch, nullptr);
+  dot_final_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nb, out, nullptr);
+  return 2;
+}
+
+int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
+                double mu, const double* fro2, const double* gw, cudaStream_t s) {
+  polar_start_kernel<<<dim3(grid_for(elems, 256, 512), nb), 256, 0, s>>>(G, W, X, elems, P, mu,
+                                                                          fro2, gw);
+  return 1;
+}
+
+int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
+                     cudaStream_t s) {
+  poly_step_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(A, Pm, P, a, c);
+  return 1;
+}
+
+int set_identity(double* F, int P, int nb, cudaStream_t s) {
+  identity_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(F, P);
+  return 1;
+}
+
+int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, alpha, beta);
+  return 1;
+}
+
+int symmetrize(double* A, int P, int nb, cudaStream_t s) {
+  symmetrize_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(A, P);
+  return 1;
+}
+
+int lz_dots(const double* basis, long long n, int count, const double* w, double* coef,
+            double* scratch, const int* skip, cudaStream_t s) {
+  lz_dots_partial<<<dim3(kDotBlocks, count), 256, 0, s>>>(basis, n, count, w, scratch, skip);
+  lz_dots_final<<<1, 128, 0, s>>>(scratch, count, coef, skip);
+  return 2;
+}
+
+int lz_sub(const double* basis, long long n, int count, double* w, const double* coef,
+           const int* skip, cudaStream_t s) {
+  lz_sub_kernel<<<grid_for(n), 256, 0, s>>>(basis, n, count, w, coef, skip);
+  return 1;
+}
+
+int lz_finish_step(double* basis, long long n, int j, double* w, const double* c1,
+                   const double* c2, double* alpha, double* beta, double* scratch, double* nrm2,
+                   int* skip, int* tdim, cudaStream_t s) {
+  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(w, w, n, 0, scratch, skip);
+  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, skip);
+  lz_step_scalars<<<1, 1, 0, s>>>(c1, c2, j, alpha, beta, nrm2, skip, tdim);
+  lz_scale_into<<<grid_for(n), 256, 0, s>>>(basis + (j + 1) * n, w, n, beta, j, skip);
+  return 4;
+}
+
+int lz_ritz(const double* alpha, const double* beta, const int* tdim, int jmax, double* y,
+            double* theta, double* res, int* conv, double tol, cudaStream_t s) {
+  lz_ritz_kernel<<<1, 32, 0, s>>>(alpha, beta, tdim, jmax, y, theta, res, conv, tol, nullptr);
+  return 1;
+}
+
+int lz_combine(double* basis, long long n, const int* tdim, const double* y, double* v,
+               double* scratch, double* nrm2, int* tdim_rw, int* skip, const int* conv,
+               cudaStream_t s) {
+  lz_combine_kernel<<<grid_for(n), 256, 0, s>>>(basis, n, tdim, y, v);
+  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, v, n, 0, scratch, nullptr);
+  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, nullptr);
+  scale_by_inv_sqrt<<<grid_for(n), 256, 0, s>>>(v, n, nrm2, basis);
+  lz_reset_kernel<<<1, 1, 0, s>>>(tdim_rw, skip, conv);
+  return 5;
+}
+
+int lz_start(double* basis, long long n, const double* v, double* scratch, double* nrm2,
+             int* tdim, int* skip, int* conv, cudaStream_t s) {
+  cudaMemsetAsync(conv, 0, sizeof(int), s);
+  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, v, n, 0, scratch, nullptr);
+  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, nullptr);
+  cudaMemcpyAsync(basis, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  scale_by_inv_sqrt<<<grid_for(n), 256, 0, s>>>(basis, n, nrm2, nullptr);
+  lz_reset_kernel<<<1, 1, 0, s>>>(tdim, skip, conv);
+  return 4;
+}
+
+int align_sign(double* v, const double* vprev, long long n, double* scratch, double* dotv,
+               cudaStream_t s) {
+  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, vprev, n, 0, scratch, nullptr);
+  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, dotv, nullptr);
+  flip_if_negative<<<grid_for(n), 256, 0, s>>>(v, n, dotv);
+  return 3;
+}
+
+int ordered_sum(const double* x, int count, double* out, double scale, double add,
+                cudaStream_t s) {
+  ordered_sum_kernel<<<1, 32, 0, s>>>(x, count, out, scale, add);
+  return 1;
+}
+
+int finite_check(const double* x, long long n, int* flag, cudaStream_t s) {
+  finite_kernel<<<grid_for(n, 256, 296), 256, 0, s>>>(x, n, flag);
+  return 1;
+}
+
+}  // namespace ttn

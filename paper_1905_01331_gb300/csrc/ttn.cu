@@ -1,0 +1,1104 @@
+// Host orchestration of the TTN sweep and the C ABI declared in include/ttn.h.
+//
+// One sweep (Sec. III, "standard energy minimisation"):
+//   ascend the Hamiltonian through every isometry layer (Fig. 3 pushed up),
+//   solve the top tensor (Sec. III.B: "the top tensor v is updated similarly"
+//   -- read as its lowest eigenvector, Lanczos in FP64),
+//   then for t = T-1 .. 0: environment of w_t as a sum of contractions
+//   (Sec. III.A, Figs. 2b, 3), w_t <- minus its polar factor (Sec. III.B,
+//   Fig. 4c-d, in the Gram form of the appendix, Fig. 9b, iterated), and
+//   descend the density matrices through the new w_t.
+// Every contraction is one grouped product (GemmDesc); nothing else touches
+// the O(chi^4) data.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ttn.h"
+#include "common.h"
+#include "host_eig.h"
+
+namespace ttn {
+
+// Lanczos helpers defined in misc.cu
+int lz_dots(const double* basis, long long n, int count, const double* w, double* coef,
+            double* scratch, const int* skip, cudaStream_t s);
+int lz_sub(const double* basis, long long n, int count, double* w, const double* coef,
+           const int* skip, cudaStream_t s);
+int lz_finish_step(double* basis, long long n, int j, double* w, const double* c1,
+                   const double* c2, double* alpha, double* beta, double* scratch, double* nrm2,
+                   int* skip, int* tdim, cudaStream_t s);
+int lz_ritz(const double* alpha, const double* beta, const int* tdim, int jmax, double* y,
+            double* theta, double* res, int* conv, double tol, cudaStream_t s);
+int lz_combine(double* basis, long long n, const int* tdim, const double* y, double* v,
+               double* scratch, double* nrm2, int* tdim_rw, int* skip, const int* conv,
+               cudaStream_t s);
+int lz_start(double* basis, long long n, const double* v, double* scratch, double* nrm2,
+             int* tdim, int* skip, int* conv, cudaStream_t s);
+int align_sign(double* v, const double* vprev, long long n, double* scratch, double* dotv,
+               cudaStream_t s);
+
+typedef long long ll;
+
+// Bump allocator over the caller's workspace; with base == nullptr it only
+// measures.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  std::vector<std::pair<size_t, size_t>>* registry = nullptr;  // (start, bytes)
+  double* take(size_t n_doubles) {
+    off = (off + 255) & ~size_t(255);
+    double* p = base ? reinterpret_cast<double*>(base + off) : nullptr;
+    if (registry && base) registry->push_back({(size_t)(base + off), n_doubles * sizeof(double)});
+    off += n_doubles * sizeof(double);
+    return p;
+  }
+  int* take_int(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    int* p = base ? reinterpret_cast<int*>(base + off) : nullptr;
+    if (registry && base) registry->push_back({(size_t)(base + off), n * sizeof(int)});
+    off += n * sizeof(int);
+    return p;
+  }
+};
+
+struct Instance {
+  int L = 0, Ly = 0, d0 = 0, K = 0, T = 0, per_node = 0, chi = 0, n_spins = 0;
+  double c = 0.0;
+  std::vector<int> chis;
+  std::vector<double> o, A, B;       // host copies of the terms
+  std::vector<double*> W, ops, adj;  // device tensors per layer / site layer
+  double* V = nullptr;
+  double* Vprev = nullptr;
+  double* E = nullptr;               // energy of the last top solve
+  int sites(int t) const { return per_node ? (L >> t) : 1; }
+  int nodes(int t) const { return per_node ? (L >> (t + 1)) : 1; }
+  size_t w_elems(int t) const {
+    return (size_t)nodes(t) * chis[t + 1] * chis[t] * chis[t];
+  }
+  size_t op_elems(int t) const { return (size_t)sites(t) * (1 + 2 * K) * chis[t] * chis[t]; }
+};
+
+struct PolarBlock {
+  std::vector<std::pair<double, double>> steps;  // p(A) = a I - c A
+};
+
+}  // namespace ttn
+
+using namespace ttn;
+
+struct ttn_ctx {
+  ttn_options opt;
+  std::vector<Instance> inst;
+  cudaStream_t user = nullptr, stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+  long long launches = 0;
+  long long launches_per_sweep = 0;
+  int sweeps_done = 0;
+  // shared scratch
+  double *Y = nullptr, *Gam = nullptr, *X = nullptr, *X2 = nullptr, *Yt = nullptr, *M1 = nullptr;
+  double *pA = nullptr, *pF = nullptr, *pP = nullptr, *pT = nullptr;
+  double* partial = nullptr;
+  size_t partial_cap = 0;
+  double* red = nullptr;       // dot scratch
+  double* scal = nullptr;      // small scalars
+  double *lz_basis = nullptr, *lz_w = nullptr, *lz_c1 = nullptr, *lz_c2 = nullptr, *lz_alpha = nullptr,
+         *lz_beta = nullptr, *lz_y = nullptr, *lz_tmp = nullptr, *top_stack0 = nullptr,
+         *top_stack1 = nullptr;
+  int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan
+  int lz_m = 48;
+  double* E_hist = nullptr;    // device energies of the current ttn_sweep call
+  std::vector<PolarBlock> polar_f64, polar_tc;
+  bool measuring = false;      // plan pass: only size the partial buffer
+  // plan pass over a fake base address: every operand's address range is
+  // checked against the buffer it points into (no launch happens)
+  std::vector<std::pair<size_t, size_t>> registry;
+  std::string bounds_error;
+};
+
+namespace {
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
+
+Operand op(const double* p, ll s_mn, ll s_k0, ll s_k1 = 0, ll s_b0 = 0, ll s_b1 = 0) {
+  Operand o;
+  o.p = p; o.s_mn = s_mn; o.s_k0 = s_k0; o.s_k1 = s_k1; o.s_b0 = s_b0; o.s_b1 = s_b1;
+  return o;
+}
+
+Group grp(Operand a, Operand b, int K0, int K1 = 1) {
+  Group g;
+  g.a = a; g.b = b; g.K = K0 * K1; g.k0_log2 = ilog2(K0);
+  return g;
+}
+
+GemmDesc desc(int M, int N, int B0, int B1, double* C, ll sc_m, ll sc_n, ll sc_b0, ll sc_b1,
+              double alpha = 1.0, double beta = 0.0) {
+  GemmDesc d;
+  memset(&d, 0, sizeof(d));
+  d.M = M; d.N = N; d.B0 = B0; d.B1 = B1; d.C = C;
+  d.sc_m = sc_m; d.sc_n = sc_n; d.sc_b0 = sc_b0; d.sc_b1 = sc_b1;
+  d.alpha = alpha; d.beta = beta; d.splits = 1;
+  return d;
+}
+
+void add(GemmDesc& d, const Group& g) {
+  if (d.ngroups < kMaxGroups) d.g[d.ngroups] = g;
+  d.ngroups++;   // an overflow is reported by the plan pass and never launched
+}
+
+// Highest element offset an operand reaches for extents (mn, K0, K1, B0, B1).
+ll max_offset(const Operand& o, int mn, int K0, int K1, int B0, int B1) {
+  return (mn - 1) * o.s_mn + (K0 - 1) * o.s_k0 + (ll)(K1 - 1) * o.s_k1 + (ll)(B0 - 1) * o.s_b0 +
+         (ll)(B1 - 1) * o.s_b1;
+}
+
+void check_range(ttn_ctx* h, const double* p, ll max_off, const char* what) {
+  if (h->registry.empty() || !h->bounds_error.empty()) return;
+  const size_t a = (size_t)p, e = a + (size_t)(max_off + 1) * sizeof(double);
+  for (auto& r : h->registry)
+    if (a >= r.first && a < r.first + r.second) {
+      if (e > r.first + r.second)
+        h->bounds_error = std::string(what) + " exceeds its buffer by " +
+                          std::to_string(e - r.first - r.second) + " bytes";
+      return;
+    }
+  h->bounds_error = std::string(what) + " points outside the workspace";
+}
+
+void check_desc(ttn_ctx* h, const GemmDesc& d) {
+  for (int g = 0; g < d.ngroups; ++g) {
+    const Group& G = d.g[g];
+    const int K0 = 1 << G.k0_log2, K1 = G.K >> G.k0_log2;
+    if (K0 * K1 != G.K || G.K <= 0) { h->bounds_error = "bad K split"; return; }
+    check_range(h, G.a.p, max_offset(G.a, d.M, K0, K1, d.B0, d.B1), "A operand");
+    check_range(h, G.b.p, max_offset(G.b, d.N, K0, K1, d.B0, d.B1), "B operand");
+  }
+  Operand c;
+  c.p = d.C; c.s_mn = d.sc_m; c.s_k0 = d.sc_n; c.s_k1 = 0; c.s_b0 = d.sc_b0; c.s_b1 = d.sc_b1;
+  check_range(h, d.C, max_offset(c, d.M, d.N, 1, d.B0, d.B1), "C output");
+}
+
+// Run (or, in the plan pass, size and bounds-check) one product.
+void run(ttn_ctx* h, GemmDesc d, int prec) {
+  d.prec = prec;
+  int s = gemm_pick_splits(d);
+  size_t need = gemm_partial_elems(d, s);
+  if (h->measuring) {
+    if (need > h->partial_cap) h->partial_cap = need;
+    if (d.ngroups > kMaxGroups) h->bounds_error = "too many groups";
+    check_desc(h, d);
+    return;
+  }
+  if (need > h->partial_cap) s = 1;   // cannot happen after planning
+  if (d.ngroups > kMaxGroups) return;
+  d.splits = s;
+  d.partial = h->partial;
+  h->launches += gemm_launch(d, h->stream);
+}
+
+// Polar schedule: scaled Newton-Schulz steps p(x) = 1.5 c x - 0.5 c^3 x^3 with
+// c = sqrt(3 / (1 + l + l^2)) for singular values in [l, 1]; steps are
+// composed on the P x P level in blocks whose growth stays below gmax, with
+// a fresh Gram matrix at the start of every block.
+std::vector<PolarBlock> polar_schedule(double l0, double gmax, double final_tol, int max_block) {
+  std::vector<PolarBlock> out;
+  double l = l0;
+  PolarBlock cur;
+  double start = l;
+  int guard = 0;
+  while (1.0 - l > final_tol && guard++ < 200) {
+    const double c = std::sqrt(3.0 / (1.0 + l + l * l));
+    const double ln = 1.5 * c * l - 0.5 * c * c * c * l * l * l;
+    if (!cur.steps.empty() && (ln / start > gmax || (int)cur.steps.size() >= max_block)) {
+      out.push_back(cur);
+      cur = PolarBlock();
+      start = l;
+    }
+    cur.steps.push_back({1.5 * c, 0.5 * c * c * c});
+    l = ln;
+  }
+  if (!cur.steps.empty()) out.push_back(cur);
+  return out;
+}
+
+// --------------------------------------------------------------------------
+// Sweep pieces.  Layer t: P = chi_{t+1}, n = chi_t, NJ nodes.
+// ops/adj of site layer t: [site][1+2K][n][n]; op 0 = o (adjoint R),
+// 1+k = A_k (P_k), 1+K+k = B_k (Q_k).  Node J's children are sites 2J, 2J+1.
+// --------------------------------------------------------------------------
+
+struct LayerView {
+  int P, n, NJ, K;
+  ll n2, Pn2, ss, node_ss;   // ss: site stride of ops_t; node_ss: ops_t stride per node
+  ll adj_ss;                 // site stride of adj_{t+1}
+  const double* opsL;        // ops_t of the left child of node 0
+  const double* opsR;        // ops_t of the right child of node 0
+};
+
+LayerView view(const Instance& I, int t) {
+  LayerView v;
+  v.P = I.chis[t + 1]; v.n = I.chis[t]; v.NJ = I.nodes(t); v.K = I.K;
+  v.n2 = (ll)v.n * v.n; v.Pn2 = (ll)v.P * v.n2;
+  v.ss = (1 + 2 * I.K) * v.n2;
+  v.node_ss = I.per_node ? 2 * v.ss : 0;
+  v.adj_ss = I.per_node ? (ll)(1 + 2 * I.K) * v.P * v.P : 0;
+  v.opsL = I.ops[t];
+  v.opsR = I.ops[t] + (I.per_node ? v.ss : 0);
+  return v;
+}
+
+// Y[b0][J] = W_J X_b0 for X = ops(side, first + b0), b0 < count:  right product.
+void right_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* side, int first,
+                int count, bool transX, double* Y, ll y_b0, int prec) {
+  GemmDesc d = desc(v.P * v.n, v.n, count, v.NJ, Y, v.n, 1, y_b0, v.Pn2);
+  // B(i = column r', k = r) = X[r][r'] (or X[r'][r] when transposed)
+  add(d, grp(op(W, v.n, 1, 0, 0, v.Pn2),
+             op(side + first * v.n2, transX ? v.n : 1, transX ? 1 : v.n, 0, v.n2, v.node_ss), v.n));
+  run(h, d, prec);
+}
+
+// Y[b0][J][p] = X_b0^T W_{J,p} (transX: X_b0 W_{J,p}): left product, batched over p.
+void left_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* side, int first,
+               int count, bool transX, double* Y, ll y_b0, int prec) {
+  for (int k = 0; k < count; ++k) {
+    GemmDesc d = desc(v.n, v.n, v.P, v.NJ, Y + k * y_b0, v.n, 1, v.n2, v.Pn2);
+    // A(m = l', k = l) = X[l][l'] (X^T), or X[l'][l] (X)
+    const double* X = side + (first + k) * v.n2;
+    add(d, grp(op(X, transX ? v.n : 1, transX ? 1 : v.n, 0, 0, v.node_ss),
+               op(W, 1, v.n, 0, v.n2, v.Pn2), v.n));
+    run(h, d, prec);
+  }
+}
+
+void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
+  const LayerView v = view(I, t);
+  const int K = I.K;
+  const double* W = I.W[t];
+  const ll slab = (ll)v.NJ * v.Pn2;    // one stacked tensor
+  double* U = h->M1;                  // U_k = W B_k(right child), K slabs
+  right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
+  // Y0 = o_L^T W_p + W_p o_R + sum_k A_{k,L}^T U_k,p
+  {
+    GemmDesc d = desc(v.n, v.n, v.P, v.NJ, h->Y, v.n, 1, v.n2, v.Pn2);
+    add(d, grp(op(v.opsL, 1, v.n, 0, 0, v.node_ss), op(W, 1, v.n, 0, v.n2, v.Pn2), v.n));
+    add(d, grp(op(W, v.n, 1, 0, v.n2, v.Pn2), op(v.opsR, 1, v.n, 0, 0, v.node_ss), v.n));
+    for (int k = 0; k < K; ++k)
+      add(d, grp(op(v.opsL + (1 + k) * v.n2, 1, v.n, 0, 0, v.node_ss),
+                 op(U + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
+    run(h, d, prec);
+  }
+  // Y_{1+k} = W A_{k,R};  Y_{1+K+k} = B_{k,L}^T W
+  right_mult(h, v, W, v.opsR, 1, K, false, h->Y + slab, slab, prec);
+  left_mult(h, v, W, v.opsL, 1 + K, K, false, h->Y + (1 + K) * slab, slab, prec);
+  // ops_{t+1}[J][j] = sum_{lr} Y_j[J][p][lr] W_J[q][lr]
+  const ll out_site = (ll)(1 + 2 * K) * v.P * v.P;
+  GemmDesc d = desc(v.P, v.P, 1 + 2 * K, v.NJ, I.ops[t + 1], v.P, 1, (ll)v.P * v.P,
+                    I.per_node ? out_site : 0);
+  add(d, grp(op(h->Y, v.n2, 1, 0, slab, v.Pn2), op(W, v.n2, 1, 0, 0, v.Pn2), (int)v.n2));
+  run(h, d, prec);
+}
+
+// Top Hamiltonian on x (c x c): w = o_0 x + x o_1^T + sum_k (A_k0 x B_k1^T + B_k0 x A_k1^T)
+void top_matvec(ttn_ctx* h, Instance& I, const double* x, double* w, const int* skip) {
+  const int T = I.T, c = I.chis[T], K = I.K;
+  const ll c2 = (ll)c * c, ss = (ll)(1 + 2 * K) * c2;
+  const double* s0 = I.ops[T];
+  const double* s1 = I.ops[T] + (I.per_node ? ss : 0);
+  double* Yk = h->lz_tmp;   // 2K stacked: A_k0 x, then B_k0 x
+  {
+    GemmDesc d = desc(c, c, 2 * K, 1, Yk, c, 1, c2, 0);
+    add(d, grp(op(s0 + c2, c, 1, 0, c2, 0), op(x, 1, c, 0, 0, 0), c));
+    d.skip = skip;
+    run(h, d, 0);
+  }
+  GemmDesc d = desc(c, c, 1, 1, w, c, 1, 0, 0);
+  d.skip = skip;
+  add(d, grp(op(s0, c, 1), op(x, 1, c), c));                 // o_0 x
+  add(d, grp(op(x, c, 1), op(s1, c, 1), c));                 // x o_1^T
+  for (int k = 0; k < K; ++k) {
+    add(d, grp(op(Yk + k * c2, c, 1), op(s1 + (1 + K + k) * c2, c, 1), c));      // (A_k0 x) B_k1^T
+    add(d, grp(op(Yk + (K + k) * c2, c, 1), op(s1 + (1 + k) * c2, c, 1), c));    // (B_k0 x) A_k1^T
+  }
+  run(h, d, 0);
+}
+
+void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
+  const int T = I.T, c = I.chis[T];
+  const ll n = (ll)c * c;
+  const int m = (int)std::min<ll>(h->lz_m, n);
+  int* skip = h->iflags;
+  int* tdim = h->iflags + 1;
+  int* conv = h->iflags + 2;
+  double* nrm2 = h->scal;
+  double* theta = h->scal + 1;
+  double* res = h->scal + 2;
+  double* dotv = h->scal + 3;
+  if (!h->measuring) {
+    cudaMemcpyAsync(I.Vprev, I.V, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    h->launches += lz_start(h->lz_basis, n, I.V, h->red, nrm2, tdim, skip, conv, h->stream);
+  }
+  for (int cyc = 0; cyc < h->opt.lanczos_restarts; ++cyc) {
+    for (int j = 0; j < m; ++j) {
+      top_matvec(h, I, h->lz_basis + j * n, h->lz_w, skip);
+      if (h->measuring) continue;
+      h->launches += lz_dots(h->lz_basis, n, j + 1, h->lz_w, h->lz_c1, h->red, skip, h->stream);
+      h->launches += lz_sub(h->lz_basis, n, j + 1, h->lz_w, h->lz_c1, skip, h->stream);
+      h->launches += lz_dots(h->lz_basis, n, j + 1, h->lz_w, h->lz_c2, h->red, skip, h->stream);
+      h->launches += lz_sub(h->lz_basis, n, j + 1, h->lz_w, h->lz_c2, skip, h->stream);
+      if (j + 1 < m || true)
+        h->launches += lz_finish_step(h->lz_basis, n, j, h->lz_w, h->lz_c1, h->lz_c2,
+                                      h->lz_alpha, h->lz_beta, h->red, nrm2, skip, tdim,
+                                      h->stream);
+    }
+    if (h->measuring) continue;
+    h->launches += lz_ritz(h->lz_alpha, h->lz_beta, tdim, h->lz_m, h->lz_y, theta, res, conv,
+                           h->opt.lanczos_tol, h->stream);
+    h->launches += lz_combine(h->lz_basis, n, tdim, h->lz_y, I.V, h->red, nrm2, tdim, skip, conv,
+                              h->stream);
+  }
+  if (h->measuring) { top_matvec(h, I, I.V, h->lz_w, nullptr); return; }
+  h->launches += align_sign(I.V, I.Vprev, n, h->red, dotv, h->stream);
+  // energy = <V, H V> + c L
+  top_matvec(h, I, I.V, h->lz_w, nullptr);
+  h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
+  h->launches += ordered_sum(h->scal + 4, 1, energy_out, 1.0, I.c * I.L, h->stream);
+}
+
+void energy_only(ttn_ctx* h, Instance& I, double* energy_out) {
+  const ll n = (ll)I.chis[I.T] * I.chis[I.T];
+  top_matvec(h, I, I.V, h->lz_w, nullptr);
+  if (h->measuring) return;
+  h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
+  h->launches += ordered_sum(h->scal + 4, 1, energy_out, 1.0, I.c * I.L, h->stream);
+}
+
+// Top adjoints: R = V V^T + V^T V, P_k = V B_k V^T + V^T B_k V, Q_k = V^T A_k V + V A_k V^T
+// (per node: site 0 gets the V ... V^T terms, site 1 the V^T ... V terms).
+void top_adjoints(ttn_ctx* h, Instance& I) {
+  const int T = I.T, c = I.chis[T], K = I.K;
+  const ll c2 = (ll)c * c, ss = (ll)(1 + 2 * K) * c2;
+  const double* s0 = I.ops[T];
+  const double* s1 = I.ops[T] + (I.per_node ? ss : 0);
+  double* T0 = h->top_stack0;   // [V | V B_k1 | V A_k1]
+  double* T1 = h->top_stack1;   // [V | B_k0 V | A_k0 V]
+  if (!h->measuring) {
+    cudaMemcpyAsync(T0, I.V, c2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(T1, I.V, c2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  }
+  {  // T0[1+j] = V X_j(site 1), X = [A..., B...] -> order B first then A
+    GemmDesc d = desc(c, c, K, 1, T0 + c2, c, 1, c2, 0);
+    add(d, grp(op(I.V, c, 1), op(s1 + (1 + K) * c2, 1, c, 0, c2, 0), c));   // V B_k1
+    run(h, d, 0);
+    GemmDesc e = desc(c, c, K, 1, T0 + (1 + K) * c2, c, 1, c2, 0);
+    add(e, grp(op(I.V, c, 1), op(s1 + c2, 1, c, 0, c2, 0), c));             // V A_k1
+    run(h, e, 0);
+    GemmDesc f = desc(c, c, K, 1, T1 + c2, c, 1, c2, 0);
+    add(f, grp(op(s0 + (1 + K) * c2, c, 1, 0, c2, 0), op(I.V, 1, c), c));   // B_k0 V
+    run(h, f, 0);
+    GemmDesc g = desc(c, c, K, 1, T1 + (1 + K) * c2, c, 1, c2, 0);
+    add(g, grp(op(s0 + c2, c, 1, 0, c2, 0), op(I.V, 1, c), c));             // A_k0 V
+    run(h, g, 0);
+  }
+  double* adj = I.adj[T];
+  // site-0 part: T0_j V^T ; site-1 part: V^T T1_j
+  Group g0 = grp(op(T0, c, 1, 0, c2, 0), op(I.V, c, 1), c);           // B(i=col, k) = V[i][k]
+  Group g1 = grp(op(I.V, 1, c), op(T1, 1, c, 0, c2, 0), c);           // A(m, k) = V[k][m]
+  if (I.per_node) {
+    GemmDesc d0 = desc(c, c, 1 + 2 * K, 1, adj, c, 1, c2, 0);
+    add(d0, g0);
+    run(h, d0, 0);
+    GemmDesc d1 = desc(c, c, 1 + 2 * K, 1, adj + ss, c, 1, c2, 0);
+    add(d1, g1);
+    run(h, d1, 0);
+  } else {
+    GemmDesc d = desc(c, c, 1 + 2 * K, 1, adj, c, 1, c2, 0);
+    add(d, g0);
+    add(d, g1);
+    run(h, d, 0);
+  }
+}
+
+// Gamma_J = R_J Zs + sum_k [P_k W A_k^T + P_k^T W A_k + Q_k B_k W + Q_k^T B_k^T W]
+void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
+  const LayerView v = view(I, t);
+  const int K = I.K;
+  const double* W = I.W[t];
+  const ll slab = (ll)v.NJ * v.Pn2;
+  double* E_ = h->M1;                 // W B_k^T (K slabs)
+  double* U = h->M1 + K * slab;       // W B_k   (K slabs)
+  right_mult(h, v, W, v.opsR, 1 + K, K, true, E_, slab, prec);
+  right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
+  double* Zs = h->Y;                  // slab 0
+  {
+    GemmDesc d = desc(v.n, v.n, v.P, v.NJ, Zs, v.n, 1, v.n2, v.Pn2);
+    Operand Wl = op(W, 1, v.n, 0, v.n2, v.Pn2);      // B operand: W_p[k][i]
+    Operand Wr = op(W, v.n, 1, 0, v.n2, v.Pn2);      // A operand: W_p[m][k]
+    add(d, grp(op(v.opsL, v.n, 1, 0, 0, v.node_ss), Wl, v.n));    // o_L W_p
+    add(d, grp(op(v.opsL, 1, v.n, 0, 0, v.node_ss), Wl, v.n));    // o_L^T W_p
+    add(d, grp(Wr, op(v.opsR, v.n, 1, 0, 0, v.node_ss), v.n));    // W_p o_R^T
+    add(d, grp(Wr, op(v.opsR, 1, v.n, 0, 0, v.node_ss), v.n));    // W_p o_R
+    for (int k = 0; k < K; ++k) {
+      const double* Ak = v.opsL + (1 + k) * v.n2;
+      add(d, grp(op(Ak, v.n, 1, 0, 0, v.node_ss), op(E_ + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
+      add(d, grp(op(Ak, 1, v.n, 0, 0, v.node_ss), op(U + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
+    }
+    run(h, d, prec);
+  }
+  // one-leg products: slabs 1.. of Y: WAt_k, WA_k, BW_k, BtW_k
+  double* WAt = h->Y + slab;
+  double* WA = WAt + K * slab;
+  double* BW = WA + K * slab;
+  double* BtW = BW + K * slab;
+  right_mult(h, v, W, v.opsR, 1, K, true, WAt, slab, prec);
+  right_mult(h, v, W, v.opsR, 1, K, false, WA, slab, prec);
+  left_mult(h, v, W, v.opsL, 1 + K, K, true, BW, slab, prec);
+  left_mult(h, v, W, v.opsL, 1 + K, K, false, BtW, slab, prec);
+  const double* G = I.adj[t + 1];
+  const ll PP = (ll)v.P * v.P;
+  GemmDesc d = desc(v.P, (int)v.n2, 1, v.NJ, Gam, v.n2, 1, 0, v.Pn2);
+  auto Gn = [&](int j) { return op(G + j * PP, v.P, 1, 0, 0, v.adj_ss); };
+  auto Gt = [&](int j) { return op(G + j * PP, 1, v.P, 0, 0, v.adj_ss); };
+  auto Tn = [&](const double* T) { return op(T, 1, v.n2, 0, 0, v.Pn2); };
+  add(d, grp(Gn(0), Tn(Zs), v.P));
+  for (int k = 0; k < K; ++k) {
+    add(d, grp(Gn(1 + k), Tn(WAt + k * slab), v.P));
+    add(d, grp(Gt(1 + k), Tn(WA + k * slab), v.P));
+    add(d, grp(Gn(1 + K + k), Tn(BW + k * slab), v.P));
+    add(d, grp(Gt(1 + K + k), Tn(BtW + k * slab), v.P));
+  }
+  run(h, d, prec);
+}
+
+// w_t <- -polar(Gam - mu |Gam| w_t) by scaled Newton-Schulz blocks.
+void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
+  const LayerView v = view(I, t);
+  const int P = v.P, NJ = v.NJ;
+  const ll N = v.n2, PN = v.Pn2, PP = (ll)P * P;
+  double* W = I.W[t];
+  double* X = h->X;
+  double* X2 = h->X2;
+  double* fro2 = h->scal + 8;
+  double* gw = fro2 + NJ;
+  if (!h->measuring) {
+    h->launches += batched_dot(Gam, Gam, PN, PN, NJ, fro2, h->red, h->stream);
+    h->launches += batched_dot(Gam, W, PN, PN, NJ, gw, h->red, h->stream);
+    h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream);
+  }
+  const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
+  for (const PolarBlock& blk : sched) {
+    // A = X X^T
+    GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
+    add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
+    run(h, g, prec);
+    if (!h->measuring) {
+      h->launches += symmetrize(h->pA, P, NJ, h->stream);
+      h->launches += set_identity(h->pF, P, NJ, h->stream);
+    }
+    for (size_t j = 0; j < blk.steps.size(); ++j) {
+      if (!h->measuring)
+        h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, blk.steps[j].first,
+                                        blk.steps[j].second, h->stream);
+      // F <- Pm F ; T <- A Pm ; A <- Pm T
+      GemmDesc a = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
+      add(a, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pF, 1, P, 0, 0, PP), P));
+      run(h, a, 0);
+      if (!h->measuring) {
+        cudaMemcpyAsync(h->pF, h->pT, NJ * PP * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+      }
+      if (j + 1 < blk.steps.size()) {
+        GemmDesc b = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
+        add(b, grp(op(h->pA, P, 1, 0, 0, PP), op(h->pP, 1, P, 0, 0, PP), P));
+        run(h, b, 0);
+        GemmDesc c = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
+        add(c, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pT, 1, P, 0, 0, PP), P));
+        run(h, c, 0);
+        if (!h->measuring) h->launches += symmetrize(h->pA, P, NJ, h->stream);
+      }
+    }
+    // X2 = F X ; swap
+    GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
+    add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
+    run(h, f, prec);
+    std::swap(X, X2);
+  }
+  if (prec != 0) {
+    // FP64 polish: A = X X^T (FP64), X2 = X - 0.5 (A - I) X
+    GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
+    add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
+    run(h, g, 0);
+    if (!h->measuring) {
+      h->launches += symmetrize(h->pA, P, NJ, h->stream);
+      h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, -1.0, -1.0, h->stream);  // A - I
+      cudaMemcpyAsync(X2, X, NJ * PN * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    }
+    GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN, -0.5, 1.0);
+    add(f, grp(op(h->pP, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
+    run(h, f, prec);
+    std::swap(X, X2);
+  }
+  if (!h->measuring) h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
+}
+
+// Adjoints of site layer t from those of t+1 through (new) w_t.
+void descend(ttn_ctx* h, Instance& I, int t, int prec) {
+  const LayerView v = view(I, t);
+  const int K = I.K;
+  const double* W = I.W[t];
+  const ll slab = (ll)v.NJ * v.Pn2;
+  const ll PP = (ll)v.P * v.P;
+  double* Yt = h->Yt;     // [j][J] G_j W
+  {
+    GemmDesc d = desc(v.P, (int)v.n2, 1 + 2 * K, v.NJ, Yt, v.n2, 1, slab, v.Pn2);
+    add(d, grp(op(I.adj[t + 1], v.P, 1, 0, PP, v.adj_ss), op(W, 1, v.n2, 0, 0, v.Pn2), v.P));
+    run(h, d, prec);
+  }
+  double* WB = h->M1;              // W B_{k,R}
+  double* AW = h->M1 + K * slab;   // A_{k,L}^T W
+  right_mult(h, v, W, v.opsR, 1 + K, K, false, WB, slab, prec);
+  left_mult(h, v, W, v.opsL, 1, K, false, AW, slab, prec);
+  // trace_r(T, Y)[l,l'] = sum_{p,r} T[p,l,r] Y[p,l',r];  trace_l(T, Y)[r,r'] = sum_{p,l} T[p,l,r] Y[p,l,r']
+  auto tr_r = [&](const double* Tt, ll tb0, const double* Y, ll yb0) {
+    return grp(op(Tt, v.n, 1, v.n2, tb0, v.Pn2), op(Y, v.n, 1, v.n2, yb0, v.Pn2), v.n, v.P);
+  };
+  auto tr_l = [&](const double* Tt, ll tb0, const double* Y, ll yb0) {
+    return grp(op(Tt, 1, v.n, v.n2, tb0, v.Pn2), op(Y, 1, v.n, v.n2, yb0, v.Pn2), v.n, v.P);
+  };
+  double* out = I.adj[t];
+  const ll n2 = v.n2;
+  if (!I.per_node) {
+    GemmDesc r = desc(v.n, v.n, 1, 1, out, v.n, 1, 0, 0);
+    add(r, tr_r(W, 0, Yt, 0));
+    add(r, tr_l(W, 0, Yt, 0));
+    run(h, r, prec);
+    GemmDesc p = desc(v.n, v.n, K, 1, out + n2, v.n, 1, n2, 0);
+    add(p, tr_r(WB, slab, Yt, 0));
+    add(p, tr_l(W, 0, Yt + slab, slab));
+    run(h, p, prec);
+    GemmDesc q = desc(v.n, v.n, K, 1, out + (1 + K) * n2, v.n, 1, n2, 0);
+    add(q, tr_l(AW, slab, Yt, 0));
+    add(q, tr_r(W, 0, Yt + (1 + K) * slab, slab));
+    run(h, q, prec);
+  } else {
+    const ll ss = v.ss;
+    double* outL = out;          // site 2J
+    double* outR = out + ss;     // site 2J+1
+    const ll so = 2 * ss;        // per node
+    GemmDesc r1 = desc(v.n, v.n, 1, v.NJ, outL, v.n, 1, 0, so);
+    add(r1, tr_r(W, 0, Yt, 0));
+    run(h, r1, prec);
+    GemmDesc r2 = desc(v.n, v.n, 1, v.NJ, outR, v.n, 1, 0, so);
+    add(r2, tr_l(W, 0, Yt, 0));
+    run(h, r2, prec);
+    GemmDesc p1 = desc(v.n, v.n, K, v.NJ, outL + n2, v.n, 1, n2, so);
+    add(p1, tr_r(WB, slab, Yt, 0));
+    run(h, p1, prec);
+    GemmDesc p2 = desc(v.n, v.n, K, v.NJ, outR + n2, v.n, 1, n2, so);
+    add(p2, tr_l(W, 0, Yt + slab, slab));
+    run(h, p2, prec);
+    GemmDesc q1 = desc(v.n, v.n, K, v.NJ, outR + (1 + K) * n2, v.n, 1, n2, so);
+    add(q1, tr_l(AW, slab, Yt, 0));
+    run(h, q1, prec);
+    GemmDesc q2 = desc(v.n, v.n, K, v.NJ, outL + (1 + K) * n2, v.n, 1, n2, so);
+    add(q2, tr_r(W, 0, Yt + (1 + K) * slab, slab));
+    run(h, q2, prec);
+  }
+}
+
+void forward(ttn_ctx* h, Instance& I, int prec) {
+  for (int t = 0; t < I.T; ++t) ascend_layer(h, I, t, prec);
+}
+
+void sweep_instance(ttn_ctx* h, Instance& I) {
+  const int prec = h->opt.prec;
+  forward(h, I, prec);
+  top_solve(h, I, I.E);
+  top_adjoints(h, I);
+  for (int t = I.T - 1; t >= 0; --t) {
+    environment(h, I, t, prec, h->Gam);
+    polar(h, I, t, prec, h->Gam);
+    descend(h, I, t, prec);
+  }
+}
+
+// Adjoints of every site layer at the stored tensors (no update).
+void adjoints_only(ttn_ctx* h, Instance& I, int down_to) {
+  forward(h, I, 0);
+  top_adjoints(h, I);
+  for (int t = I.T - 1; t >= down_to; --t) descend(h, I, t, 0);
+}
+
+// Plan all scratch sizes (pass with base == nullptr) or carve them.
+void layout(ttn_ctx* h, Arena& ar) {
+  size_t slab_max = 0, pp_max = 0, c2_max = 0, nj_max = 1;
+  int K_max = 1;
+  for (Instance& I : h->inst) {
+    I.W.assign(I.T, nullptr);
+    I.ops.assign(I.T + 1, nullptr);
+    I.adj.assign(I.T + 1, nullptr);
+    for (int t = 0; t < I.T; ++t) {
+      I.W[t] = ar.take(I.w_elems(t));
+      slab_max = std::max(slab_max, I.w_elems(t));
+      pp_max = std::max(pp_max, (size_t)I.nodes(t) * I.chis[t + 1] * I.chis[t + 1]);
+      nj_max = std::max(nj_max, (size_t)I.nodes(t));
+    }
+    for (int t = 0; t <= I.T; ++t) {
+      I.ops[t] = ar.take(I.op_elems(t));
+      I.adj[t] = ar.take(I.op_elems(t));
+    }
+    const int c = I.chis[I.T];
+    I.V = ar.take((size_t)c * c);
+    I.Vprev = ar.take((size_t)c * c);
+    I.E = ar.take(4);
+    c2_max = std::max(c2_max, (size_t)c * c);
+    K_max = std::max(K_max, I.K);
+  }
+  h->Y = ar.take((1 + 4 * K_max) * slab_max);
+  h->Yt = ar.take((1 + 2 * K_max) * slab_max);
+  h->M1 = ar.take(2 * K_max * slab_max);
+  h->Gam = ar.take(slab_max);
+  h->X = ar.take(slab_max);
+  h->X2 = ar.take(slab_max);
+  h->pA = ar.take(pp_max);
+  h->pF = ar.take(pp_max);
+  h->pP = ar.take(pp_max);
+  h->pT = ar.take(pp_max);
+  h->red = ar.take(std::max<size_t>(kDotBlocks * (h->lz_m + 2), kDotBlocks * nj_max * 2));
+  h->scal = ar.take(16 + 2 * nj_max);
+  h->lz_basis = ar.take((h->lz_m + 1) * c2_max);
+  h->lz_w = ar.take(c2_max);
+  h->lz_tmp = ar.take(2 * K_max * c2_max);
+  h->lz_c1 = ar.take(h->lz_m + 2);
+  h->lz_c2 = ar.take(h->lz_m + 2);
+  h->lz_alpha = ar.take(h->lz_m + 2);
+  h->lz_beta = ar.take(h->lz_m + 2);
+  h->lz_y = ar.take(h->lz_m + 2);
+  h->top_stack0 = ar.take((1 + 2 * K_max) * c2_max);
+  h->top_stack1 = ar.take((1 + 2 * K_max) * c2_max);
+  h->iflags = ar.take_int(8);
+  h->E_hist = ar.take(4096 * h->inst.size() + 16);
+  h->partial = ar.take(h->partial_cap);
+}
+
+int fail(ttn_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int check_cuda(ttn_ctx* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TTN_OK;
+  return fail(h, TTN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int build_instances(ttn_ctx* h, const ttn_problem* probs, int n) {
+  for (int i = 0; i < n; ++i) {
+    const ttn_problem& p = probs[i];
+    if (p.Lx < 4 || !is_pow2(p.Lx) || p.Ly < 1 || p.d < 2 || p.chi < 1 || p.K < 1 ||
+        !p.onesite || !p.A || !p.B)
+      return fail(h, TTN_EINVAL, "problem " + std::to_string(i) + ": bad shape or null terms");
+    Instance I;
+    I.L = p.Lx; I.Ly = p.Ly; I.K = p.K; I.per_node = p.per_node ? 1 : 0; I.chi = p.chi;
+    double d0f = std::pow((double)p.d, p.Ly);
+    if (d0f > 4096) return fail(h, TTN_EINVAL, "d^Ly too large");
+    I.d0 = (int)d0f;
+    if (!is_pow2(I.d0)) return fail(h, TTN_EINVAL, "d^Ly must be a power of two");
+    I.n_spins = p.Lx * p.Ly;
+    I.T = ilog2(p.Lx) - 1;
+    I.chis.push_back(I.d0);
+    for (int t = 0; t < I.T; ++t) {
+      long long sq = (long long)I.chis.back() * I.chis.back();
+      I.chis.push_back((int)std::min<long long>(p.chi, sq));
+    }
+    for (int c : I.chis)
+      if (!is_pow2(c)) return fail(h, TTN_EINVAL, "bond dimensions must be powers of two");
+    if (I.chis.back() * (long long)I.chis.back() > (1 << 20))
+      return fail(h, TTN_EINVAL, "top tensor too large");
+    const size_t d2 = (size_t)I.d0 * I.d0;
+    I.o.assign(p.onesite, p.onesite + d2);
+    I.A.assign(p.A, p.A + d2 * p.K);
+    I.B.assign(p.B, p.B + d2 * p.K);
+    for (double x : I.o) if (!std::isfinite(x)) return fail(h, TTN_ENAN, "non-finite one-site term");
+    for (double x : I.A) if (!std::isfinite(x)) return fail(h, TTN_ENAN, "non-finite product term");
+    for (double x : I.B) if (!std::isfinite(x)) return fail(h, TTN_ENAN, "non-finite product term");
+    const double sh = h->opt.shift;
+    I.c = std::isnan(sh) ? bond_lambda_max(I.o.data(), I.A.data(), I.B.data(), I.d0, I.K) : sh;
+    h->inst.push_back(I);
+  }
+  return TTN_OK;
+}
+
+void plan(ttn_ctx* h) {
+  h->measuring = true;
+  h->partial_cap = 0;
+  for (Instance& I : h->inst) {
+    sweep_instance(h, I);
+    adjoints_only(h, I, 0);
+    energy_only(h, I, nullptr);
+  }
+  h->measuring = false;
+}
+
+void setup_schedules(ttn_ctx* h) {
+  const double l0 = std::max(h->opt.polar_damping * 0.25, 1e-300);
+  h->polar_f64 = polar_schedule(l0, 1e5, 1e-15, 16);
+  h->polar_tc = polar_schedule(l0, 30.0, 1e-7, 8);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+
+extern "C" {
+
+void ttn_default_options(ttn_options* o) {
+  if (!o) return;
+  o->prec = TTN_FP64;
+  o->top_mode = 0;
+  o->lanczos_tol = 1e-13;
+  o->lanczos_max = 48;
+  o->lanczos_restarts = 3;
+  o->shift = NAN;
+  o->polar_damping = 1e-10;
+  o->deterministic = 1;
+  o->use_graph = 1;
+}
+
+static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_options* opt) {
+  if (!probs || n <= 0) return fail(h, TTN_EINVAL, "no problems");
+  if (opt) h->opt = *opt; else ttn_default_options(&h->opt);
+  if (h->opt.prec < 0 || h->opt.prec > 4) return fail(h, TTN_EINVAL, "bad precision");
+  if (h->opt.lanczos_max < 2 || h->opt.lanczos_max > 120) return fail(h, TTN_EINVAL, "lanczos_max in [2,120]");
+  if (h->opt.lanczos_restarts < 1) h->opt.lanczos_restarts = 1;
+  if (!(h->opt.polar_damping >= 0.0)) return fail(h, TTN_EINVAL, "polar_damping < 0");
+  h->lz_m = h->opt.lanczos_max;
+  int rc = build_instances(h, probs, n);
+  if (rc) return rc;
+  setup_schedules(h);
+  Arena a0;
+  a0.base = reinterpret_cast<char*>((size_t)1 << 40);   // fake address, never dereferenced
+  a0.registry = &h->registry;
+  layout(h, a0);          // sizes of everything but the partial buffer
+  plan(h);                // partial buffer size; bounds of every product
+  h->registry.clear();
+  if (!h->bounds_error.empty()) return fail(h, TTN_EINVAL, "internal bounds check: " + h->bounds_error);
+  return TTN_OK;
+}
+
+size_t ttn_workspace_bytes(const ttn_problem* probs, int n, const ttn_options* opt) {
+  ttn_ctx tmp;
+  if (prepare(&tmp, probs, n, opt)) return 0;
+  Arena a;
+  layout(&tmp, a);
+  return a.off + 256;
+}
+
+int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* opt, void* d_ws,
+               size_t bytes, void* stream) {
+  if (!out) return TTN_EINVAL;
+  *out = nullptr;
+  ttn_ctx* h = new ttn_ctx();
+  int rc = prepare(h, probs, n, opt);
+  if (rc) { *out = h; return rc; }
+  Arena a;
+  layout(h, a);
+  if (!d_ws || bytes < a.off) { *out = h; return fail(h, TTN_ENOMEM, "workspace too small: need " + std::to_string(a.off)); }
+  Arena real;
+  real.base = reinterpret_cast<char*>(d_ws);
+  layout(h, real);
+  h->user = reinterpret_cast<cudaStream_t>(stream);
+  rc = check_cuda(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+  if (rc) { *out = h; return rc; }
+  // upload operators of site layer 0 (shifted one-site term)
+  for (Instance& I : h->inst) {
+    const size_t d2 = (size_t)I.d0 * I.d0;
+    std::vector<double> host((size_t)(1 + 2 * I.K) * d2);
+    for (size_t e = 0; e < d2; ++e) host[e] = I.o[e];
+    for (int i = 0; i < I.d0; ++i) host[(size_t)i * I.d0 + i] -= I.c;
+    std::memcpy(host.data() + d2, I.A.data(), I.K * d2 * sizeof(double));
+    std::memcpy(host.data() + (1 + I.K) * d2, I.B.data(), I.K * d2 * sizeof(double));
+    for (int s = 0; s < I.sites(0); ++s) {
+      rc = check_cuda(h, cudaMemcpyAsync(I.ops[0] + s * host.size(), host.data(),
+                                         host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                         h->stream), "upload");
+      if (rc) { *out = h; return rc; }
+    }
+  }
+  rc = check_cuda(h, cudaStreamSynchronize(h->stream), "create sync");
+  *out = h;
+  return rc;
+}
+
+int ttn_sizes(ttn_t h, int inst, size_t* n_w, size_t* n_v, int* n_layers) {
+  if (!h || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  const Instance& I = h->inst[inst];
+  size_t s = 0;
+  for (int t = 0; t < I.T; ++t) s += I.w_elems(t);
+  if (n_w) *n_w = s;
+  if (n_v) *n_v = (size_t)I.chis[I.T] * I.chis[I.T];
+  if (n_layers) *n_layers = I.T;
+  return TTN_OK;
+}
+
+int ttn_chis(ttn_t h, int inst, int* chis) {
+  if (!h || !chis || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  const Instance& I = h->inst[inst];
+  for (int t = 0; t <= I.T; ++t) chis[t] = I.chis[t];
+  return TTN_OK;
+}
+
+static int sync_user(ttn_ctx* h) {
+  // order: work on the library stream starts after what the user enqueued
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, h->user);
+  cudaStreamWaitEvent(h->stream, ev, 0);
+  cudaEventDestroy(ev);
+  return TTN_OK;
+}
+
+int ttn_set_isometries(ttn_t h, int inst, const double* w, const double* v) {
+  if (!h || !w || !v || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  Instance& I = h->inst[inst];
+  sync_user(h);
+  size_t off = 0;
+  for (int t = 0; t < I.T; ++t) {
+    int rc = check_cuda(h, cudaMemcpyAsync(I.W[t], w + off, I.w_elems(t) * sizeof(double),
+                                           cudaMemcpyHostToDevice, h->stream), "set w");
+    if (rc) return rc;
+    off += I.w_elems(t);
+  }
+  const size_t c2 = (size_t)I.chis[I.T] * I.chis[I.T];
+  int rc = check_cuda(h, cudaMemcpyAsync(I.V, v, c2 * sizeof(double), cudaMemcpyHostToDevice,
+                                         h->stream), "set v");
+  if (rc) return rc;
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "set sync");
+}
+
+int ttn_get_isometries(ttn_t h, int inst, double* w, double* v) {
+  if (!h || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  Instance& I = h->inst[inst];
+  size_t off = 0;
+  for (int t = 0; t < I.T && w; ++t) {
+    int rc = check_cuda(h, cudaMemcpyAsync(w + off, I.W[t], I.w_elems(t) * sizeof(double),
+                                           cudaMemcpyDeviceToHost, h->stream), "get w");
+    if (rc) return rc;
+    off += I.w_elems(t);
+  }
+  if (v) {
+    const size_t c2 = (size_t)I.chis[I.T] * I.chis[I.T];
+    int rc = check_cuda(h, cudaMemcpyAsync(v, I.V, c2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                           h->stream), "get v");
+    if (rc) return rc;
+  }
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "get sync");
+}
+
+static void enqueue_sweep(ttn_ctx* h) {
+  for (Instance& I : h->inst) sweep_instance(h, I);
+}
+
+int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
+  if (!h || n_sweeps < 0) return TTN_EINVAL;
+  if (n_sweeps == 0) return TTN_OK;
+  sync_user(h);
+  const int ni = (int)h->inst.size();
+  int rc = TTN_OK;
+  h->launches = 0;
+  const bool graph = h->opt.use_graph != 0;
+  if (graph && !h->exec) {
+    rc = check_cuda(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "capture");
+    if (rc) return rc;
+    enqueue_sweep(h);
+    rc = check_cuda(h, cudaStreamEndCapture(h->stream, &h->graph), "end capture");
+    if (rc) return rc;
+    rc = check_cuda(h, cudaGraphInstantiate(&h->exec, h->graph, 0), "instantiate");
+    if (rc) return rc;
+    h->launches_per_sweep = h->launches;
+  }
+  h->launches = 0;
+  std::vector<double> buf;
+  int done = 0;
+  while (done < n_sweeps) {
+    const int chunk = std::min(n_sweeps - done, 4096 / 1);
+    for (int s = 0; s < chunk; ++s) {
+      if (graph) {
+        rc = check_cuda(h, cudaGraphLaunch(h->exec, h->stream), "graph launch");
+        if (rc) return rc;
+        h->launches += h->launches_per_sweep;
+      } else {
+        enqueue_sweep(h);
+      }
+      if (host_energy)
+        for (int i = 0; i < ni; ++i)
+          cudaMemcpyAsync(h->E_hist + (size_t)s * ni + i, h->inst[i].E, sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (host_energy) {
+      rc = check_cuda(h, cudaMemcpyAsync(host_energy + (size_t)done * ni, h->E_hist,
+                                         (size_t)chunk * ni * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream), "energies");
+      if (rc) return rc;
+      rc = check_cuda(h, cudaStreamSynchronize(h->stream), "sweep sync");
+      if (rc) return rc;
+    }
+    done += chunk;
+  }
+  h->sweeps_done += n_sweeps;
+  // make the user's stream wait for the sweeps
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, h->stream);
+  cudaStreamWaitEvent(h->user, ev, 0);
+  cudaEventDestroy(ev);
+  rc = check_cuda(h, cudaGetLastError(), "sweep");
+  if (rc) return rc;
+  if (host_energy)
+    for (int i = 0; i < n_sweeps * ni; ++i)
+      if (!std::isfinite(host_energy[i])) return fail(h, TTN_ENAN, "non-finite energy");
+  return TTN_OK;
+}
+
+int ttn_energy(ttn_t h, int inst, double* E) {
+  if (!h || !E || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  sync_user(h);
+  Instance& I = h->inst[inst];
+  forward(h, I, 0);
+  energy_only(h, I, h->scal + 5);
+  int rc = check_cuda(h, cudaMemcpyAsync(E, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost,
+                                         h->stream), "energy");
+  if (rc) return rc;
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "energy sync");
+}
+
+int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
+  if (!h || !out || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  Instance& I = h->inst[inst];
+  if (site_layer < 0 || site_layer > I.T || (which != 0 && which != 1)) return fail(h, TTN_EINVAL, "bad layer");
+  sync_user(h);
+  const int n = I.chis[site_layer];
+  const size_t n2 = (size_t)n * n;
+  std::vector<double> host;
+  if (which == 0 || I.per_node) {
+    adjoints_only(h, I, site_layer);
+    const int S = I.sites(site_layer);
+    host.resize((size_t)S * (1 + 2 * I.K) * n2);
+    int rc = check_cuda(h, cudaMemcpyAsync(host.data(), I.adj[site_layer], host.size() * sizeof(double),
+                                           cudaMemcpyDeviceToHost, h->stream), "rdm");
+    if (rc) return rc;
+    rc = check_cuda(h, cudaStreamSynchronize(h->stream), "rdm sync");
+    if (rc) return rc;
+    const size_t ss = (1 + 2 * I.K) * n2;
+    if (which == 1) {
+      for (size_t e = 0; e < n2; ++e) out[e] = host[e];
+    } else {
+      for (size_t e = 0; e < n2; ++e) {
+        double s = 0;
+        for (int j = 0; j < S; ++j) s += host[j * ss + e];
+        out[e] = s / (double)(I.L >> site_layer);
+      }
+    }
+    return TTN_OK;
+  }
+  // translation-invariant tree, leftmost site: rho = V V^T, then Tr_r(W^T rho W) downwards
+  const int c = I.chis[I.T];
+  double* rho = h->pA;
+  {
+    GemmDesc d = desc(c, c, 1, 1, rho, c, 1, 0, 0);
+    add(d, grp(op(I.V, c, 1), op(I.V, c, 1), c));
+    run(h, d, 0);
+  }
+  for (int t = I.T - 1; t >= site_layer; --t) {
+    const LayerView v = view(I, t);
+    GemmDesc g = desc(v.P, (int)v.n2, 1, 1, h->Yt, v.n2, 1, 0, 0);
+    add(g, grp(op(rho, v.P, 1), op(I.W[t], 1, v.n2), v.P));
+    run(h, g, 0);
+    GemmDesc r = desc(v.n, v.n, 1, 1, rho, v.n, 1, 0, 0);
+    add(r, grp(op(I.W[t], v.n, 1, v.n2), op(h->Yt, v.n, 1, v.n2), v.n, v.P));
+    run(h, r, 0);
+  }
+  int rc = check_cuda(h, cudaMemcpyAsync(out, rho, n2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "rdm");
+  if (rc) return rc;
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "rdm sync");
+}
+
+int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
+  if (!h || !d_out || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  Instance& I = h->inst[inst];
+  if (layer < 0 || layer >= I.T) return fail(h, TTN_EINVAL, "bad layer");
+  sync_user(h);
+  adjoints_only(h, I, layer + 1);
+  environment(h, I, layer, 0, h->Gam);
+  int rc = check_cuda(h, cudaMemcpyAsync(d_out, h->Gam, I.w_elems(layer) * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, h->stream), "env");
+  if (rc) return rc;
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+}
+
+int ttn_get_state(ttn_t h, void* buf, size_t* bytes) {
+  if (!h || !bytes) return TTN_EINVAL;
+  size_t need = 2 * sizeof(long long);
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    size_t nw, nv;
+    ttn_sizes(h, (int)i, &nw, &nv, nullptr);
+    need += (nw + nv + 1) * sizeof(double);
+  }
+  if (!buf) { *bytes = need; return TTN_OK; }
+  if (*bytes < need) return fail(h, TTN_EINVAL, "state buffer too small");
+  char* p = reinterpret_cast<char*>(buf);
+  long long hdr[2] = {(long long)h->inst.size(), (long long)h->sweeps_done};
+  std::memcpy(p, hdr, sizeof(hdr));
+  p += sizeof(hdr);
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    size_t nw, nv;
+    ttn_sizes(h, (int)i, &nw, &nv, nullptr);
+    double* d = reinterpret_cast<double*>(p);
+    d[0] = h->inst[i].c;
+    int rc = ttn_get_isometries(h, (int)i, d + 1, d + 1 + nw);
+    if (rc) return rc;
+    p += (nw + nv + 1) * sizeof(double);
+  }
+  *bytes = need;
+  return TTN_OK;
+}
+
+int ttn_set_state(ttn_t h, const void* buf, size_t bytes) {
+  if (!h || !buf) return TTN_EINVAL;
+  const char* p = reinterpret_cast<const char*>(buf);
+  long long hdr[2];
+  if (bytes < sizeof(hdr)) return fail(h, TTN_EINVAL, "state too short");
+  std::memcpy(hdr, p, sizeof(hdr));
+  if (hdr[0] != (long long)h->inst.size()) return fail(h, TTN_EINVAL, "state instance count");
+  p += sizeof(hdr);
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    size_t nw, nv;
+    ttn_sizes(h, (int)i, &nw, &nv, nullptr);
+    const double* d = reinterpret_cast<const double*>(p);
+    if (d[0] != h->inst[i].c) return fail(h, TTN_EINVAL, "state was made with another shift");
+    int rc = ttn_set_isometries(h, (int)i, d + 1, d + 1 + nw);
+    if (rc) return rc;
+    p += (nw + nv + 1) * sizeof(double);
+  }
+  h->sweeps_done = (int)hdr[1];
+  return TTN_OK;
+}
+
+long long ttn_launch_count(ttn_t h) { return h ? h->launches : 0; }
+
+const char* ttn_last_error(ttn_t h) { return h ? h->err.c_str() : "null handle"; }
+
+void ttn_destroy(ttn_t h) {
+  if (!h) return;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->stream) { cudaStreamSynchronize(h->stream); cudaStreamDestroy(h->stream); }
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+"""Parity of the CUDA sweep (through the C ABI) with the FP64 oracle.
+
+Two kinds of comparison:
+* resynchronised: GPU and oracle start one sweep from the same tensors; the
+  energy of the top solve and the energy of the updated tensors must agree to
+  1e-10 relative (FP64 mode);
+* trajectories over several sweeps from the seeded start.  The sweep amplifies
+  rounding differences (the polar factor of a nearly rank-deficient
+  environment is ill-conditioned), so trajectories are compared at a looser,
+  measured tolerance.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import ttn_inputs as ti
+from oracle import ed
+from oracle import ttn as oracle
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sweeper(model, chi, per_node=False, **kw):
+    from paper_1905_01331_gb300 import Sweeper
+    return Sweeper(model, chi, per_node=per_node, **kw)
+
+
+def _resync_check(model, chi, seed, per_node=False, warm=2, checks=2, tol=1e-10, prec="fp64"):
+    ws, V = ti.initial_tensors(model.Lx, model.d0, chi, seed, per_node)
+    st = oracle.make_state(model, ws, V, per_node=per_node)
+    for _ in range(warm):
+        oracle.sweep(st)
+    s = _sweeper(model, chi, per_node, prec=prec)
+    worst = 0.0
+    for _ in range(checks):
+        s.set_isometries(0, st.ws, st.V)
+        E_gpu = s.sweep(1)[0, 0]
+        ws_g, V_g = s.get_isometries(0)
+        E_ref = oracle.sweep(st)
+        # energy of the GPU's updated tensors, evaluated by the oracle
+        st_g = oracle.make_state(model, ws_g, V_g, c=st.c, per_node=per_node)
+        E_next_g = oracle.energy(st_g)
+        E_next_o = oracle.energy(st)
+        worst = max(worst, abs(E_gpu - E_ref) / abs(E_ref), abs(E_next_g - E_next_o) / abs(E_next_o))
+        for w in ws_g:
+            Wm = w.reshape(-1, w.shape[-3], w.shape[-2] * w.shape[-1])
+            for x in Wm:
+                assert np.abs(x @ x.T - np.eye(x.shape[0])).max() < 1e-11
+    s.close()
+    assert worst < tol, worst
+    return worst
+
+
+def test_energy_function_parity():
+    m = ti.heisenberg_xxx(32)
+    ws, V = ti.initial_tensors(32, 2, 8, 3)
+    s = _sweeper(m, 8)
+    s.set_isometries(0, ws, V)
+    st = oracle.make_state(m, ws, V)
+    assert abs(s.energy(0) - oracle.energy(st)) < 1e-12 * abs(oracle.energy(st))
+
+
+@pytest.mark.parametrize("per_node", [False, True])
+def test_env_and_rdm_parity(per_node):
+    m = ti.heisenberg_xxx(16)
+    ws, V = ti.initial_tensors(16, 2, 4, 13, per_node)
+    st = oracle.make_state(m, ws, V, per_node=per_node)
+    s = _sweeper(m, 4, per_node)
+    s.set_isometries(0, ws, V)
+    for layer in range(len(ws)):
+        g_ref = oracle.env_layer(st, layer)
+        g = s.env(0, layer).cpu().numpy()
+        assert np.abs(g - g_ref).max() < 1e-12 * max(1.0, np.abs(g_ref).max())
+    for t in range(len(ws) + 1):
+        for which in (0, 1):
+            r_ref = oracle.rdm(st, t, which)
+            r = s.rdm(0, t, which)
+            assert np.abs(r - r_ref).max() < 1e-12
+
+
+def test_resync_tfim_l16_per_node():
+    _resync_check(ti.tfim_chain(16, 1.0), 8, 0, per_node=True, warm=3, checks=3)
+
+
+def test_resync_tfim_l1024_chi32():
+    _resync_check(ti.tfim_chain(1024, 1.0), 32, 1, warm=5, checks=2)
+
+
+def test_resync_heisenberg_nonsymmetric_factors():
+    _resync_check(ti.heisenberg_xxx(64), 16, 2, warm=3, checks=2)
+
+
+def test_resync_thin_torus():
+    _resync_check(ti.tfim_torus(8, 4, 3.04), 32, 3, warm=2, checks=2)
+
+
+def test_full_chi_is_exact_on_gpu():
+    m = ti.tfim_chain(8, 1.0)
+    ws, V = ti.initial_tensors(8, 2, 16, 5)
+    s = _sweeper(m, 16)
+    s.set_isometries(0, ws, V)
+    E = s.sweep(1)[0, 0]
+    E0 = ed.tfim_closed_form(8, 1.0)
+    assert abs(E - E0) < 1e-11 * abs(E0)
+
+
+def test_trajectory_l16_per_node_30_sweeps():
+    wl = ti.tfim_l16_pernode()
+    ws, V = ti.initial_tensors(16, 2, 8, wl.seed, True)
+    s = _sweeper(wl.model, 8, True)
+    s.set_isometries(0, ws, V)
+    E = s.sweep(30)[:, 0]
+    with open(os.path.join(GOLDEN, "oracle_tfim_L16_chi8_pernode.json")) as f:
+        ref = np.array(json.load(f)["energies"])
+    rel = np.abs(E - ref) / np.abs(ref)
+    print("max rel deviation over 30 sweeps", rel.max(), rel[:5])
+    assert np.all(np.diff(E) <= 1e-9 * np.abs(E[1:]))
+    assert rel[:5].max() < 1e-10
+    assert rel.max() < 1e-6
+
+
+def test_checkpoint_resume_is_bitwise():
+    m = ti.tfim_chain(64, 1.0)
+    ws, V = ti.initial_tensors(64, 2, 16, 7)
+    a = _sweeper(m, 16)
+    a.set_isometries(0, ws, V)
+    Ea = a.sweep(6)[:, 0]
+    b = _sweeper(m, 16)
+    b.set_isometries(0, ws, V)
+    Eb1 = b.sweep(3)[:, 0]
+    blob = b.get_state()
+    c = _sweeper(m, 16)
+    c.set_state(blob)
+    Eb2 = c.sweep(3)[:, 0]
+    assert np.array_equal(Ea, np.concatenate([Eb1, Eb2]))
