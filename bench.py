@@ -1,0 +1,337 @@
+"""Benchmark of the TTN sweep on GB300 (one JSON line on stdout).
+
+Workload: the critical transverse-field Ising chain, L = 1024, h = 1, one
+shared isometry per layer, bond dimension chi = 128 (chi_t = 2, 4, 16, 128 ...),
+seeded QR-orthonormalised Gaussian start (seed 1).  A step is one sweep.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|fp64|...]
+    python bench.py --impl reference ...      # the FP64 CPU oracle, same workload
+
+The GPU arm reports sweeps/s of the chosen precision with the tensors resident
+in HBM (``value``), the same through the C ABI with host buffers (``e2e``), the
+FP64 GPU path for comparison, the energy error against the oracle's reference
+trajectory, the roofline of the dominant kernel family and the oracle timed on
+this host (``cpu_baseline``).  With N > 1 (torchrun) every rank advances its own
+replica: the sweep of one instance does not shard (replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "tfim_chain_L1024_h1_chi128", "L": 1024, "h": 1.0, "chi": 128,
+            "seed": 1, "model": "transverse-field Ising chain, periodic",
+            "tree": "binary TTN, one isometry per layer"}
+METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--prec", default=os.environ.get("TTN_BENCH_PREC", "tf32x3"))
+    p.add_argument("--chi", type=int, default=128)
+    p.add_argument("--no-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the same workload
+# --------------------------------------------------------------------------
+
+def oracle_sweeps_per_s(n_sweeps: int, warm: int, chi: int):
+    import numpy as np  # noqa: F401
+    import ttn_inputs as ti
+    from oracle import ttn as oracle
+    m = ti.tfim_chain(1024, 1.0)
+    ws, V = ti.initial_tensors(1024, 2, chi, 1)
+    st = oracle.make_state(m, ws, V)
+    for _ in range(warm):
+        oracle.sweep(st)
+    t0 = time.perf_counter()
+    for _ in range(n_sweeps):
+        oracle.sweep(st)
+    dt = time.perf_counter() - t0
+    return n_sweeps / dt, dt
+
+
+def threads_used():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # each step is one full oracle sweep of the workload
+    v, dt = oracle_sweeps_per_s(args.steps, args.warmup, args.chi)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded QR-orthonormalised Gaussian isometries)",
+            "config": dict(WORKLOAD, precision="fp64", engine="numpy/LAPACK oracle"),
+            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": threads_used(), "kind": "oracle",
+                             "sample": f"{args.steps} full sweeps after {args.warmup} warm-up sweeps"},
+            "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def golden_energy(chi, sweeps):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_tfim_L1024_chi{chi}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    E = g["energies"]
+    return E[sweeps - 1] if len(E) >= sweeps else None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import ttn_inputs as ti
+    from oracle import flops as oracle_flops
+    from paper_1905_01331_gb300 import Sweeper, _abi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    chi = args.chi
+    model = ti.tfim_chain(1024, 1.0)
+    ws, V = ti.initial_tensors(1024, 2, chi, 1)
+    s = Sweeper(model, chi, prec=args.prec)
+    s.set_isometries(0, ws, V)
+    chis = s.chis(0)
+    flops_per_sweep = oracle_flops.sweep_flops(1024, chis, 1, symmetric=True)
+
+    # warm-up (also builds the CUDA graph)
+    s.sweep(args.warmup)
+    stream = s.stream
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.sweep_async(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max * 1e-3)
+
+    # profiling sweep: dominant kernel family
+    prof = s.profile_sweep()
+
+    # e2e through the C ABI with host buffers: upload the state, one sweep,
+    # read the energy back, every step
+    n_w = sum(int(np.prod(w.shape)) for w in ws)
+    flat_host = torch.from_numpy(np.concatenate([w.ravel() for w in ws])).pin_memory()
+    v_host = torch.from_numpy(np.ascontiguousarray(V)).pin_memory()
+    E_host = np.zeros(1)
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    fp = ctypes.cast(flat_host.data_ptr(), dp)
+    vp = ctypes.cast(v_host.data_ptr(), dp)
+    ep = E_host.ctypes.data_as(dp)
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        s.lib.ttn_set_isometries(s.h, 0, fp, vp)
+        s.lib.ttn_sweep(s.h, 1, ep)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = s.lib.ttn_set_isometries(s.h, 0, fp, vp)
+        rc |= s.lib.ttn_sweep(s.h, 1, ep)
+        if rc:
+            raise RuntimeError("e2e call failed")
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "sweeps/s",
+           "h2d_bytes_per_step": 8 * (n_w + V.size), "d2h_bytes_per_step": 8}
+
+    # roofline of the dominant kernel family (grouped products)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    if prof["tc_ms"] >= prof["fp64_ms"]:
+        dom_ms, dom_fl, dom_n = prof["tc_ms"], prof["tc_flops"], prof["tc_launches"]
+        # TF32 dense peak = measured bf16 peak x nominal tf32/bf16 ratio (1/2)
+        peak = peaks.get("bf16_tflops", 1932.2) * 0.5
+        peak_src = "MEASURED_PEAKS bf16_tflops x 0.5 (nominal tf32:bf16)"
+        bound = "tensor"
+        kernel = "gemm_tc (tcgen05 grouped products)"
+    else:
+        dom_ms, dom_fl, dom_n = prof["fp64_ms"], prof["fp64_flops"], prof["fp64_launches"]
+        peak = 1.10   # measured torch float64 8192^3 matmul on GB300 (cuBLAS DGEMM)
+        peak_src = "measured cuBLAS DGEMM 8192^3 on this pool's GB300 (1.10 TFLOP/s)"
+        bound = "alu"
+        kernel = "gemm_f64_kernel (FP64 grouped products)"
+    achieved = dom_fl / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                "peak_source": peak_src, "launches_per_sweep": dom_n,
+                "ms_per_sweep": dom_ms, "share_of_sweep": dom_ms / prof["total_ms"]}
+
+    out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.prec == "fp64" else "f32(" + args.prec + ")+f64",
+           "data": "synthetic (seeded QR-orthonormalised Gaussian isometries)",
+           "config": dict(WORKLOAD, precision=args.prec, chis=chis,
+                          parallelism=("replicas x%d" % world) if world > 1 else "single GPU",
+                          l2="working set %.0f MB > 129 MB L2" % (s.workspace.numel() / 1e6)),
+           "tflops": flops_per_sweep * value / world / 1e12,
+           "algorithmic_flops_per_sweep": flops_per_sweep,
+           "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "roofline": roofline,
+           "profile": prof}
+
+    if not args.quick:
+        # energy error after 200 sweeps from the seeded start, against the
+        # oracle's reference trajectory, for this precision and for FP64
+        ref = golden_energy(chi, 200)
+
+        def err_after(prec):
+            t = Sweeper(model, chi, prec=prec)
+            t.set_isometries(0, ws, V)
+            tt = time.perf_counter()
+            E = t.sweep(200)[:, 0]
+            dt = time.perf_counter() - tt
+            E_cert = t.energy(0)
+            t.close()
+            rel = abs(E[-1] - ref) / abs(ref) if ref is not None else None
+            return {"E_200": float(E[-1]), "E_200_fp64_certified": E_cert,
+                    "energy_rel_err_vs_oracle": rel, "sweeps_per_s_200": 200 / dt}
+        out["energy"] = {"oracle_E_200": ref, args.prec: err_after(args.prec)}
+        if args.prec != "fp64":
+            out["energy"]["fp64"] = err_after("fp64")
+
+    if rank == 0 and not args.no_baseline and world == 1:
+        n = 1 if chi >= 128 else 3
+        v, dt = oracle_sweeps_per_s(n, 0, chi)
+        out["cpu_baseline"] = {"value": v, "unit": "sweeps/s", "cores": threads_used(), "kind": "oracle",
+                               "sample": f"{n} full oracle sweep(s) of the same workload from the seeded start"}
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

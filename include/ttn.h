@@ -75,11 +75,11 @@ typedef struct {
 typedef struct {
   int prec;                 /* ttn_precision */
   int top_mode;             /* 0: lowest eigenvector of the top Hamiltonian */
-  double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-12) */
+  double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-13) */
   int lanczos_max;          /* Krylov dimension per restart (default 48) */
-  int lanczos_restarts;     /* restarts per sweep (default 4) */
+  int lanczos_restarts;     /* restarts per sweep (default 3) */
   double shift;             /* bond shift c; NaN = lambda_max of the bond term */
-  double polar_damping;     /* proximal weight mu of the update (default 1e-10) */
+  double polar_damping;     /* proximal weight mu of the update (default 1e-7) */
   int deterministic;        /* 1: fixed-order reductions (always on) */
   int use_graph;            /* 1: capture a sweep as a CUDA graph and replay */
 } ttn_options;
@@ -139,6 +139,14 @@ int ttn_set_state(ttn_t h, const void* host_buf, size_t bytes);
 
 /* Kernel launches enqueued by the last ttn_sweep call (a count). */
 long long ttn_launch_count(ttn_t h);
+
+/* Run one sweep without graph capture, timing every grouped product with CUDA
+ * events on the library's stream.  out[0..8] = FP64-engine milliseconds,
+ * useful flops (2*M*N*K summed over groups and batches), launches; the same
+ * three for the tensor-core engine; milliseconds and launches of all other
+ * kernels (including event gaps); total milliseconds of the sweep.  The
+ * sweep updates the tensors like ttn_sweep.  n_out >= 9. */
+int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);

@@ -104,7 +104,7 @@ def bond_shift(o, A, B):
 
 
 # Proximal weight of the update (a reading, see ``polar_update``).
-POLAR_DAMPING = 1e-10
+POLAR_DAMPING = 1e-7
 
 
 def polar_update(gamma, w_old, damping=POLAR_DAMPING):
@@ -120,7 +120,9 @@ def polar_update(gamma, w_old, damping=POLAR_DAMPING):
     changes later sweeps at the 1e-5 level.  The update therefore takes the SVD
     of gamma - damping * ||gamma||_F * w_old: the null directions keep the old
     isometry, the fixed points w = -polar(gamma) are unchanged, and the energy
-    still cannot rise (the added term is a proximal penalty).
+    still cannot rise (the added term is a proximal penalty).  The weight 1e-7
+    bounds the condition number of the factor near 1e7, so that two correct
+    FP64 implementations of the polar factor give energies equal to ~1e-11.
     """
     P = gamma.shape[0]
     g = gamma.reshape(P, -1)

@@ -35,7 +35,7 @@ class Sweeper:
 
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
                  lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
-                 polar_damping=1e-10, use_graph=True, shift=None):
+                 polar_damping=1e-7, use_graph=True, shift=None):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -160,6 +160,14 @@ class Sweeper:
     def set_state(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(self.lib.ttn_set_state(self.h, buf, len(data)), "set_state")
+
+    def profile_sweep(self):
+        """One eagerly launched sweep with every product timed by CUDA events."""
+        out = np.zeros(9)
+        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 9), "profile_sweep")
+        keys = ["fp64_ms", "fp64_flops", "fp64_launches", "tc_ms", "tc_flops", "tc_launches",
+                "other_ms", "other_launches", "total_ms"]
+        return dict(zip(keys, out.tolist()))
 
     @property
     def launch_count(self):

@@ -46,6 +46,7 @@ SIGNATURES = {
     "ttn_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ttn_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ttn_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "ttn_profile_sweep": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int]),
     "ttn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ttn_destroy": (None, [ctypes.c_void_p]),
 }

@@ -118,6 +118,10 @@ struct ttn_ctx {
   // checked against the buffer it points into (no launch happens)
   std::vector<std::pair<size_t, size_t>> registry;
   std::string bounds_error;
+  // profiling sweep: events around every product, by engine (0 FP64, 1 TC)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, double>> ev_flops;   // (engine, flops) per event pair
 };
 
 namespace {
@@ -199,6 +203,21 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
   if (d.ngroups > kMaxGroups) return;
   d.splits = s;
   d.partial = h->partial;
+  if (h->profiling) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h->stream);
+    h->launches += gemm_launch(d, h->stream);
+    cudaEventRecord(b, h->stream);
+    h->ev_pool.push_back(a);
+    h->ev_pool.push_back(b);
+    double kk = 0.0;
+    for (int g = 0; g < d.ngroups; ++g) kk += d.g[g].K;
+    const int engine = (d.prec != 0 && gemm_tc_supported(d)) ? 1 : 0;
+    h->ev_flops.push_back({engine, 2.0 * d.M * d.N * kk * d.B0 * d.B1});
+    return;
+  }
   h->launches += gemm_launch(d, h->stream);
 }
 
@@ -745,8 +764,10 @@ void plan(ttn_ctx* h) {
 
 void setup_schedules(ttn_ctx* h) {
   const double l0 = std::max(h->opt.polar_damping * 0.25, 1e-300);
-  h->polar_f64 = polar_schedule(l0, 1e5, 1e-15, 16);
-  h->polar_tc = polar_schedule(l0, 30.0, 1e-7, 8);
+  // At most four composed steps (growth <= 30) per fresh Gram matrix: longer
+  // compositions lose accuracy on the small singular directions.
+  h->polar_f64 = polar_schedule(l0, 30.0, 1e-15, 4);
+  h->polar_tc = polar_schedule(l0, 30.0, 1e-7, 4);
 }
 
 }  // namespace
@@ -765,7 +786,7 @@ void ttn_default_options(ttn_options* o) {
   o->lanczos_max = 48;
   o->lanczos_restarts = 3;
   o->shift = NAN;
-  o->polar_damping = 1e-10;
+  o->polar_damping = 1e-7;
   o->deterministic = 1;
   o->use_graph = 1;
 }
@@ -1090,6 +1111,42 @@ int ttn_set_state(ttn_t h, const void* buf, size_t bytes) {
 }
 
 long long ttn_launch_count(ttn_t h) { return h ? h->launches : 0; }
+
+int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
+  if (!h || !out || n_out < 9) return TTN_EINVAL;
+  sync_user(h);
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  h->profiling = true;
+  h->launches = 0;
+  cudaEventRecord(t0, h->stream);
+  enqueue_sweep(h);
+  cudaEventRecord(t1, h->stream);
+  h->profiling = false;
+  int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
+  double ms[2] = {0, 0}, fl[2] = {0, 0}, cnt[2] = {0, 0};
+  for (size_t i = 0; i < h->ev_flops.size(); ++i) {
+    float e = 0.f;
+    cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
+    const int g = h->ev_flops[i].first;
+    ms[g] += e;
+    fl[g] += h->ev_flops[i].second;
+    cnt[g] += 1;
+  }
+  float tot = 0.f;
+  cudaEventElapsedTime(&tot, t0, t1);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  h->ev_flops.clear();
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
+  out[3] = ms[1]; out[4] = fl[1]; out[5] = cnt[1];
+  out[6] = tot - ms[0] - ms[1]; out[7] = (double)h->launches - cnt[0] - cnt[1]; out[8] = tot;
+  h->sweeps_done += 1;
+  return rc;
+}
 
 const char* ttn_last_error(ttn_t h) { return h ? h->err.c_str() : "null handle"; }
 
