@@ -148,6 +148,14 @@ long long ttn_launch_count(ttn_t h);
  * sweep updates the tensors like ttn_sweep.  n_out >= 9. */
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
+/* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
+ * operands over six operand layouts (K-major / M-major, two-level K and batch,
+ * ragged edges, split K, alpha/beta).  d_ws: caller device memory of at least
+ * ttn_selftest_bytes(); prec: 1..4 (ttn_precision); out_rel[i] receives
+ * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 6). */
+size_t ttn_selftest_bytes(void);
+int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out, void* stream);
+
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);
 

@@ -47,6 +47,9 @@ SIGNATURES = {
     "ttn_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ttn_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "ttn_profile_sweep": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int]),
+    "ttn_selftest_bytes": (ctypes.c_size_t, []),
+    "ttn_selftest_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, _dp,
+                                         ctypes.c_int, ctypes.c_void_p]),
     "ttn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ttn_destroy": (None, [ctypes.c_void_p]),
 }

@@ -39,6 +39,7 @@ struct GemmDesc {
   double* partial;   // splits * B0 * B1 * M * N doubles when splits > 1
   int prec;          // ttn_precision of the products
   const int* skip;   // if non-null and *skip != 0 the launch does nothing
+  int* err;          // device flag raised when a bounded wait of a kernel expires
 };
 
 // Launch one grouped product on `stream` (FP64 CUDA-core kernel or tcgen05
@@ -52,6 +53,8 @@ size_t gemm_partial_elems(const GemmDesc& d, int splits);
 // Tensor-core path (gemm_tc.cu).
 int gemm_tc_launch(const GemmDesc& d, cudaStream_t stream);
 bool gemm_tc_supported(const GemmDesc& d);
+int tc_pick_splits(const GemmDesc& d);
+void gemm_tc_init();
 
 // ---------------------------------------------------------------------------
 // Small kernels (misc.cu).  All reductions are two-pass with fixed order.

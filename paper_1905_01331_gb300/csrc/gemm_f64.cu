@@ -157,6 +157,7 @@ int launch_tile(const GemmDesc& d, cudaStream_t s) {
 }  // namespace
 
 int gemm_pick_splits(const GemmDesc& d) {
+  if (d.prec != 0 && gemm_tc_supported(d)) return tc_pick_splits(d);
   const int bm = (d.M >= 64 && d.N >= 64) ? 64 : (d.M >= 32 && d.N >= 32) ? 32 : 16;
   const int bn = bm;
   const long long base = (long long)((d.M + bm - 1) / bm) * ((d.N + bn - 1) / bn) * d.B0 * d.B1;

@@ -1,10 +1,430 @@
-// Tensor-core (tcgen05) path of the grouped product: placeholder until the
-// sm_103a kernel is in; every descriptor then runs on the FP64 kernel.
+// Tensor-core (tcgen05) engine of the grouped products, sm_103a.
+//
+// The O(chi^4) contractions of the sweep (Sec. III.A; Sec. V: "the cost
+// scales as chi^4") run here in split precision: every FP64 operand element x
+// is cut into a TF32 (or BF16) head h = round(x) and tail l = round(x - h) on
+// the way into shared memory, and the product is accumulated in FP32 tensor
+// memory as  A_l B_h + A_h B_l + A_h B_h  (3xTF32 / BF16x3) or A_h B_h alone.
+//
+// One CTA owns a 128 x BN output tile.  All 256 threads stage operand tiles
+// (any strides: the two-level K/batch index of GemmDesc), converting FP64 to
+// the MMA type and writing the K-major SWIZZLE_128B canonical layout; one
+// thread issues tcgen05.mma into a TMEM accumulator and commits to an
+// mbarrier per stage, so that staging of the next K tile overlaps the MMAs of
+// the current one (two stages).  The epilogue reads TMEM with tcgen05.ld and
+// writes FP64 (or a split-K partial).  Every mbarrier wait is bounded; on a
+// timeout the kernel raises an error flag, waits (bounded) for its own MMAs,
+// frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
 #include "common.h"
 
 namespace ttn {
 
-bool gemm_tc_supported(const GemmDesc&) { return false; }
-int gemm_tc_launch(const GemmDesc&, cudaStream_t) { return 0; }
+namespace {
+
+constexpr int kThreadsTC = 256;
+constexpr int kBM = 128;
+constexpr int kStages = 2;
+constexpr long kWaitLimit = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major, 128-byte swizzle, 8-row atoms stacked every 1024 bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);        // start address
+  d |= static_cast<uint64_t>(1) << 16;                      // leading byte offset (unused)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;              // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                      // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                      // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A/B format fmt (2 = TF32, 1 = BF16), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                    uint32_t acc) {
+  if constexpr (kBF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ double ld_op(const Operand& o, int k0_log2, long long base, int i,
+                                        int k) {
+  const int k0 = k & ((1 << k0_log2) - 1);
+  const int k1 = k >> k0_log2;
+  return o.p[base + i * o.s_mn + k0 * o.s_k0 + static_cast<long long>(k1) * o.s_k1];
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Split x into head/tail bit patterns of the MMA type.
+template <bool kBF16>
+__device__ __forceinline__ void split(double x, uint32_t& hi, uint32_t& lo) {
+  if constexpr (kBF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(x));
+    const float hf = __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(static_cast<float>(x - static_cast<double>(hf)));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+  } else {
+    hi = tf32_bits(static_cast<float>(x));
+    const float hf = __uint_as_float(hi);
+    lo = tf32_bits(static_cast<float>(x - static_cast<double>(hf)));
+  }
+}
+
+// Byte offset of element (row r, k) in a K-major SWIZZLE_128B tile whose rows
+// are 128 bytes (32 TF32 or 64 BF16 elements).
+template <bool kBF16>
+__device__ __forceinline__ uint32_t swz_off(int r, int k) {
+  const uint32_t byte = kBF16 ? k * 2 : k * 4;
+  const uint32_t chunk = (byte >> 4) ^ (r & 7);
+  return r * 128 + (chunk << 4) + (byte & 15);
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void st_elem(uint8_t* tile, int r, int k, uint32_t bits) {
+  if constexpr (kBF16)
+    *reinterpret_cast<uint16_t*>(tile + swz_off<true>(r, k)) = static_cast<uint16_t>(bits);
+  else
+    *reinterpret_cast<uint32_t*>(tile + swz_off<false>(r, k)) = bits;
+}
+
+// Stage rows [r0, r0 + rows) x K tile [kb, kb + BK) of one operand.
+template <bool kBF16, bool kSplit, int BK>
+__device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, long long base,
+                                              int r0, int rows, int nrows_valid, int kb,
+                                              int Kg, uint8_t* hi_tile, uint8_t* lo_tile) {
+  const bool kfast = (o.s_k0 == 1);
+  const int total = rows * BK;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < total; e += kThreadsTC) {
+    int r, kk;
+    if (kfast) { kk = e % BK; r = e / BK; } else { r = e % rows; kk = e / rows; }
+    const int k = kb + kk;
+    double x = 0.0;
+    if (r < nrows_valid && k < Kg) x = ld_op(o, k0_log2, base, r0 + r, k);
+    uint32_t h, l;
+    split<kBF16>(x, h, l);
+    st_elem<kBF16>(hi_tile, r, kk, h);
+    if constexpr (kSplit) st_elem<kBF16>(lo_tile, r, kk, l);
+  }
+}
+
+struct TCParams {
+  int total_tiles;
+  int* err;
+};
+
+template <bool kBF16, bool kSplit, int BN>
+__global__ void gemm_tc_kernel(const GemmDesc d, TCParams tp);
+
+template <bool kBF16, bool kSplit, int BN>
+constexpr int tc_smem_bytes() {
+  return kStages * (kSplit ? 2 : 1) * (kBM * 128 + BN * 128) + 1024;
+}
+
+template <bool kBF16, bool kSplit, int BN>
+void tc_configure() {
+  cudaFuncSetAttribute(gemm_tc_kernel<kBF16, kSplit, BN>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tc_smem_bytes<kBF16, kSplit, BN>());
+}
+
+template <bool kBF16, bool kSplit, int BN>
+__global__ void __launch_bounds__(kThreadsTC, 1) gemm_tc_kernel(const GemmDesc d, TCParams tp) {
+  constexpr int BK = kBF16 ? 64 : 32;            // one 128-byte swizzle row
+  constexpr int KSTEP = kBF16 ? 16 : 8;          // K of one tcgen05.mma
+  constexpr int kA = kBM * 128;                  // bytes of one A tile (128 rows)
+  constexpr int kB = BN * 128;                   // bytes of one B tile
+  constexpr int kStageBytes = (kSplit ? 2 : 1) * (kA + kB);
+  constexpr uint32_t kIdesc = instr_desc(kBF16 ? 1u : 2u, kBM, BN);
+  constexpr int kCols = BN < 32 ? 32 : BN;       // TMEM columns (power of two >= 32)
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ uint32_t tmem_slot;
+
+  if (d.skip && *d.skip) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (d.N + BN - 1) / BN;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  const int b = blockIdx.y;
+  const int b0 = b % d.B0, b1 = b / d.B0;
+  const int split_id = blockIdx.z;
+  const int m0 = tm * kBM, n0 = tn * BN;
+  const int mvalid = min(kBM, d.M - m0), nvalid = min(BN, d.N - n0);
+  const int t_lo = static_cast<int>(static_cast<long long>(tp.total_tiles) * split_id / d.splits);
+  const int t_hi =
+      static_cast<int>(static_cast<long long>(tp.total_tiles) * (split_id + 1) / d.splits);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  bool ok = true;
+  int issued = 0;   // K tiles whose MMAs were committed
+  int t_global = 0;
+  for (int g = 0; g < d.ngroups && t_global < t_hi && ok; ++g) {
+    const Group& G = d.g[g];
+    const int nt = (G.K + BK - 1) / BK;
+    if (t_global + nt <= t_lo) { t_global += nt; continue; }
+    const long long abase = b0 * G.a.s_b0 + static_cast<long long>(b1) * G.a.s_b1;
+    const long long bbase = b0 * G.b.s_b0 + static_cast<long long>(b1) * G.b.s_b1;
+    const int first = max(0, t_lo - t_global), last = min(nt, t_hi - t_global);
+    for (int t = first; t < last; ++t) {
+      const int stage = issued % kStages;
+      // the MMAs that read this stage (tile issued - kStages) must be done;
+      // the decision to stop is taken by the whole CTA
+      bool w_ok = true;
+      if (issued >= kStages) w_ok = mbar_wait(&bars[stage], ((issued / kStages) - 1) & 1);
+      if (!__syncthreads_and(w_ok)) { ok = false; break; }
+      uint8_t* st = smem + stage * kStageBytes;
+      uint8_t* a_hi = st;
+      uint8_t* b_hi = st + kA;
+      uint8_t* a_lo = st + kA + kB;
+      uint8_t* b_lo = st + 2 * kA + kB;
+      const int kb = t * BK;
+      stage_operand<kBF16, kSplit, BK>(G.a, G.k0_log2, abase, m0, kBM, mvalid, kb, G.K, a_hi, a_lo);
+      stage_operand<kBF16, kSplit, BK>(G.b, G.k0_log2, bbase, n0, BN, nvalid, kb, G.K, b_hi, b_lo);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa_hi = smem_u32(a_hi), sb_hi = smem_u32(b_hi);
+        const uint32_t sa_lo = smem_u32(a_lo), sb_lo = smem_u32(b_lo);
+#pragma unroll
+        for (int j = 0; j < BK / KSTEP; ++j) {
+          const uint32_t off = j * 32;   // 32 bytes of K per instruction
+          const uint32_t acc = (issued > 0 || j > 0) ? 1u : 0u;
+          if constexpr (kSplit) {
+            mma<kBF16>(tmem, smem_desc(sa_lo + off), smem_desc(sb_hi + off), kIdesc, acc);
+            mma<kBF16>(tmem, smem_desc(sa_hi + off), smem_desc(sb_lo + off), kIdesc, 1u);
+            mma<kBF16>(tmem, smem_desc(sa_hi + off), smem_desc(sb_hi + off), kIdesc, 1u);
+          } else {
+            mma<kBF16>(tmem, smem_desc(sa_hi + off), smem_desc(sb_hi + off), kIdesc, acc);
+          }
+        }
+        mma_commit(&bars[stage]);
+      }
+      ++issued;
+    }
+    t_global += nt;
+  }
+  // wait for the last committed stage (MMAs complete in order)
+  bool f_ok = true;
+  if (issued > 0) {
+    const int last = issued - 1;
+    f_ok = mbar_wait(&bars[last % kStages], (last / kStages) & 1);
+  }
+  ok = __syncthreads_and(ok && f_ok);
+  if (!ok && tp.err && threadIdx.x == 0) atomicOr(tp.err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // Epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (rows), columns half w/4.
+  // A split with no K tile contributes zeros (its accumulator was never written).
+  if (ok) {
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int m = m0 + row;
+    constexpr int kHalf = BN >= 32 ? BN / 2 : BN;
+    const int c_begin = (warp >> 2) * kHalf;
+    const bool active = (BN >= 32) || (warp < 4);
+    const long long MN = static_cast<long long>(d.M) * d.N;
+    for (int c0 = c_begin; active && c0 < c_begin + kHalf; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0;
+      if (issued == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = 0u;
+      } else {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      if (m < d.M) {
+        if (d.splits == 1) {
+          double* C = d.C + b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < d.N) {
+              const double v = static_cast<double>(__uint_as_float(r[j]));
+              double* c = C + n * d.sc_n;
+              *c = d.beta == 0.0 ? d.alpha * v : d.alpha * v + d.beta * *c;
+            }
+          }
+        } else {
+          double* P = d.partial + (static_cast<long long>(split_id) * d.B0 * d.B1 + b) * MN +
+                      static_cast<long long>(m) * d.N;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < d.N) P[n] = static_cast<double>(__uint_as_float(r[j]));
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+__global__ void splitk_reduce_tc(const GemmDesc d) {
+  if (d.skip && *d.skip) return;
+  const long long MN = static_cast<long long>(d.M) * d.N;
+  const long long total = MN * d.B0 * d.B1;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = e / MN, r = e % MN;
+    const int m = static_cast<int>(r / d.N), n = static_cast<int>(r % d.N);
+    double s = 0.0;
+    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
+    const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
+    double* c = d.C + b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
+    *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
+  }
+}
+
+int tc_bn(int N) { return N >= 128 ? 128 : N >= 64 ? 64 : 32; }
+
+int tc_total_tiles(const GemmDesc& d, int BK) {
+  int t = 0;
+  for (int g = 0; g < d.ngroups; ++g) t += (d.g[g].K + BK - 1) / BK;
+  return t;
+}
+
+template <bool kBF16, bool kSplit, int BN>
+int launch_tc(const GemmDesc& d, cudaStream_t s, int* err) {
+  constexpr int BK = kBF16 ? 64 : 32;
+  const int smem = tc_smem_bytes<kBF16, kSplit, BN>();
+  const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
+  dim3 grid(tiles, d.B0 * d.B1, d.splits);
+  TCParams tp{tc_total_tiles(d, BK), err};
+  gemm_tc_kernel<kBF16, kSplit, BN><<<grid, kThreadsTC, smem, s>>>(d, tp);
+  return 1;
+}
+
+template <bool kBF16, bool kSplit>
+int launch_tc_bn(const GemmDesc& d, cudaStream_t s, int* err) {
+  switch (tc_bn(d.N)) {
+    case 128: return launch_tc<kBF16, kSplit, 128>(d, s, err);
+    case 64: return launch_tc<kBF16, kSplit, 64>(d, s, err);
+    default: return launch_tc<kBF16, kSplit, 32>(d, s, err);
+  }
+}
+
+}  // namespace
+
+void gemm_tc_init() {
+  tc_configure<false, false, 32>(); tc_configure<false, false, 64>(); tc_configure<false, false, 128>();
+  tc_configure<false, true, 32>(); tc_configure<false, true, 64>(); tc_configure<false, true, 128>();
+  tc_configure<true, false, 32>(); tc_configure<true, false, 64>(); tc_configure<true, false, 128>();
+  tc_configure<true, true, 32>(); tc_configure<true, true, 64>(); tc_configure<true, true, 128>();
+}
+
+bool gemm_tc_supported(const GemmDesc& d) {
+  if (d.prec == 0) return false;
+  if (d.M < 64 || d.N < 32) return false;
+  long long k = 0;
+  for (int g = 0; g < d.ngroups; ++g) k += d.g[g].K;
+  return k >= 32;
+}
+
+int tc_pick_splits(const GemmDesc& d) {
+  const int BK = (d.prec == 3 || d.prec == 4) ? 64 : 32;
+  const long long base = static_cast<long long>((d.M + kBM - 1) / kBM) *
+                         ((d.N + tc_bn(d.N) - 1) / tc_bn(d.N)) * d.B0 * d.B1;
+  const int kt = tc_total_tiles(d, BK);
+  if (base >= 148 || kt < 8) return 1;
+  int s = static_cast<int>(std::min<long long>((148 + base - 1) / base, kt / 4));
+  return std::max(1, std::min(s, 64));
+}
+
+int gemm_tc_launch(const GemmDesc& d, cudaStream_t s) {
+  int n = 0;
+  switch (d.prec) {
+    case 1: n = launch_tc_bn<false, false>(d, s, d.err); break;
+    case 2: n = launch_tc_bn<false, true>(d, s, d.err); break;
+    case 3: n = launch_tc_bn<true, false>(d, s, d.err); break;
+    default: n = launch_tc_bn<true, true>(d, s, d.err); break;
+  }
+  if (d.splits > 1) {
+    const long long total = static_cast<long long>(d.M) * d.N * d.B0 * d.B1;
+    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 4096));
+    splitk_reduce_tc<<<blocks, 256, 0, s>>>(d);
+    ++n;
+  }
+  return n;
+}
 
 }  // namespace ttn

@@ -1,0 +1,169 @@
+// Diagnostic entry point: the tensor-core engine against the FP64 engine on
+// seeded random operands, over the operand layouts the sweep uses (K-major,
+// M/N-major, two-level K, two-level batch, ragged edges, split K, alpha/beta).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ttn.h"
+#include "common.h"
+
+namespace ttn {
+namespace {
+
+__global__ void fill_uniform(double* x, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;   // splitmix64 -> [-1, 1)
+  }
+}
+
+__global__ void max_abs_diff(const double* a, const double* b, long long n, double* out) {
+  __shared__ double sd[256], sm[256];
+  double d = 0.0, m = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    d = fmax(d, fabs(a[i] - b[i]));
+    m = fmax(m, fabs(b[i]));
+  }
+  sd[threadIdx.x] = d;
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = sd[0]; out[1] = sm[0]; }
+}
+
+Operand mk(const double* p, long long mn, long long k0, long long k1 = 0, long long b0 = 0,
+           long long b1 = 0) {
+  Operand o;
+  o.p = p; o.s_mn = mn; o.s_k0 = k0; o.s_k1 = k1; o.s_b0 = b0; o.s_b1 = b1;
+  return o;
+}
+
+int lg(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
+
+}  // namespace
+}  // namespace ttn
+
+using namespace ttn;
+
+extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out,
+                                 void* stream) {
+  if (!d_ws || !out_rel || n_out < 6 || prec < 1 || prec > 4) return TTN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  gemm_tc_init();
+  double* base = reinterpret_cast<double*>(d_ws);
+  const size_t cap = bytes / sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t n) -> double* {
+    off = (off + 31) & ~size_t(31);
+    double* p = base + off;
+    off += n;
+    return p;
+  };
+  struct Case { GemmDesc d; long long c_elems; };
+  std::vector<Case> cases;
+  const size_t big = 16384 * 128;
+  double* A = take(4 * big);
+  double* B = take(4 * big);
+  double* C1 = take(big);
+  double* C2 = take(big);
+  double* partial = take(64 * big / 4);
+  double* res = take(4);
+  int* err = reinterpret_cast<int*>(take(1));
+  if (off > cap) return TTN_ENOMEM;
+  fill_uniform<<<592, 256, 0, s>>>(A, 4 * big, 11);
+  fill_uniform<<<592, 256, 0, s>>>(B, 4 * big, 23);
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+
+  auto base_desc = [&](int M, int N, int B0, int B1, long long sm, long long sn, long long sb0,
+                       long long sb1) {
+    GemmDesc d;
+    memset(&d, 0, sizeof(d));
+    d.M = M; d.N = N; d.B0 = B0; d.B1 = B1;
+    d.sc_m = sm; d.sc_n = sn; d.sc_b0 = sb0; d.sc_b1 = sb1;
+    d.alpha = 1.0; d.beta = 0.0; d.splits = 1; d.err = err;
+    return d;
+  };
+  auto group = [&](Operand a, Operand b, int K0, int K1) {
+    Group g; g.a = a; g.b = b; g.K = K0 * K1; g.k0_log2 = lg(K0); return g;
+  };
+  {  // 1: A K-major, B N-major, M=256 N=128 K=256
+    GemmDesc d = base_desc(256, 128, 1, 1, 128, 1, 0, 0);
+    d.g[d.ngroups++] = group(mk(A, 256, 1), mk(B, 1, 128), 256, 1);
+    cases.push_back({d, 256 * 128});
+  }
+  {  // 2: A M-major, B K-major, ragged K = 96
+    GemmDesc d = base_desc(128, 64, 1, 1, 64, 1, 0, 0);
+    d.g[d.ngroups++] = group(mk(A, 1, 128), mk(B, 96, 1), 32, 3);
+    cases.push_back({d, 128 * 64});
+  }
+  {  // 3: ragged M = 200, N = 48, K = 40 (two groups of K 32 + 8)
+    GemmDesc d = base_desc(200, 48, 1, 1, 48, 1, 0, 0);
+    d.g[d.ngroups++] = group(mk(A, 32, 1), mk(B, 1, 48), 32, 1);
+    d.g[d.ngroups++] = group(mk(A + 8192, 1, 200), mk(B + 8192, 8, 1), 8, 1);
+    cases.push_back({d, 200 * 48});
+  }
+  {  // 4: long K = 16384 (split K), both K-major
+    GemmDesc d = base_desc(128, 128, 1, 1, 128, 1, 0, 0);
+    d.g[d.ngroups++] = group(mk(A, 16384, 1), mk(B, 16384, 1), 16384, 1);
+    cases.push_back({d, 128 * 128});
+  }
+  {  // 5: two-level K (K0=16, K1=8) and two-level batch (B0=4, B1=3), two groups
+    GemmDesc d = base_desc(128, 64, 4, 3, 64, 1, 128 * 64, 4 * 128 * 64);
+    d.g[d.ngroups++] = group(mk(A, 16, 1, 4096, 128 * 16 * 8, 4 * 128 * 16 * 8),
+                             mk(B, 1, 64, 8 * 64 * 16 / 8 * 8, 16 * 64 * 8, 0), 16, 8);
+    d.g[d.ngroups++] = group(mk(A + 65536, 1, 128, 0, 0, 128 * 64),
+                             mk(B + 65536, 64, 1, 0, 4096, 0), 64, 1);
+    cases.push_back({d, 12 * 128 * 64});
+  }
+  {  // 6: alpha / beta, N = 256 (two BN=128 tiles), batch of 128 left products
+    GemmDesc d = base_desc(128, 128, 128, 1, 128, 1, 128 * 128, 0);
+    d.alpha = 2.0; d.beta = 0.5;
+    d.g[d.ngroups++] = group(mk(A, 1, 128, 0, 0, 0), mk(B, 1, 128, 0, 128 * 128, 0), 128, 1);
+    cases.push_back({d, 128 * 128 * 128});
+  }
+  const int nc = std::min<int>((int)cases.size(), n_out);
+  std::vector<double> host(2);
+  for (int i = 0; i < nc; ++i) {
+    GemmDesc d = cases[i].d;
+    d.partial = partial;
+    if (d.beta != 0.0) {
+      fill_uniform<<<592, 256, 0, s>>>(C1, cases[i].c_elems, 77);
+      fill_uniform<<<592, 256, 0, s>>>(C2, cases[i].c_elems, 77);
+    }
+    GemmDesc r = d;
+    r.prec = 0;
+    r.splits = gemm_pick_splits(r);
+    r.C = C1;
+    gemm_launch(r, s);
+    GemmDesc t = d;
+    t.prec = prec;
+    t.splits = gemm_pick_splits(t);
+    t.C = C2;
+    gemm_launch(t, s);
+    max_abs_diff<<<1, 256, 0, s>>>(C2, C1, cases[i].c_elems, res);
+    cudaMemcpyAsync(host.data(), res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TTN_ECUDA;
+    out_rel[i] = host[0] / std::max(host[1], 1e-300);
+  }
+  int e = 0;
+  cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return TTN_ETIMEOUT;
+  return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ECUDA;
+}
+
+extern "C" size_t ttn_selftest_bytes(void) {
+  const size_t big = 16384 * 128;
+  return (4 * big * 2 + 2 * big + 64 * big / 4 + 64) * sizeof(double) + 4096;
+}

@@ -203,6 +203,7 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
   if (d.ngroups > kMaxGroups) return;
   d.splits = s;
   d.partial = h->partial;
+  d.err = h->iflags + 4;
   if (h->profiling) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -526,17 +527,17 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // F <- Pm F ; T <- A Pm ; A <- Pm T
       GemmDesc a = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
       add(a, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pF, 1, P, 0, 0, PP), P));
-      run(h, a, 0);
+      run(h, a, prec);
       if (!h->measuring) {
         cudaMemcpyAsync(h->pF, h->pT, NJ * PP * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
       }
       if (j + 1 < blk.steps.size()) {
         GemmDesc b = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
         add(b, grp(op(h->pA, P, 1, 0, 0, PP), op(h->pP, 1, P, 0, 0, PP), P));
-        run(h, b, 0);
+        run(h, b, prec);
         GemmDesc c = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
         add(c, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pT, 1, P, 0, 0, PP), P));
-        run(h, c, 0);
+        run(h, c, prec);
         if (!h->measuring) h->launches += symmetrize(h->pA, P, NJ, h->stream);
       }
     }
@@ -834,7 +835,9 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
   real.base = reinterpret_cast<char*>(d_ws);
   layout(h, real);
   h->user = reinterpret_cast<cudaStream_t>(stream);
+  gemm_tc_init();
   rc = check_cuda(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = check_cuda(h, cudaMemsetAsync(h->iflags, 0, 8 * sizeof(int), h->stream), "flags");
   if (rc) { *out = h; return rc; }
   // upload operators of site layer 0 (shifted one-site term)
   for (Instance& I : h->inst) {
@@ -980,6 +983,13 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
   cudaEventDestroy(ev);
   rc = check_cuda(h, cudaGetLastError(), "sweep");
   if (rc) return rc;
+  if (host_energy) {
+    int flag = 0;
+    cudaMemcpyAsync(&flag, h->iflags + 4, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    rc = check_cuda(h, cudaStreamSynchronize(h->stream), "flag sync");
+    if (rc) return rc;
+    if (flag) return fail(h, TTN_ETIMEOUT, "a bounded wait in a tensor-core kernel expired");
+  }
   if (host_energy)
     for (int i = 0; i < n_sweeps * ni; ++i)
       if (!std::isfinite(host_energy[i])) return fail(h, TTN_ENAN, "non-finite energy");
