@@ -119,6 +119,14 @@ int ttn_get_isometries(ttn_t h, int inst, double* host_w_all, double* host_v);
  * solve, shift restored. */
 int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy);
 
+/* Operators of site layer `site_layer` ascended through the current
+ * isometries (Fig. 3 pushed upward: o' = W[o(x)I + I(x)o + sum_k A_k(x)B_k]W^T,
+ * A'_k = W(I(x)A_k)W^T, B'_k = W(B_k(x)I)W^T), computed with the products in
+ * precision `prec`, copied to host as [site][1+2K][chi_t][chi_t] (o, A_k, B_k;
+ * one site when the tree is translation invariant).  The one-site term
+ * includes the bond shift. */
+int ttn_ascend(ttn_t h, int inst, int site_layer, int prec, double* host_out);
+
 /* Energy <psi|H|psi> of one instance's current tensors, in FP64 (ascend and
  * top contraction, no re-optimisation). */
 int ttn_energy(ttn_t h, int inst, double* E_total);
@@ -149,10 +157,10 @@ long long ttn_launch_count(ttn_t h);
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
- * operands over six operand layouts (K-major / M-major, two-level K and batch,
+ * operands over nine operand layouts (K-major / M-major, two-level K and batch,
  * ragged edges, split K, alpha/beta).  d_ws: caller device memory of at least
  * ttn_selftest_bytes(); prec: 1..4 (ttn_precision); out_rel[i] receives
- * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 6). */
+ * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 9). */
 size_t ttn_selftest_bytes(void);
 int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out, void* stream);
 

@@ -135,6 +135,17 @@ class Sweeper:
         self._check(self.lib.ttn_energy(self.h, inst, ctypes.byref(E)), "energy")
         return E.value
 
+    def ascend(self, inst, site_layer, prec=None):
+        """Operators of a site layer ascended through the current isometries:
+        array [site][1+2K][chi][chi] holding (o - c I, A_k, B_k) coarse-grained."""
+        p = self.opt.prec if prec is None else (PRECISIONS[prec] if isinstance(prec, str) else prec)
+        chis = self.chis(inst)
+        K = self.models[inst].A.shape[0]
+        S = (self.models[inst].Lx >> site_layer) if self.per_node else 1
+        out = np.empty((S, 1 + 2 * K, chis[site_layer], chis[site_layer]))
+        self._check(self.lib.ttn_ascend(self.h, inst, site_layer, p, _ptr(out)), "ascend")
+        return out
+
     def rdm(self, inst, site_layer, which=0):
         n = self.chis(inst)[site_layer]
         out = np.empty((n, n))

@@ -41,6 +41,7 @@ SIGNATURES = {
     "ttn_get_isometries": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
     "ttn_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
     "ttn_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "ttn_ascend": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "ttn_rdm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "ttn_env": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "ttn_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),

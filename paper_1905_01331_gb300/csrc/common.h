@@ -88,6 +88,19 @@ int symmetrize(double* A, int P, int nb, cudaStream_t s);
 int ordered_sum(const double* x, int count, double* out, double scale, double add,
                 cudaStream_t s);
 
+// Identity bookkeeping of the one-site operators (exact FP64 scalars):
+// for node J (P x P block at O + J*stride): tr = trace/P, O -= tr I,
+// e_out[J] = e_in[left] + e_in[right] + tr, where left/right = 2J, 2J+1 when
+// per_node, else both 0.
+int split_identity(double* O, long long stride, int P, int nodes, const double* e_in,
+                   int per_node, double* e_out, cudaStream_t s);
+// Z_J += coef * (e_in[left] + e_in[right]) * W_J for each node J (elems each).
+int add_identity_part(double* Z, const double* W, long long elems, int nodes, const double* e_in,
+                      int per_node, double coef, cudaStream_t s);
+// *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add.
+int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
+                   cudaStream_t s);
+
 // NaN/Inf scan: flag[0] |= 1 if any element is not finite.
 int finite_check(const double* x, long long n, int* flag, cudaStream_t s);
 

@@ -148,7 +148,8 @@ __global__ void lz_step_scalars(const double* c1, const double* c2, int j, doubl
   const double b = sqrt(fmax(nrm2[0], 0.0));
   beta[j] = b;
   *tdim = j + 1;
-  if (!(b > 1e-12 * fmax(fabs(a), 1e-300))) { beta[j] = 0.0; *skip = 1; }
+  const double scale = fabs(a) + (j > 0 ? beta[j - 1] : 0.0);
+  if (!(b > 1e-12 * fmax(scale, 1e-300))) { beta[j] = 0.0; *skip = 1; }
 }
 
 __global__ void lz_scale_into(double* dst, const double* w, long long n, const double* beta, int j,
@@ -291,6 +292,41 @@ __global__ void finite_kernel(const double* x, long long n, int* flag) {
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+__global__ void split_identity_kernel(double* O, long long stride, int P, const double* e_in,
+                                      int per_node, double* e_out) {
+  const int J = blockIdx.x;
+  double* o = O + J * stride;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s += o[(long long)i * P + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double tr = sh[0] / P;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) o[(long long)i * P + i] -= tr;
+  if (threadIdx.x == 0) {
+    const double el = e_in[per_node ? 2 * J : 0], er = e_in[per_node ? 2 * J + 1 : 0];
+    e_out[J] = el + er + tr;
+  }
+}
+
+__global__ void add_identity_kernel(double* Z, const double* W, long long elems, const double* e_in,
+                                    int per_node, double coef) {
+  const int J = blockIdx.y;
+  const double c = coef * (e_in[per_node ? 2 * J : 0] + e_in[per_node ? 2 * J + 1 : 0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
+       i += (long long)gridDim.x * blockDim.x)
+    Z[J * elems + i] += c * W[J * elems + i];
+}
+
+__global__ void top_energy_kernel(const double* dot, const double* e, int per_node, double add,
+                                  double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add;
+}
+
 int grid_for(long long n, int per = 256, int cap = 1184) {
   long long g = (n + per - 1) / per;
   if (g < 1) g = 1;
@@ -397,6 +433,25 @@ int align_sign(double* v, const double* vprev, long long n, double* scratch, dou
 int ordered_sum(const double* x, int count, double* out, double scale, double add,
                 cudaStream_t s) {
   ordered_sum_kernel<<<1, 32, 0, s>>>(x, count, out, scale, add);
+  return 1;
+}
+
+int split_identity(double* O, long long stride, int P, int nodes, const double* e_in,
+                   int per_node, double* e_out, cudaStream_t s) {
+  split_identity_kernel<<<nodes, 256, 0, s>>>(O, stride, P, e_in, per_node, e_out);
+  return 1;
+}
+
+int add_identity_part(double* Z, const double* W, long long elems, int nodes, const double* e_in,
+                      int per_node, double coef, cudaStream_t s) {
+  add_identity_kernel<<<dim3(grid_for(elems, 256, 512), nodes), 256, 0, s>>>(Z, W, elems, e_in,
+                                                                              per_node, coef);
+  return 1;
+}
+
+int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
+                   cudaStream_t s) {
+  top_energy_kernel<<<1, 32, 0, s>>>(dot, e, per_node, add, out);
   return 1;
 }
 

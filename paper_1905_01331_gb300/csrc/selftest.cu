@@ -59,7 +59,7 @@ using namespace ttn;
 
 extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out,
                                  void* stream) {
-  if (!d_ws || !out_rel || n_out < 6 || prec < 1 || prec > 4) return TTN_EINVAL;
+  if (!d_ws || !out_rel || n_out < 9 || prec < 1 || prec > 4) return TTN_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   gemm_tc_init();
   double* base = reinterpret_cast<double*>(d_ws);
@@ -132,6 +132,24 @@ extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out
     d.alpha = 2.0; d.beta = 0.5;
     d.g[d.ngroups++] = group(mk(A, 1, 128, 0, 0, 0), mk(B, 1, 128, 0, 128 * 128, 0), 128, 1);
     cases.push_back({d, 128 * 128 * 128});
+  }
+  {  // 7: M = 64 (half tile), N = 64, K = 4096, batch 3 with A batch stride (a close)
+    GemmDesc d = base_desc(64, 64, 3, 1, 64, 1, 64 * 64, 0);
+    d.g[d.ngroups++] = group(mk(A, 4096, 1, 0, 262144, 0), mk(B, 4096, 1, 0, 0, 0), 4096, 1);
+    cases.push_back({d, 3 * 64 * 64});
+  }
+  {  // 8: left products batched over p (B0 = 64), M = N = K = 64, four groups, A shared
+    GemmDesc d = base_desc(64, 64, 64, 1, 64, 1, 4096, 0);
+    d.g[d.ngroups++] = group(mk(A, 1, 64), mk(B, 1, 64, 0, 4096, 0), 64, 1);
+    d.g[d.ngroups++] = group(mk(B, 64, 1, 0, 4096, 0), mk(A + 4096, 1, 64), 64, 1);
+    d.g[d.ngroups++] = group(mk(A + 8192, 1, 64), mk(B + 262144, 1, 64, 0, 4096, 0), 64, 1);
+    d.g[d.ngroups++] = group(mk(A + 12288, 64, 1), mk(B + 524288, 1, 64, 0, 4096, 0), 64, 1);
+    cases.push_back({d, 64 * 64 * 64});
+  }
+  {  // 9: right product M = 4096, N = 64, K = 64 (B = small operator, N-major)
+    GemmDesc d = base_desc(4096, 64, 1, 1, 64, 1, 0, 0);
+    d.g[d.ngroups++] = group(mk(A, 64, 1), mk(B, 1, 64), 64, 1);
+    cases.push_back({d, 4096 * 64});
   }
   const int nc = std::min<int>((int)cases.size(), n_out);
   std::vector<double> host(2);

@@ -73,6 +73,9 @@ struct Instance {
   double* V = nullptr;
   double* Vprev = nullptr;
   double* E = nullptr;               // energy of the last top solve
+  // Identity part of the one-site operators, kept exactly in FP64: the true
+  // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
+  std::vector<double*> eoff;
   int sites(int t) const { return per_node ? (L >> t) : 1; }
   int nodes(int t) const { return per_node ? (L >> (t + 1)) : 1; }
   size_t w_elems(int t) const {
@@ -322,6 +325,10 @@ void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
                     I.per_node ? out_site : 0);
   add(d, grp(op(h->Y, v.n2, 1, 0, slab, v.Pn2), op(W, v.n2, 1, 0, 0, v.Pn2), (int)v.n2));
   run(h, d, prec);
+  // identity part: e'_J = e_L + e_R + tr(o'_J)/P, o'_J -= tr/P I
+  if (!h->measuring)
+    h->launches += split_identity(I.ops[t + 1], I.per_node ? out_site : 0, v.P, v.NJ, I.eoff[t],
+                                  I.per_node ? 1 : 0, I.eoff[t + 1], h->stream);
 }
 
 // Top Hamiltonian on x (c x c): w = o_0 x + x o_1^T + sum_k (A_k0 x B_k1^T + B_k0 x A_k1^T)
@@ -387,7 +394,8 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
   // energy = <V, H V> + c L
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
-  h->launches += ordered_sum(h->scal + 4, 1, energy_out, 1.0, I.c * I.L, h->stream);
+  h->launches += top_energy_sum(h->scal + 4, I.eoff[I.T], I.per_node ? 1 : 0, I.c * I.L,
+                                energy_out, h->stream);
 }
 
 void energy_only(ttn_ctx* h, Instance& I, double* energy_out) {
@@ -395,7 +403,8 @@ void energy_only(ttn_ctx* h, Instance& I, double* energy_out) {
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   if (h->measuring) return;
   h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
-  h->launches += ordered_sum(h->scal + 4, 1, energy_out, 1.0, I.c * I.L, h->stream);
+  h->launches += top_energy_sum(h->scal + 4, I.eoff[I.T], I.per_node ? 1 : 0, I.c * I.L,
+                                energy_out, h->stream);
 }
 
 // Top adjoints: R = V V^T + V^T V, P_k = V B_k V^T + V^T B_k V, Q_k = V^T A_k V + V A_k V^T
@@ -469,6 +478,10 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
       add(d, grp(op(Ak, 1, v.n, 0, 0, v.node_ss), op(U + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
     }
     run(h, d, prec);
+    // identity parts of o_L and o_R: W (e I (x) I + I (x) e I) = (e_L + e_R) W, twice (S + S^T)
+    if (!h->measuring)
+      h->launches += add_identity_part(Zs, W, v.Pn2, v.NJ, I.eoff[t], I.per_node ? 1 : 0, 2.0,
+                                       h->stream);
   }
   // one-leg products: slabs 1.. of Y: WAt_k, WA_k, BW_k, BtW_k
   double* WAt = h->Y + slab;
@@ -667,9 +680,11 @@ void layout(ttn_ctx* h, Arena& ar) {
       pp_max = std::max(pp_max, (size_t)I.nodes(t) * I.chis[t + 1] * I.chis[t + 1]);
       nj_max = std::max(nj_max, (size_t)I.nodes(t));
     }
+    I.eoff.assign(I.T + 1, nullptr);
     for (int t = 0; t <= I.T; ++t) {
       I.ops[t] = ar.take(I.op_elems(t));
       I.adj[t] = ar.take(I.op_elems(t));
+      I.eoff[t] = ar.take(I.sites(t));
     }
     const int c = I.chis[I.T];
     I.V = ar.take((size_t)c * c);
@@ -844,7 +859,14 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
     const size_t d2 = (size_t)I.d0 * I.d0;
     std::vector<double> host((size_t)(1 + 2 * I.K) * d2);
     for (size_t e = 0; e < d2; ++e) host[e] = I.o[e];
-    for (int i = 0; i < I.d0; ++i) host[(size_t)i * I.d0 + i] -= I.c;
+    double tr = 0.0;
+    for (int i = 0; i < I.d0; ++i) tr += I.o[(size_t)i * I.d0 + i];
+    const double e0 = tr / I.d0 - I.c;   // o - c I = (o - tr/d0 I) + e0 I
+    for (int i = 0; i < I.d0; ++i) host[(size_t)i * I.d0 + i] -= tr / I.d0;
+    std::vector<double> e0s(I.sites(0), e0);
+    rc = check_cuda(h, cudaMemcpyAsync(I.eoff[0], e0s.data(), e0s.size() * sizeof(double),
+                                       cudaMemcpyHostToDevice, h->stream), "upload");
+    if (rc) { *out = h; return rc; }
     std::memcpy(host.data() + d2, I.A.data(), I.K * d2 * sizeof(double));
     std::memcpy(host.data() + (1 + I.K) * d2, I.B.data(), I.K * d2 * sizeof(double));
     for (int s = 0; s < I.sites(0); ++s) {
@@ -993,6 +1015,28 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
   if (host_energy)
     for (int i = 0; i < n_sweeps * ni; ++i)
       if (!std::isfinite(host_energy[i])) return fail(h, TTN_ENAN, "non-finite energy");
+  return TTN_OK;
+}
+
+int ttn_ascend(ttn_t h, int inst, int site_layer, int prec, double* host_out) {
+  if (!h || !host_out || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  Instance& I = h->inst[inst];
+  if (site_layer < 0 || site_layer > I.T || prec < 0 || prec > 4) return fail(h, TTN_EINVAL, "bad layer");
+  sync_user(h);
+  for (int t = 0; t < site_layer; ++t) ascend_layer(h, I, t, prec);
+  std::vector<double> e(I.sites(site_layer));
+  int rc = check_cuda(h, cudaMemcpyAsync(host_out, I.ops[site_layer], I.op_elems(site_layer) * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream), "ascend");
+  if (rc) return rc;
+  rc = check_cuda(h, cudaMemcpyAsync(e.data(), I.eoff[site_layer], e.size() * sizeof(double),
+                                     cudaMemcpyDeviceToHost, h->stream), "ascend");
+  if (rc) return rc;
+  rc = check_cuda(h, cudaStreamSynchronize(h->stream), "ascend sync");
+  if (rc) return rc;
+  const int n = I.chis[site_layer];
+  const size_t ss = (size_t)(1 + 2 * I.K) * n * n;
+  for (size_t j = 0; j < e.size(); ++j)
+    for (int i = 0; i < n; ++i) host_out[j * ss + (size_t)i * n + i] += e[j];
   return TTN_OK;
 }
 
