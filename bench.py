@@ -172,7 +172,7 @@ def run_gpu(args):
     import torch
 
     import ttn_inputs as ti
-    from oracle import flops as oracle_flops
+    from paper_1905_01331_gb300 import flops as ttn_flops
     from paper_1905_01331_gb300 import Sweeper, _abi
 
     rank, world, local = dist_env()
@@ -192,7 +192,7 @@ def run_gpu(args):
     s = Sweeper(model, chi, prec=args.prec)
     s.set_isometries(0, ws, V)
     chis = s.chis(0)
-    flops_per_sweep = oracle_flops.sweep_flops(1024, chis, 1, symmetric=True)
+    flops_per_sweep = ttn_flops.sweep_flops(1024, chis, 1, symmetric=True)
 
     # warm-up (also builds the CUDA graph)
     s.sweep(args.warmup)

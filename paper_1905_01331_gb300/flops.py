@@ -1,4 +1,4 @@
-"""Algorithmic floating-point work of one TTN sweep (test infrastructure).
+"""Algorithmic floating-point work of one TTN sweep.
 
 Counts 2*m*n*k for every matrix product the method needs (Sec. III.A: each
 environment contribution reduces to products of cost at most O(chi^4); Sec. V:

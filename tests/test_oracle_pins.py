@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 
 import ttn_inputs as ti
-from oracle import ed, flops, ttn
+from oracle import ed, ttn
+from paper_1905_01331_gb300 import flops
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
