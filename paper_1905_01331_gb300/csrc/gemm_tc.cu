@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kThreadsTC = 256;
 constexpr int kBM = 128;
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr long kWaitLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -137,24 +137,113 @@ __device__ __forceinline__ void st_elem(uint8_t* tile, int r, int k, uint32_t bi
     *reinterpret_cast<uint32_t*>(tile + swz_off<false>(r, k)) = bits;
 }
 
-// Stage rows [r0, r0 + rows) x K tile [kb, kb + BK) of one operand.
-template <bool kBF16, bool kSplit, int BK>
+// Store 4 (TF32) or 8 (BF16) consecutive K values of row r, starting at a
+// 16-byte chunk boundary kk, as one 16-byte swizzled chunk.
+template <bool kBF16>
+__device__ __forceinline__ void st_chunk(uint8_t* tile, int r, int kk, const uint32_t* v) {
+  uint4 q;
+  if constexpr (kBF16) {
+    q.x = v[0] | (v[1] << 16); q.y = v[2] | (v[3] << 16);
+    q.z = v[4] | (v[5] << 16); q.w = v[6] | (v[7] << 16);
+  } else {
+    q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3];
+  }
+  *reinterpret_cast<uint4*>(tile + swz_off<kBF16>(r, kk)) = q;
+}
+
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    a = t.x; b = t.y;
+  } else {
+    a = p[0]; b = p[1];
+  }
+}
+
+// Stage rows [r0, r0 + ROWS) x K tile [kb, kb + BK) of one operand.  Fast
+// paths when the tile lies inside one K0 slice and the source is K-major
+// (s_k0 == 1: 16-byte loads along K) or MN-major (s_mn == 1: 16-byte loads
+// along rows, transposed in registers); otherwise element by element.
+template <bool kBF16, bool kSplit, int BK, int ROWS>
 __device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, long long base,
-                                              int r0, int rows, int nrows_valid, int kb,
-                                              int Kg, uint8_t* hi_tile, uint8_t* lo_tile) {
+                                              int r0, int nrows_valid, int kb, int Kg,
+                                              uint8_t* hi_tile, uint8_t* lo_tile) {
+  constexpr int CH = kBF16 ? 8 : 4;           // K values per 16-byte chunk
+  constexpr int NCH = BK / CH;                // chunks per row (8)
+  const int K0 = 1 << k0_log2;
+  const int kvalid = min(BK, Kg - kb);
+  const bool slice = (K0 >= BK) && (kvalid == BK);
+  if (slice && o.s_k0 == 1) {
+    const double* tb = o.p + base + static_cast<long long>(kb >> k0_log2) * o.s_k1 +
+                       (kb & (K0 - 1));
+    for (int task = threadIdx.x; task < ROWS * NCH; task += kThreadsTC) {
+      const int r = task / NCH, c = task % NCH;
+      uint32_t h[CH], l[CH];
+      if (r < nrows_valid) {
+        const double* src = tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH;
+#pragma unroll
+        for (int q = 0; q < CH; q += 2) {
+          double a, b;
+          ld2(src + q, a, b);
+          split<kBF16>(a, h[q], l[q]);
+          split<kBF16>(b, h[q + 1], l[q + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) { h[q] = 0u; l[q] = 0u; }
+      }
+      st_chunk<kBF16>(hi_tile, r, c * CH, h);
+      if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r, c * CH, l);
+    }
+    return;
+  }
+  if (slice && o.s_mn == 1 && (nrows_valid & 3) == 0) {
+    const double* tb = o.p + base + static_cast<long long>(kb >> k0_log2) * o.s_k1 +
+                       static_cast<long long>(kb & (K0 - 1)) * o.s_k0;
+    // task: 4 consecutive rows x one chunk of CH consecutive K values
+    for (int task = threadIdx.x; task < (ROWS / 4) * NCH; task += kThreadsTC) {
+      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int r = rq * 4;
+      uint32_t h[4][CH], l[4][CH];
+      if (r < nrows_valid) {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          const double* src = tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r);
+          double v0, v1, v2, v3;
+          ld2(src, v0, v1);
+          ld2(src + 2, v2, v3);
+          split<kBF16>(v0, h[0][q], l[0][q]);
+          split<kBF16>(v1, h[1][q], l[1][q]);
+          split<kBF16>(v2, h[2][q], l[2][q]);
+          split<kBF16>(v3, h[3][q], l[3][q]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < CH; ++q) { h[i][q] = 0u; l[i][q] = 0u; }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        st_chunk<kBF16>(hi_tile, r + i, c * CH, h[i]);
+        if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r + i, c * CH, l[i]);
+      }
+    }
+    return;
+  }
   const bool kfast = (o.s_k0 == 1);
-  const int total = rows * BK;
+  constexpr int total = ROWS * BK;
 #pragma unroll 4
   for (int e = threadIdx.x; e < total; e += kThreadsTC) {
     int r, kk;
-    if (kfast) { kk = e % BK; r = e / BK; } else { r = e % rows; kk = e / rows; }
+    if (kfast) { kk = e % BK; r = e / BK; } else { r = e % ROWS; kk = e / ROWS; }
     const int k = kb + kk;
     double x = 0.0;
     if (r < nrows_valid && k < Kg) x = ld_op(o, k0_log2, base, r0 + r, k);
-    uint32_t h, l;
-    split<kBF16>(x, h, l);
-    st_elem<kBF16>(hi_tile, r, kk, h);
-    if constexpr (kSplit) st_elem<kBF16>(lo_tile, r, kk, l);
+    uint32_t hh, ll;
+    split<kBF16>(x, hh, ll);
+    st_elem<kBF16>(hi_tile, r, kk, hh);
+    if constexpr (kSplit) st_elem<kBF16>(lo_tile, r, kk, ll);
   }
 }
 
@@ -248,8 +337,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_tc_kernel(const GemmDesc d
       uint8_t* a_lo = st + kA + kB;
       uint8_t* b_lo = st + 2 * kA + kB;
       const int kb = t * BK;
-      stage_operand<kBF16, kSplit, BK>(G.a, G.k0_log2, abase, m0, kBM, mvalid, kb, G.K, a_hi, a_lo);
-      stage_operand<kBF16, kSplit, BK>(G.b, G.k0_log2, bbase, n0, BN, nvalid, kb, G.K, b_hi, b_lo);
+      stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, a_hi, a_lo);
+      stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, b_hi, b_lo);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (threadIdx.x == 0) {

@@ -523,12 +523,16 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += batched_dot(Gam, W, PN, PN, NJ, gw, h->red, h->stream);
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream);
   }
+  // FP64 mode: every product FP64, short blocks.  Mixed modes: the Gram
+  // matrices and the P x P polynomial are FP64 (the small singular directions
+  // must not drown in tensor-core rounding), only X <- F X runs on the tensor
+  // cores, followed by one FP64 Newton-Schulz polish of the isometry.
   const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
   for (const PolarBlock& blk : sched) {
     // A = X X^T
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
     add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
-    run(h, g, prec);
+    run(h, g, 0);
     if (!h->measuring) {
       h->launches += symmetrize(h->pA, P, NJ, h->stream);
       h->launches += set_identity(h->pF, P, NJ, h->stream);
@@ -540,17 +544,17 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // F <- Pm F ; T <- A Pm ; A <- Pm T
       GemmDesc a = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
       add(a, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pF, 1, P, 0, 0, PP), P));
-      run(h, a, prec);
+      run(h, a, 0);
       if (!h->measuring) {
         cudaMemcpyAsync(h->pF, h->pT, NJ * PP * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
       }
       if (j + 1 < blk.steps.size()) {
         GemmDesc b = desc(P, P, 1, NJ, h->pT, P, 1, 0, PP);
         add(b, grp(op(h->pA, P, 1, 0, 0, PP), op(h->pP, 1, P, 0, 0, PP), P));
-        run(h, b, prec);
+        run(h, b, 0);
         GemmDesc c = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
         add(c, grp(op(h->pP, P, 1, 0, 0, PP), op(h->pT, 1, P, 0, 0, PP), P));
-        run(h, c, prec);
+        run(h, c, 0);
         if (!h->measuring) h->launches += symmetrize(h->pA, P, NJ, h->stream);
       }
     }
@@ -783,7 +787,9 @@ void setup_schedules(ttn_ctx* h) {
   // At most four composed steps (growth <= 30) per fresh Gram matrix: longer
   // compositions lose accuracy on the small singular directions.
   h->polar_f64 = polar_schedule(l0, 30.0, 1e-15, 4);
-  h->polar_tc = polar_schedule(l0, 30.0, 1e-7, 4);
+  // mixed modes: one FP64 Gram and one long FP64 composition (its accuracy
+  // loss, ~1e-8, is below the tensor-core apply that follows)
+  h->polar_tc = polar_schedule(l0, 1e300, 1e-12, 1000);
 }
 
 }  // namespace
