@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--chi", type=int, default=128)
     p.add_argument("--no-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
+    p.add_argument("--profile-sweeps", type=int, default=0,
+                   help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
     return p.parse_args()
 
 
@@ -326,8 +328,27 @@ def run_gpu(args):
         print(json.dumps(out), flush=True)
 
 
+def run_profile_only(args):
+    """Eager sweeps (no CUDA graph) of the bench workload, for ncu."""
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+    model = ti.tfim_chain(1024, 1.0)
+    ws, V = ti.initial_tensors(1024, 2, args.chi, 1)
+    s = Sweeper(model, args.chi, prec=args.prec, use_graph=False)
+    s.set_isometries(0, ws, V)
+    E = s.sweep(args.profile_sweeps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sweeps": args.profile_sweeps, "prec": args.prec,
+                      "energies": E[:, 0].tolist(), "launches": s.launch_count}))
+    s.close()
+
+
 def main():
     args = parse()
+    if args.profile_sweeps:
+        run_profile_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
