@@ -156,14 +156,24 @@ int launch_tile(const GemmDesc& d, cudaStream_t s) {
 
 }  // namespace
 
+// 64 x 64 tiles when they alone give two waves, else 32 x 32 or 16 x 16.
+int f64_tile(const GemmDesc& d) {
+  const long long b = (long long)d.B0 * d.B1;
+  if (d.M >= 64 && d.N >= 64 && ((long long)((d.M + 63) / 64) * ((d.N + 63) / 64) * b >= 296 ||
+                                 total_k_tiles(d) < 8))
+    return 64;
+  if (d.M >= 32 && d.N >= 32) return 32;
+  if (d.M >= 64 && d.N >= 64) return 64;
+  return 16;
+}
+
 int gemm_pick_splits(const GemmDesc& d) {
   if (d.prec != 0 && gemm_tc_supported(d)) return tc_pick_splits(d);
-  const int bm = (d.M >= 64 && d.N >= 64) ? 64 : (d.M >= 32 && d.N >= 32) ? 32 : 16;
-  const int bn = bm;
-  const long long base = (long long)((d.M + bm - 1) / bm) * ((d.N + bn - 1) / bn) * d.B0 * d.B1;
+  const int bm = f64_tile(d);
+  const long long base = (long long)((d.M + bm - 1) / bm) * ((d.N + bm - 1) / bm) * d.B0 * d.B1;
   const int kt = total_k_tiles(d);
-  if (base >= 296 || kt < 8) return 1;
-  int s = (int)std::min<long long>((296 + base - 1) / base, kt / 4);
+  if (base >= 296 || kt < 4) return 1;
+  int s = (int)std::min<long long>((296 + base - 1) / base, kt / 2);
   s = std::max(1, std::min(s, 64));
   return s;
 }
@@ -177,8 +187,9 @@ int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
   GemmDesc d = d0;
   if (d.M <= 0 || d.N <= 0 || d.B0 * d.B1 <= 0) return 0;
   int n = 0;
-  if (d.M >= 64 && d.N >= 64) n += launch_tile<64, 64>(d, s);
-  else if (d.M >= 32 && d.N >= 32) n += launch_tile<32, 32>(d, s);
+  const int t = f64_tile(d);
+  if (t == 64) n += launch_tile<64, 64>(d, s);
+  else if (t == 32) n += launch_tile<32, 32>(d, s);
   else n += launch_tile<16, 16>(d, s);
   if (d.splits > 1) {
     const long long total = (long long)d.M * d.N * d.B0 * d.B1;

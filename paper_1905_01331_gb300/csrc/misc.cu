@@ -188,9 +188,9 @@ __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const in
     lo = fmin(lo, alpha[i] - r);
     hi = fmax(hi, alpha[i] + r);
   }
-  for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+  for (int it = 0; it < 120; ++it) {
     const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
+    if (mid <= lo || mid >= hi || hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
     if (sturm_count(alpha, beta, m, mid) >= 1) hi = mid; else lo = mid;
   }
   const double th = 0.5 * (lo + hi);
@@ -198,7 +198,7 @@ __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const in
   double x[128], dd[128], du[128], du2[128], rhs[128];
   for (int i = 0; i < m; ++i) x[i] = 1.0 / sqrt((double)m);
   const double eps = fmax(fabs(th), 1.0) * 1e-15;
-  for (int round = 0; round < 3; ++round) {
+  for (int round = 0; round < 2; ++round) {
     for (int i = 0; i < m; ++i) { dd[i] = alpha[i] - th; du[i] = i + 1 < m ? beta[i] : 0.0; du2[i] = 0.0; rhs[i] = x[i]; }
     double dl[128];
     for (int i = 0; i + 1 < m; ++i) dl[i] = beta[i];

@@ -523,10 +523,10 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += batched_dot(Gam, W, PN, PN, NJ, gw, h->red, h->stream);
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream);
   }
-  // FP64 mode: every product FP64, short blocks.  Mixed modes: the Gram
-  // matrices and the P x P polynomial are FP64 (the small singular directions
-  // must not drown in tensor-core rounding), only X <- F X runs on the tensor
-  // cores, followed by one FP64 Newton-Schulz polish of the isometry.
+  // The polar factor is FP64 in every mode (the small singular directions
+  // must not drown in tensor-core rounding).  FP64 mode: short blocks (at most
+  // four composed steps per Gram matrix) for full accuracy; mixed modes: one
+  // Gram matrix and one long composition.
   const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
   for (const PolarBlock& blk : sched) {
     // A = X X^T
@@ -558,25 +558,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
         if (!h->measuring) h->launches += symmetrize(h->pA, P, NJ, h->stream);
       }
     }
-    // X2 = F X ; swap
+    // X2 = F X ; swap.  F amplifies the small singular directions by up to
+    // 1/damping, so this product is FP64 in every mode (a tensor-core product
+    // of it would lose those directions to cancellation).
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
-    run(h, f, prec);
-    std::swap(X, X2);
-  }
-  if (prec != 0) {
-    // FP64 polish: A = X X^T (FP64), X2 = X - 0.5 (A - I) X
-    GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
-    add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
-    run(h, g, 0);
-    if (!h->measuring) {
-      h->launches += symmetrize(h->pA, P, NJ, h->stream);
-      h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, -1.0, -1.0, h->stream);  // A - I
-      cudaMemcpyAsync(X2, X, NJ * PN * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
-    }
-    GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN, -0.5, 1.0);
-    add(f, grp(op(h->pP, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
-    run(h, f, prec);
+    run(h, f, 0);
     std::swap(X, X2);
   }
   if (!h->measuring) h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
@@ -787,9 +774,10 @@ void setup_schedules(ttn_ctx* h) {
   // At most four composed steps (growth <= 30) per fresh Gram matrix: longer
   // compositions lose accuracy on the small singular directions.
   h->polar_f64 = polar_schedule(l0, 30.0, 1e-15, 4);
-  // mixed modes: one FP64 Gram and one long FP64 composition (its accuracy
-  // loss, ~1e-8, is below the tensor-core apply that follows)
-  h->polar_tc = polar_schedule(l0, 1e300, 1e-12, 1000);
+  // mixed modes: one FP64 Gram and one long FP64 composition; its loss of
+  // accuracy on the small singular directions (~1e-8) is below the rounding
+  // of the tensor-core contractions around it
+  h->polar_tc = polar_schedule(l0, 1e300, 1e-15, 1000);
 }
 
 }  // namespace
