@@ -566,6 +566,23 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     run(h, f, 0);
     std::swap(X, X2);
   }
+  if (prec != 0) {
+    // The long composition leaves an isometry defect near 1e-8: one Newton-
+    // Schulz polish X <- X - (X X^T - I) X / 2 with an FP64 Gram matrix; the
+    // correction is that small, so its product may run on the tensor cores.
+    GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
+    add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
+    run(h, g, 0);
+    if (!h->measuring) {
+      h->launches += symmetrize(h->pA, P, NJ, h->stream);
+      h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, -1.0, -1.0, h->stream);  // A - I
+      cudaMemcpyAsync(X2, X, NJ * PN * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    }
+    GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN, -0.5, 1.0);
+    add(f, grp(op(h->pP, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
+    run(h, f, prec);
+    std::swap(X, X2);
+  }
   if (!h->measuring) h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
 }
 
