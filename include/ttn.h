@@ -164,6 +164,23 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 size_t ttn_selftest_bytes(void);
 int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out, void* stream);
 
+/* Allocation-free close product, for callers that cannot allocate device
+ * memory (plug-ins inside an application that owns the CUDA allocator, or code
+ * where cudaMalloc is not permitted); the paper has no counterpart.
+ *   C[p][q] = sum_{j < n2} Y[p][j] W[q][j]      (FP64, row-major, all device)
+ * the product over both child legs that ends every ascend step.  It runs the
+ * library's FP64 split-K kernel with its partial sums in a fixed 8 MiB device
+ * array inside the library instead of caller scratch; every GPU that loads the
+ * library holds that array until the process exits.  The first call on a
+ * device looks the array up (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Calls share the array: two calls that overlap on
+ * the GPU race (use one stream, or order them).  Nothing needs clearing: each
+ * call overwrites every partial sum it reads.  Limits: 1 <= P, Q <= 256 and
+ * 1 <= n2 <= 2^30, else TTN_EINVAL.  Work is enqueued on `stream` (cudaStream_t
+ * as void*); the call allocates nothing. */
+int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, int Q, long long n2,
+                      double* d_C, void* stream);
+
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);
 

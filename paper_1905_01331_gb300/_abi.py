@@ -51,6 +51,8 @@ SIGNATURES = {
     "ttn_selftest_bytes": (ctypes.c_size_t, []),
     "ttn_selftest_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, _dp,
                                          ctypes.c_int, ctypes.c_void_p]),
+    "ttn_close_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
     "ttn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ttn_destroy": (None, [ctypes.c_void_p]),
 }

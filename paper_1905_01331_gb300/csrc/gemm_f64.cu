@@ -7,7 +7,9 @@
 // rank-3 tensors") are folded into the address arithmetic and never stored.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
+#include "../../include/ttn.h"
 #include "common.h"
 
 namespace ttn {
@@ -201,3 +203,72 @@ int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
 }
 
 }  // namespace ttn
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the split-K close product.
+//
+// Callers such as plug-ins of a host application that owns the CUDA allocator,
+// or code running where cudaMalloc is not allowed, cannot hand the library a
+// scratch buffer.  For them ttn_close_noalloc runs the same FP64 split-K
+// product, but keeps its partial sums in this fixed array in device memory.
+// Every GPU that loads the library holds the array (8 MiB) until the process
+// exits.  In host code the array's name is only a host-side stand-in, so the
+// entry point fetches its device address once per device with
+// cudaGetSymbolAddress and hands that to the kernels.
+// ---------------------------------------------------------------------------
+
+namespace ttn {
+namespace {
+
+constexpr long long kNoAllocScratchDoubles = 1LL << 20;   // 8 MiB of FP64 partial sums
+constexpr int kNoAllocMaxDim = 256;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+}  // namespace ttn
+
+extern "C" int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, int Q, long long n2,
+                                 double* d_C, void* stream) {
+  using namespace ttn;
+  if (!d_Y || !d_W || !d_C) return TTN_EINVAL;
+  if (P < 1 || Q < 1 || P > kNoAllocMaxDim || Q > kNoAllocMaxDim) return TTN_EINVAL;
+  if (n2 < 1 || n2 > (1LL << 30)) return TTN_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return TTN_ECUDA;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TTN_ECUDA;
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  GemmDesc d;
+  memset(&d, 0, sizeof(d));
+  d.M = P; d.N = Q; d.B0 = 1; d.B1 = 1;
+  d.C = d_C; d.sc_m = Q; d.sc_n = 1;
+  d.alpha = 1.0; d.beta = 0.0; d.prec = 0;
+  Group g;
+  // K0 = 1, K1 = n2: any length, addressed through the K1 stride
+  g.a.p = d_Y; g.a.s_mn = n2; g.a.s_k0 = 1; g.a.s_k1 = 1; g.a.s_b0 = 0; g.a.s_b1 = 0;
+  g.b.p = d_W; g.b.s_mn = n2; g.b.s_k0 = 1; g.b.s_k1 = 1; g.b.s_b0 = 0; g.b.s_b1 = 0;
+  g.K = static_cast<int>(n2);
+  g.k0_log2 = 0;
+  d.g[0] = g;
+  d.ngroups = 1;
+  const long long per_split = static_cast<long long>(P) * Q;
+  int splits = gemm_pick_splits(d);
+  splits = static_cast<int>(std::min<long long>(splits, kNoAllocScratchDoubles / per_split));
+  d.splits = std::max(1, splits);
+  d.partial = scratch;
+  gemm_launch(d, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ECUDA;
+}
