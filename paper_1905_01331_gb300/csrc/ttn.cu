@@ -525,8 +525,8 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   }
   // The polar factor is FP64 in every mode (the small singular directions
   // must not drown in tensor-core rounding).  FP64 mode: short blocks (at most
-  // four composed steps per Gram matrix) for full accuracy; mixed modes: one
-  // Gram matrix and one long composition.
+  // four composed steps per Gram matrix) for full accuracy; mixed modes: two
+  // Gram matrices and two long compositions.
   const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
   for (const PolarBlock& blk : sched) {
     // A = X X^T
@@ -564,23 +564,6 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
     run(h, f, 0);
-    std::swap(X, X2);
-  }
-  if (prec != 0) {
-    // The long composition leaves an isometry defect near 1e-8: one Newton-
-    // Schulz polish X <- X - (X X^T - I) X / 2 with an FP64 Gram matrix; the
-    // correction is that small, so its product may run on the tensor cores.
-    GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
-    add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
-    run(h, g, 0);
-    if (!h->measuring) {
-      h->launches += symmetrize(h->pA, P, NJ, h->stream);
-      h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, -1.0, -1.0, h->stream);  // A - I
-      cudaMemcpyAsync(X2, X, NJ * PN * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
-    }
-    GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN, -0.5, 1.0);
-    add(f, grp(op(h->pP, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
-    run(h, f, prec);
     std::swap(X, X2);
   }
   if (!h->measuring) h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
@@ -791,10 +774,11 @@ void setup_schedules(ttn_ctx* h) {
   // At most four composed steps (growth <= 30) per fresh Gram matrix: longer
   // compositions lose accuracy on the small singular directions.
   h->polar_f64 = polar_schedule(l0, 30.0, 1e-15, 4);
-  // mixed modes: one FP64 Gram and one long FP64 composition; its loss of
-  // accuracy on the small singular directions (~1e-8) is below the rounding
-  // of the tensor-core contractions around it
-  h->polar_tc = polar_schedule(l0, 1e300, 1e-15, 1000);
+  // mixed modes: two blocks -- one long composition for the growth of the
+  // small singular values (its ~1e-8 loss of accuracy on those directions is
+  // below the rounding of the tensor-core contractions around it), then a
+  // fresh Gram matrix for the well-conditioned convergence to an exact isometry
+  h->polar_tc = polar_schedule(l0, 1e5, 1e-15, 1000);
 }
 
 }  // namespace
