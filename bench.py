@@ -51,6 +51,19 @@ def parse():
     return p.parse_args()
 
 
+def aggregate(ms_local: float, steps: int, world: int, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank ran `steps` sweeps in
+    ms_local milliseconds; the job takes the slowest rank's time.  Returns
+    (sweeps per second over all ranks, max milliseconds)."""
+    t_max = ms_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return world * steps / (t_max * 1e-3), t_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,12 +228,7 @@ def run_gpu(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     launches = s.launch_count
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max * 1e-3)
+    value, t_max = aggregate(ms, args.steps, world, dist, device="cuda")
 
     # profiling sweep: dominant kernel family
     prof = s.profile_sweep()

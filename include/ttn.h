@@ -104,11 +104,13 @@ int ttn_sizes(ttn_t h, int inst, size_t* n_w, size_t* n_v, int* n_layers);
 /* Bond dimensions chi_0..chi_T of one instance (host array of n_layers+1). */
 int ttn_chis(ttn_t h, int inst, int* chis);
 
-/* Copy host isometries (concatenated as ttn_sizes describes) and top tensor
- * of one instance to the device.  No check of the isometric constraint. */
+/* Copy isometries (concatenated as ttn_sizes describes) and top tensor of
+ * one instance into the context.  The pointers may be host or device memory
+ * (unified addressing).  No check of the isometric constraint. */
 int ttn_set_isometries(ttn_t h, int inst, const double* host_w_all, const double* host_v);
 
-/* Copy one instance's current isometries and top tensor to host buffers. */
+/* Copy one instance's current isometries and top tensor out (host or device
+ * pointers; either may be NULL to skip it). */
 int ttn_get_isometries(ttn_t h, int inst, double* host_w_all, double* host_v);
 
 /* Run n_sweeps sweeps of every instance (Sec. III): ascend the Hamiltonian
@@ -136,9 +138,14 @@ int ttn_energy(ttn_t h, int inst, double* E_total);
  * over the sites of that layer (R / N_t); which = 1: the leftmost site. */
 int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* host_out);
 
-/* Environment dE/dw of isometry layer `layer` at the current tensors, written
- * to caller device memory d_out (FP64, the isometry's shape; per node, all
- * nodes).  This is the backward of the energy with respect to w. */
+/* Environment dE/dw of isometry layer `layer` at the current tensors (Sec.
+ * III.A: the sum of the contributions of all Hamiltonian terms), written to
+ * caller device memory d_out (FP64, the isometry's shape; per node, all
+ * nodes).  layer == T (the number of isometry layers) gives dE/dv = 2 H_top v
+ * of the top tensor; layer == -1 gives every layer, concatenated as
+ * ttn_set_isometries lays them out, followed by dE/dv.  This is the backward
+ * of ttn_energy with respect to the tensors; ascended operators are kept and
+ * the chi^3 intermediates recomputed. */
 int ttn_env(ttn_t h, int inst, int layer, double* d_out);
 
 /* Serialise / restore all isometries, top tensors and sweep counters. */
@@ -157,10 +164,10 @@ long long ttn_launch_count(ttn_t h);
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
- * operands over nine operand layouts (K-major / M-major, two-level K and batch,
- * ragged edges, split K, alpha/beta).  d_ws: caller device memory of at least
+ * operands over eleven cases (K-major / M-major, two-level K and batch, ragged
+ * edges, split K, alpha/beta, FP32 sources).  d_ws: caller device memory of at least
  * ttn_selftest_bytes(); prec: 1..4 (ttn_precision); out_rel[i] receives
- * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 9). */
+ * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 11). */
 size_t ttn_selftest_bytes(void);
 int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out, void* stream);
 

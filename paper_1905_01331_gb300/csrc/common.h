@@ -12,8 +12,9 @@ namespace ttn {
 // express every contraction of the sweep on tensors w[p][l][r] without
 // materialising a permutation.
 struct Operand {
-  const double* p;
+  const void* p;     // FP64 data, or FP32 when f32 != 0
   long long s_mn, s_k0, s_k1, s_b0, s_b1;
+  int f32;
 };
 
 struct Group {
@@ -32,7 +33,8 @@ struct GemmDesc {
   int M, N, B0, B1;
   int ngroups;
   Group g[kMaxGroups];
-  double* C;
+  void* C;           // FP64 output, or FP32 when c_f32 != 0
+  int c_f32;
   long long sc_m, sc_n, sc_b0, sc_b1;
   double alpha, beta;
   int splits;
@@ -94,12 +96,16 @@ int ordered_sum(const double* x, int count, double* out, double scale, double ad
 // per_node, else both 0.
 int split_identity(double* O, long long stride, int P, int nodes, const double* e_in,
                    int per_node, double* e_out, cudaStream_t s);
-// Z_J += coef * (e_in[left] + e_in[right]) * W_J for each node J (elems each).
-int add_identity_part(double* Z, const double* W, long long elems, int nodes, const double* e_in,
-                      int per_node, double coef, cudaStream_t s);
+// Z_J += coef * (e_in[left] + e_in[right]) * W_J for each node J (elems each);
+// Z and W are FP32 when f32 != 0, else FP64.
+int add_identity_part(void* Z, const void* W, int f32, long long elems, int nodes,
+                      const double* e_in, int per_node, double coef, cudaStream_t s);
 // *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add.
 int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
                    cudaStream_t s);
+
+// dst[i] = (float) src[i]
+int to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 
 // NaN/Inf scan: flag[0] |= 1 if any element is not finite.
 int finite_check(const double* x, long long n, int* flag, cudaStream_t s);

@@ -28,7 +28,18 @@ __device__ __forceinline__ double ld_operand(const Operand& o, int k0_log2, long
                                              int i, int k) {
   const int k0 = k & ((1 << k0_log2) - 1);
   const int k1 = k >> k0_log2;
-  return o.p[base + i * o.s_mn + k0 * o.s_k0 + (long long)k1 * o.s_k1];
+  const long long e = base + i * o.s_mn + k0 * o.s_k0 + (long long)k1 * o.s_k1;
+  return o.f32 ? (double)static_cast<const float*>(o.p)[e] : static_cast<const double*>(o.p)[e];
+}
+
+__device__ __forceinline__ void st_out(const GemmDesc& d, long long e, double acc) {
+  if (d.c_f32) {
+    float* c = static_cast<float*>(d.C) + e;
+    *c = d.beta == 0.0 ? (float)(d.alpha * acc) : (float)(d.alpha * acc + d.beta * (double)*c);
+  } else {
+    double* c = static_cast<double*>(d.C) + e;
+    *c = d.beta == 0.0 ? d.alpha * acc : d.alpha * acc + d.beta * *c;
+  }
 }
 
 // BM x BN output tile per CTA, 256 threads, each thread TM x TN outputs.
@@ -101,16 +112,13 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
   }
 
   if (d.splits == 1) {
-    double* C = d.C + b0 * d.sc_b0 + (long long)b1 * d.sc_b1;
+    const long long cb = b0 * d.sc_b0 + (long long)b1 * d.sc_b1;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-        if (m < d.M && n < d.N) {
-          double* c = C + m * d.sc_m + n * d.sc_n;
-          *c = d.beta == 0.0 ? d.alpha * acc[i][j] : d.alpha * acc[i][j] + d.beta * *c;
-        }
+        if (m < d.M && n < d.N) st_out(d, cb + m * d.sc_m + n * d.sc_n, acc[i][j]);
       }
   } else {
     const long long MN = (long long)d.M * d.N;
@@ -137,8 +145,7 @@ __global__ void splitk_reduce_kernel(const GemmDesc d) {
     double s = 0.0;
     for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
     const int b0 = (int)(b % d.B0), b1 = (int)(b / d.B0);
-    double* c = d.C + b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n;
-    *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
+    st_out(d, b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n, s);
   }
 }
 
@@ -258,8 +265,8 @@ extern "C" int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, in
   d.alpha = 1.0; d.beta = 0.0; d.prec = 0;
   Group g;
   // K0 = 1, K1 = n2: any length, addressed through the K1 stride
-  g.a.p = d_Y; g.a.s_mn = n2; g.a.s_k0 = 1; g.a.s_k1 = 1; g.a.s_b0 = 0; g.a.s_b1 = 0;
-  g.b.p = d_W; g.b.s_mn = n2; g.b.s_k0 = 1; g.b.s_k1 = 1; g.b.s_b0 = 0; g.b.s_b1 = 0;
+  g.a.p = d_Y; g.a.s_mn = n2; g.a.s_k0 = 1; g.a.s_k1 = 1; g.a.s_b0 = 0; g.a.s_b1 = 0; g.a.f32 = 0;
+  g.b.p = d_W; g.b.s_mn = n2; g.b.s_k0 = 1; g.b.s_k1 = 1; g.b.s_b0 = 0; g.b.s_b1 = 0; g.b.f32 = 0;
   g.K = static_cast<int>(n2);
   g.k0_log2 = 0;
   d.g[0] = g;

@@ -91,11 +91,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ double ld_op(const Operand& o, int k0_log2, long long base, int i,
-                                        int k) {
+template <typename T>
+__device__ __forceinline__ T ld_op(const Operand& o, int k0_log2, long long base, int i, int k) {
   const int k0 = k & ((1 << k0_log2) - 1);
   const int k1 = k >> k0_log2;
-  return o.p[base + i * o.s_mn + k0 * o.s_k0 + static_cast<long long>(k1) * o.s_k1];
+  return static_cast<const T*>(o.p)[base + i * o.s_mn + k0 * o.s_k0 +
+                                    static_cast<long long>(k1) * o.s_k1];
 }
 
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
@@ -117,6 +118,20 @@ __device__ __forceinline__ void split(double x, uint32_t& hi, uint32_t& lo) {
     hi = tf32_bits(static_cast<float>(x));
     const float hf = __uint_as_float(hi);
     lo = tf32_bits(static_cast<float>(x - static_cast<double>(hf)));
+  }
+}
+
+// The same split of an FP32 value: FP32 arithmetic only (no FP64 pipe).
+template <bool kBF16>
+__device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
+  if constexpr (kBF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+  } else {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
   }
 }
 
@@ -160,30 +175,39 @@ __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
   }
 }
 
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+  if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    a = t.x; b = t.y;
+  } else {
+    a = p[0]; b = p[1];
+  }
+}
+
 // Stage rows [r0, r0 + ROWS) x K tile [kb, kb + BK) of one operand.  Fast
 // paths when the tile lies inside one K0 slice and the source is K-major
 // (s_k0 == 1: 16-byte loads along K) or MN-major (s_mn == 1: 16-byte loads
 // along rows, transposed in registers); otherwise element by element.
-template <bool kBF16, bool kSplit, int BK, int ROWS>
-__device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, long long base,
-                                              int r0, int nrows_valid, int kb, int Kg,
-                                              uint8_t* hi_tile, uint8_t* lo_tile) {
+template <typename T, bool kBF16, bool kSplit, int BK, int ROWS>
+__device__ __forceinline__ void stage_operand_t(const Operand& o, int k0_log2, long long base,
+                                                int r0, int nrows_valid, int kb, int Kg,
+                                                uint8_t* hi_tile, uint8_t* lo_tile) {
   constexpr int CH = kBF16 ? 8 : 4;           // K values per 16-byte chunk
   constexpr int NCH = BK / CH;                // chunks per row (8)
   const int K0 = 1 << k0_log2;
   const int kvalid = min(BK, Kg - kb);
   const bool slice = (K0 >= BK) && (kvalid == BK);
   if (slice && o.s_k0 == 1) {
-    const double* tb = o.p + base + static_cast<long long>(kb >> k0_log2) * o.s_k1 +
-                       (kb & (K0 - 1));
+    const T* tb = static_cast<const T*>(o.p) + base +
+                  static_cast<long long>(kb >> k0_log2) * o.s_k1 + (kb & (K0 - 1));
     for (int task = threadIdx.x; task < ROWS * NCH; task += kThreadsTC) {
       const int r = task / NCH, c = task % NCH;
       uint32_t h[CH], l[CH];
       if (r < nrows_valid) {
-        const double* src = tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH;
+        const T* src = tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH;
 #pragma unroll
         for (int q = 0; q < CH; q += 2) {
-          double a, b;
+          T a, b;
           ld2(src + q, a, b);
           split<kBF16>(a, h[q], l[q]);
           split<kBF16>(b, h[q + 1], l[q + 1]);
@@ -198,8 +222,9 @@ __device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, lon
     return;
   }
   if (slice && o.s_mn == 1 && (nrows_valid & 3) == 0) {
-    const double* tb = o.p + base + static_cast<long long>(kb >> k0_log2) * o.s_k1 +
-                       static_cast<long long>(kb & (K0 - 1)) * o.s_k0;
+    const T* tb = static_cast<const T*>(o.p) + base +
+                  static_cast<long long>(kb >> k0_log2) * o.s_k1 +
+                  static_cast<long long>(kb & (K0 - 1)) * o.s_k0;
     // task: 4 consecutive rows x one chunk of CH consecutive K values
     for (int task = threadIdx.x; task < (ROWS / 4) * NCH; task += kThreadsTC) {
       const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
@@ -208,8 +233,8 @@ __device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, lon
       if (r < nrows_valid) {
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
-          const double* src = tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r);
-          double v0, v1, v2, v3;
+          const T* src = tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r);
+          T v0, v1, v2, v3;
           ld2(src, v0, v1);
           ld2(src + 2, v2, v3);
           split<kBF16>(v0, h[0][q], l[0][q]);
@@ -238,13 +263,25 @@ __device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, lon
     int r, kk;
     if (kfast) { kk = e % BK; r = e / BK; } else { r = e % ROWS; kk = e / ROWS; }
     const int k = kb + kk;
-    double x = 0.0;
-    if (r < nrows_valid && k < Kg) x = ld_op(o, k0_log2, base, r0 + r, k);
+    T x = T(0);
+    if (r < nrows_valid && k < Kg) x = ld_op<T>(o, k0_log2, base, r0 + r, k);
     uint32_t hh, ll;
     split<kBF16>(x, hh, ll);
     st_elem<kBF16>(hi_tile, r, kk, hh);
     if constexpr (kSplit) st_elem<kBF16>(lo_tile, r, kk, ll);
   }
+}
+
+template <bool kBF16, bool kSplit, int BK, int ROWS>
+__device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, long long base,
+                                              int r0, int nrows_valid, int kb, int Kg,
+                                              uint8_t* hi_tile, uint8_t* lo_tile) {
+  if (o.f32)
+    stage_operand_t<float, kBF16, kSplit, BK, ROWS>(o, k0_log2, base, r0, nrows_valid, kb, Kg,
+                                                    hi_tile, lo_tile);
+  else
+    stage_operand_t<double, kBF16, kSplit, BK, ROWS>(o, k0_log2, base, r0, nrows_valid, kb, Kg,
+                                                     hi_tile, lo_tile);
 }
 
 struct TCParams {
@@ -400,14 +437,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_tc_kernel(const GemmDesc d
       }
       if (m < d.M) {
         if (d.splits == 1) {
-          double* C = d.C + b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m;
+          const long long cb = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
             if (n < d.N) {
               const double v = static_cast<double>(__uint_as_float(r[j]));
-              double* c = C + n * d.sc_n;
-              *c = d.beta == 0.0 ? d.alpha * v : d.alpha * v + d.beta * *c;
+              if (d.c_f32) {
+                float* c = static_cast<float*>(d.C) + cb + n * d.sc_n;
+                *c = d.beta == 0.0 ? static_cast<float>(d.alpha * v)
+                                   : static_cast<float>(d.alpha * v + d.beta * static_cast<double>(*c));
+              } else {
+                double* c = static_cast<double*>(d.C) + cb + n * d.sc_n;
+                *c = d.beta == 0.0 ? d.alpha * v : d.alpha * v + d.beta * *c;
+              }
             }
           }
         } else {
@@ -439,8 +482,15 @@ __global__ void splitk_reduce_tc(const GemmDesc d) {
     double s = 0.0;
     for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
     const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
-    double* c = d.C + b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
-    *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
+    const long long ce = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
+    if (d.c_f32) {
+      float* c = static_cast<float*>(d.C) + ce;
+      *c = d.beta == 0.0 ? static_cast<float>(d.alpha * s)
+                         : static_cast<float>(d.alpha * s + d.beta * static_cast<double>(*c));
+    } else {
+      double* c = static_cast<double*>(d.C) + ce;
+      *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
+    }
   }
 }
 

@@ -313,18 +313,25 @@ __global__ void split_identity_kernel(double* O, long long stride, int P, const 
   }
 }
 
-__global__ void add_identity_kernel(double* Z, const double* W, long long elems, const double* e_in,
+template <typename T>
+__global__ void add_identity_kernel(T* Z, const T* W, long long elems, const double* e_in,
                                     int per_node, double coef) {
   const int J = blockIdx.y;
   const double c = coef * (e_in[per_node ? 2 * J : 0] + e_in[per_node ? 2 * J + 1 : 0]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
        i += (long long)gridDim.x * blockDim.x)
-    Z[J * elems + i] += c * W[J * elems + i];
+    Z[J * elems + i] += static_cast<T>(c) * W[J * elems + i];
 }
 
 __global__ void top_energy_kernel(const double* dot, const double* e, int per_node, double add,
                                   double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add;
+}
+
+__global__ void to_f32_kernel(const double* src, float* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = static_cast<float>(src[i]);
 }
 
 int grid_for(long long n, int per = 256, int cap = 1184) {
@@ -442,16 +449,28 @@ int split_identity(double* O, long long stride, int P, int nodes, const double* 
   return 1;
 }
 
-int add_identity_part(double* Z, const double* W, long long elems, int nodes, const double* e_in,
-                      int per_node, double coef, cudaStream_t s) {
-  add_identity_kernel<<<dim3(grid_for(elems, 256, 512), nodes), 256, 0, s>>>(Z, W, elems, e_in,
-                                                                              per_node, coef);
+int add_identity_part(void* Z, const void* W, int f32, long long elems, int nodes,
+                      const double* e_in, int per_node, double coef, cudaStream_t s) {
+  const dim3 grid(grid_for(elems, 256, 512), nodes);
+  if (f32)
+    add_identity_kernel<float><<<grid, 256, 0, s>>>(static_cast<float*>(Z),
+                                                    static_cast<const float*>(W), elems, e_in,
+                                                    per_node, coef);
+  else
+    add_identity_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(Z),
+                                                     static_cast<const double*>(W), elems, e_in,
+                                                     per_node, coef);
   return 1;
 }
 
 int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
                    cudaStream_t s) {
   top_energy_kernel<<<1, 32, 0, s>>>(dot, e, per_node, add, out);
+  return 1;
+}
+
+int to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  to_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
   return 1;
 }
 

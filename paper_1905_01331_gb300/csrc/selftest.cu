@@ -46,7 +46,7 @@ __global__ void max_abs_diff(const double* a, const double* b, long long n, doub
 Operand mk(const double* p, long long mn, long long k0, long long k1 = 0, long long b0 = 0,
            long long b1 = 0) {
   Operand o;
-  o.p = p; o.s_mn = mn; o.s_k0 = k0; o.s_k1 = k1; o.s_b0 = b0; o.s_b1 = b1;
+  o.p = p; o.s_mn = mn; o.s_k0 = k0; o.s_k1 = k1; o.s_b0 = b0; o.s_b1 = b1; o.f32 = 0;
   return o;
 }
 
@@ -59,7 +59,7 @@ using namespace ttn;
 
 extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out,
                                  void* stream) {
-  if (!d_ws || !out_rel || n_out < 9 || prec < 1 || prec > 4) return TTN_EINVAL;
+  if (!d_ws || !out_rel || n_out < 11 || prec < 1 || prec > 4) return TTN_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   gemm_tc_init();
   double* base = reinterpret_cast<double*>(d_ws);
@@ -150,6 +150,28 @@ extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out
     GemmDesc d = base_desc(4096, 64, 1, 1, 64, 1, 0, 0);
     d.g[d.ngroups++] = group(mk(A, 64, 1), mk(B, 1, 64), 64, 1);
     cases.push_back({d, 4096 * 64});
+  }
+  // FP32 sources (the storage of the mixed modes): copies of A and B
+  float* A32 = reinterpret_cast<float*>(partial + 48 * big / 4);
+  float* B32 = reinterpret_cast<float*>(partial + 56 * big / 4);
+  to_f32(A, A32, 2 * big, s);
+  to_f32(B, B32, 2 * big, s);
+  auto mkf = [&](const float* p, long long mn, long long k0, long long k1, long long b0,
+                 long long b1) {
+    Operand o = mk(nullptr, mn, k0, k1, b0, b1);
+    o.p = p;
+    o.f32 = 1;
+    return o;
+  };
+  {  // 10: FP32 sources, K-major A and N-major B, batch of 64 (right products)
+    GemmDesc d = base_desc(4096, 64, 1, 1, 64, 1, 0, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 64, 1, 0, 0, 0), mkf(B32, 1, 64, 0, 0, 0), 64, 1);
+    cases.push_back({d, 4096 * 64});
+  }
+  {  // 11: FP32 sources, M-major A and K-major B, K = 8192 (split K)
+    GemmDesc d = base_desc(128, 128, 1, 1, 128, 1, 0, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 1, 128, 0, 0, 0), mkf(B32, 8192, 1, 0, 0, 0), 8192, 1);
+    cases.push_back({d, 128 * 128});
   }
   const int nc = std::min<int>((int)cases.size(), n_out);
   std::vector<double> host(2);

@@ -76,6 +76,8 @@ struct Instance {
   // Identity part of the one-site operators, kept exactly in FP64: the true
   // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
   std::vector<double*> eoff;
+  // FP32 copies used by the tensor-core products (mixed modes)
+  std::vector<float*> w32, ops32, adj32;
   int sites(int t) const { return per_node ? (L >> t) : 1; }
   int nodes(int t) const { return per_node ? (L >> (t + 1)) : 1; }
   size_t w_elems(int t) const {
@@ -132,10 +134,26 @@ namespace {
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
 
-Operand op(const double* p, ll s_mn, ll s_k0, ll s_k1 = 0, ll s_b0 = 0, ll s_b1 = 0) {
+// A typed device pointer: FP64, or FP32 (the mixed modes keep the chi^3
+// intermediates and copies of w and of the operators in FP32).
+struct TP {
+  void* p;
+  int f32;
+  TP operator+(ll e) const {
+    return TP{static_cast<char*>(p) + e * (f32 ? 4 : 8), f32};
+  }
+};
+TP tp(double* p) { return TP{p, 0}; }
+TP tp(const double* p) { return TP{const_cast<double*>(p), 0}; }
+
+Operand op(TP p, ll s_mn, ll s_k0, ll s_k1 = 0, ll s_b0 = 0, ll s_b1 = 0) {
   Operand o;
-  o.p = p; o.s_mn = s_mn; o.s_k0 = s_k0; o.s_k1 = s_k1; o.s_b0 = s_b0; o.s_b1 = s_b1;
+  o.p = p.p; o.s_mn = s_mn; o.s_k0 = s_k0; o.s_k1 = s_k1; o.s_b0 = s_b0; o.s_b1 = s_b1;
+  o.f32 = p.f32;
   return o;
+}
+Operand op(const double* p, ll s_mn, ll s_k0, ll s_k1 = 0, ll s_b0 = 0, ll s_b1 = 0) {
+  return op(tp(p), s_mn, s_k0, s_k1, s_b0, s_b1);
 }
 
 Group grp(Operand a, Operand b, int K0, int K1 = 1) {
@@ -144,14 +162,18 @@ Group grp(Operand a, Operand b, int K0, int K1 = 1) {
   return g;
 }
 
-GemmDesc desc(int M, int N, int B0, int B1, double* C, ll sc_m, ll sc_n, ll sc_b0, ll sc_b1,
+GemmDesc desc(int M, int N, int B0, int B1, TP C, ll sc_m, ll sc_n, ll sc_b0, ll sc_b1,
               double alpha = 1.0, double beta = 0.0) {
   GemmDesc d;
   memset(&d, 0, sizeof(d));
-  d.M = M; d.N = N; d.B0 = B0; d.B1 = B1; d.C = C;
+  d.M = M; d.N = N; d.B0 = B0; d.B1 = B1; d.C = C.p; d.c_f32 = C.f32;
   d.sc_m = sc_m; d.sc_n = sc_n; d.sc_b0 = sc_b0; d.sc_b1 = sc_b1;
   d.alpha = alpha; d.beta = beta; d.splits = 1;
   return d;
+}
+GemmDesc desc(int M, int N, int B0, int B1, double* C, ll sc_m, ll sc_n, ll sc_b0, ll sc_b1,
+              double alpha = 1.0, double beta = 0.0) {
+  return desc(M, N, B0, B1, tp(C), sc_m, sc_n, sc_b0, sc_b1, alpha, beta);
 }
 
 void add(GemmDesc& d, const Group& g) {
@@ -165,9 +187,9 @@ ll max_offset(const Operand& o, int mn, int K0, int K1, int B0, int B1) {
          (ll)(B1 - 1) * o.s_b1;
 }
 
-void check_range(ttn_ctx* h, const double* p, ll max_off, const char* what) {
+void check_range(ttn_ctx* h, const void* p, ll max_off, int f32, const char* what) {
   if (h->registry.empty() || !h->bounds_error.empty()) return;
-  const size_t a = (size_t)p, e = a + (size_t)(max_off + 1) * sizeof(double);
+  const size_t a = (size_t)p, e = a + (size_t)(max_off + 1) * (f32 ? 4 : 8);
   for (auto& r : h->registry)
     if (a >= r.first && a < r.first + r.second) {
       if (e > r.first + r.second)
@@ -183,12 +205,12 @@ void check_desc(ttn_ctx* h, const GemmDesc& d) {
     const Group& G = d.g[g];
     const int K0 = 1 << G.k0_log2, K1 = G.K >> G.k0_log2;
     if (K0 * K1 != G.K || G.K <= 0) { h->bounds_error = "bad K split"; return; }
-    check_range(h, G.a.p, max_offset(G.a, d.M, K0, K1, d.B0, d.B1), "A operand");
-    check_range(h, G.b.p, max_offset(G.b, d.N, K0, K1, d.B0, d.B1), "B operand");
+    check_range(h, G.a.p, max_offset(G.a, d.M, K0, K1, d.B0, d.B1), G.a.f32, "A operand");
+    check_range(h, G.b.p, max_offset(G.b, d.N, K0, K1, d.B0, d.B1), G.b.f32, "B operand");
   }
   Operand c;
   c.p = d.C; c.s_mn = d.sc_m; c.s_k0 = d.sc_n; c.s_k1 = 0; c.s_b0 = d.sc_b0; c.s_b1 = d.sc_b1;
-  check_range(h, d.C, max_offset(c, d.M, d.N, 1, d.B0, d.B1), "C output");
+  check_range(h, d.C, max_offset(c, d.M, d.N, 1, d.B0, d.B1), d.c_f32, "C output");
 }
 
 // Run (or, in the plan pass, size and bounds-check) one product.
@@ -260,25 +282,36 @@ struct LayerView {
   int P, n, NJ, K;
   ll n2, Pn2, ss, node_ss;   // ss: site stride of ops_t; node_ss: ops_t stride per node
   ll adj_ss;                 // site stride of adj_{t+1}
-  const double* opsL;        // ops_t of the left child of node 0
-  const double* opsR;        // ops_t of the right child of node 0
+  TP opsL;                   // ops_t of the left child of node 0
+  TP opsR;                   // ops_t of the right child of node 0
+  TP W;                      // w_t
+  TP adj;                    // adjoints of site layer t+1
+  int f32;                   // storage of the chi^3 intermediates
 };
 
-LayerView view(const Instance& I, int t) {
+// Storage of one layer for a product precision: FP64 tensors for FP64
+// products, their FP32 copies for tensor-core products.
+LayerView view(const Instance& I, int t, int prec) {
   LayerView v;
   v.P = I.chis[t + 1]; v.n = I.chis[t]; v.NJ = I.nodes(t); v.K = I.K;
   v.n2 = (ll)v.n * v.n; v.Pn2 = (ll)v.P * v.n2;
   v.ss = (1 + 2 * I.K) * v.n2;
   v.node_ss = I.per_node ? 2 * v.ss : 0;
   v.adj_ss = I.per_node ? (ll)(1 + 2 * I.K) * v.P * v.P : 0;
-  v.opsL = I.ops[t];
-  v.opsR = I.ops[t] + (I.per_node ? v.ss : 0);
+  v.f32 = prec != 0;
+  const TP ops = v.f32 ? TP{I.ops32[t], 1} : tp(I.ops[t]);
+  v.opsL = ops;
+  v.opsR = ops + (I.per_node ? v.ss : 0);
+  v.W = v.f32 ? TP{I.w32[t], 1} : tp(I.W[t]);
+  v.adj = v.f32 ? TP{I.adj32[t + 1], 1} : tp(I.adj[t + 1]);
   return v;
 }
 
+TP scratch(double* p, const LayerView& v) { return TP{p, v.f32}; }
+
 // Y[b0][J] = W_J X_b0 for X = ops(side, first + b0), b0 < count:  right product.
-void right_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* side, int first,
-                int count, bool transX, double* Y, ll y_b0, int prec) {
+void right_mult(ttn_ctx* h, const LayerView& v, TP W, TP side, int first, int count, bool transX,
+                TP Y, ll y_b0, int prec) {
   GemmDesc d = desc(v.P * v.n, v.n, count, v.NJ, Y, v.n, 1, y_b0, v.Pn2);
   // B(i = column r', k = r) = X[r][r'] (or X[r'][r] when transposed)
   add(d, grp(op(W, v.n, 1, 0, 0, v.Pn2),
@@ -287,12 +320,12 @@ void right_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* s
 }
 
 // Y[b0][J][p] = X_b0^T W_{J,p} (transX: X_b0 W_{J,p}): left product, batched over p.
-void left_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* side, int first,
-               int count, bool transX, double* Y, ll y_b0, int prec) {
+void left_mult(ttn_ctx* h, const LayerView& v, TP W, TP side, int first, int count, bool transX,
+               TP Y, ll y_b0, int prec) {
   for (int k = 0; k < count; ++k) {
     GemmDesc d = desc(v.n, v.n, v.P, v.NJ, Y + k * y_b0, v.n, 1, v.n2, v.Pn2);
     // A(m = l', k = l) = X[l][l'] (X^T), or X[l'][l] (X)
-    const double* X = side + (first + k) * v.n2;
+    const TP X = side + (first + k) * v.n2;
     add(d, grp(op(X, transX ? v.n : 1, transX ? 1 : v.n, 0, 0, v.node_ss),
                op(W, 1, v.n, 0, v.n2, v.Pn2), v.n));
     run(h, d, prec);
@@ -300,15 +333,16 @@ void left_mult(ttn_ctx* h, const LayerView& v, const double* W, const double* si
 }
 
 void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
-  const LayerView v = view(I, t);
+  const LayerView v = view(I, t, prec);
   const int K = I.K;
-  const double* W = I.W[t];
+  const TP W = v.W;
   const ll slab = (ll)v.NJ * v.Pn2;    // one stacked tensor
-  double* U = h->M1;                  // U_k = W B_k(right child), K slabs
+  const TP U = scratch(h->M1, v);     // U_k = W B_k(right child), K slabs
+  const TP Y = scratch(h->Y, v);
   right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
   // Y0 = o_L^T W_p + W_p o_R + sum_k A_{k,L}^T U_k,p
   {
-    GemmDesc d = desc(v.n, v.n, v.P, v.NJ, h->Y, v.n, 1, v.n2, v.Pn2);
+    GemmDesc d = desc(v.n, v.n, v.P, v.NJ, Y, v.n, 1, v.n2, v.Pn2);
     add(d, grp(op(v.opsL, 1, v.n, 0, 0, v.node_ss), op(W, 1, v.n, 0, v.n2, v.Pn2), v.n));
     add(d, grp(op(W, v.n, 1, 0, v.n2, v.Pn2), op(v.opsR, 1, v.n, 0, 0, v.node_ss), v.n));
     for (int k = 0; k < K; ++k)
@@ -317,18 +351,20 @@ void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
     run(h, d, prec);
   }
   // Y_{1+k} = W A_{k,R};  Y_{1+K+k} = B_{k,L}^T W
-  right_mult(h, v, W, v.opsR, 1, K, false, h->Y + slab, slab, prec);
-  left_mult(h, v, W, v.opsL, 1 + K, K, false, h->Y + (1 + K) * slab, slab, prec);
-  // ops_{t+1}[J][j] = sum_{lr} Y_j[J][p][lr] W_J[q][lr]
+  right_mult(h, v, W, v.opsR, 1, K, false, Y + slab, slab, prec);
+  left_mult(h, v, W, v.opsL, 1 + K, K, false, Y + (1 + K) * slab, slab, prec);
+  // ops_{t+1}[J][j] = sum_{lr} Y_j[J][p][lr] W_J[q][lr]   (FP64 output)
   const ll out_site = (ll)(1 + 2 * K) * v.P * v.P;
   GemmDesc d = desc(v.P, v.P, 1 + 2 * K, v.NJ, I.ops[t + 1], v.P, 1, (ll)v.P * v.P,
                     I.per_node ? out_site : 0);
-  add(d, grp(op(h->Y, v.n2, 1, 0, slab, v.Pn2), op(W, v.n2, 1, 0, 0, v.Pn2), (int)v.n2));
+  add(d, grp(op(Y, v.n2, 1, 0, slab, v.Pn2), op(W, v.n2, 1, 0, 0, v.Pn2), (int)v.n2));
   run(h, d, prec);
   // identity part: e'_J = e_L + e_R + tr(o'_J)/P, o'_J -= tr/P I
-  if (!h->measuring)
+  if (!h->measuring) {
     h->launches += split_identity(I.ops[t + 1], I.per_node ? out_site : 0, v.P, v.NJ, I.eoff[t],
                                   I.per_node ? 1 : 0, I.eoff[t + 1], h->stream);
+    if (v.f32) h->launches += to_f32(I.ops[t + 1], I.ops32[t + 1], I.op_elems(t + 1), h->stream);
+  }
 }
 
 // Top Hamiltonian on x (c x c): w = o_0 x + x o_1^T + sum_k (A_k0 x B_k1^T + B_k0 x A_k1^T)
@@ -455,15 +491,15 @@ void top_adjoints(ttn_ctx* h, Instance& I) {
 
 // Gamma_J = R_J Zs + sum_k [P_k W A_k^T + P_k^T W A_k + Q_k B_k W + Q_k^T B_k^T W]
 void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
-  const LayerView v = view(I, t);
+  const LayerView v = view(I, t, prec);
   const int K = I.K;
-  const double* W = I.W[t];
+  const TP W = v.W;
   const ll slab = (ll)v.NJ * v.Pn2;
-  double* E_ = h->M1;                 // W B_k^T (K slabs)
-  double* U = h->M1 + K * slab;       // W B_k   (K slabs)
+  const TP E_ = scratch(h->M1, v);            // W B_k^T (K slabs)
+  const TP U = E_ + K * slab;                 // W B_k   (K slabs)
   right_mult(h, v, W, v.opsR, 1 + K, K, true, E_, slab, prec);
   right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
-  double* Zs = h->Y;                  // slab 0
+  const TP Zs = scratch(h->Y, v);             // slab 0
   {
     GemmDesc d = desc(v.n, v.n, v.P, v.NJ, Zs, v.n, 1, v.n2, v.Pn2);
     Operand Wl = op(W, 1, v.n, 0, v.n2, v.Pn2);      // B operand: W_p[k][i]
@@ -473,31 +509,31 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
     add(d, grp(Wr, op(v.opsR, v.n, 1, 0, 0, v.node_ss), v.n));    // W_p o_R^T
     add(d, grp(Wr, op(v.opsR, 1, v.n, 0, 0, v.node_ss), v.n));    // W_p o_R
     for (int k = 0; k < K; ++k) {
-      const double* Ak = v.opsL + (1 + k) * v.n2;
+      const TP Ak = v.opsL + (1 + k) * v.n2;
       add(d, grp(op(Ak, v.n, 1, 0, 0, v.node_ss), op(E_ + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
       add(d, grp(op(Ak, 1, v.n, 0, 0, v.node_ss), op(U + k * slab, 1, v.n, 0, v.n2, v.Pn2), v.n));
     }
     run(h, d, prec);
     // identity parts of o_L and o_R: W (e I (x) I + I (x) e I) = (e_L + e_R) W, twice (S + S^T)
     if (!h->measuring)
-      h->launches += add_identity_part(Zs, W, v.Pn2, v.NJ, I.eoff[t], I.per_node ? 1 : 0, 2.0,
-                                       h->stream);
+      h->launches += add_identity_part(Zs.p, W.p, v.f32, v.Pn2, v.NJ, I.eoff[t],
+                                       I.per_node ? 1 : 0, 2.0, h->stream);
   }
   // one-leg products: slabs 1.. of Y: WAt_k, WA_k, BW_k, BtW_k
-  double* WAt = h->Y + slab;
-  double* WA = WAt + K * slab;
-  double* BW = WA + K * slab;
-  double* BtW = BW + K * slab;
+  const TP WAt = Zs + slab;
+  const TP WA = WAt + K * slab;
+  const TP BW = WA + K * slab;
+  const TP BtW = BW + K * slab;
   right_mult(h, v, W, v.opsR, 1, K, true, WAt, slab, prec);
   right_mult(h, v, W, v.opsR, 1, K, false, WA, slab, prec);
   left_mult(h, v, W, v.opsL, 1 + K, K, true, BW, slab, prec);
   left_mult(h, v, W, v.opsL, 1 + K, K, false, BtW, slab, prec);
-  const double* G = I.adj[t + 1];
+  const TP G = v.adj;
   const ll PP = (ll)v.P * v.P;
-  GemmDesc d = desc(v.P, (int)v.n2, 1, v.NJ, Gam, v.n2, 1, 0, v.Pn2);
+  GemmDesc d = desc(v.P, (int)v.n2, 1, v.NJ, Gam, v.n2, 1, 0, v.Pn2);   // FP64 output
   auto Gn = [&](int j) { return op(G + j * PP, v.P, 1, 0, 0, v.adj_ss); };
   auto Gt = [&](int j) { return op(G + j * PP, 1, v.P, 0, 0, v.adj_ss); };
-  auto Tn = [&](const double* T) { return op(T, 1, v.n2, 0, 0, v.Pn2); };
+  auto Tn = [&](TP T) { return op(T, 1, v.n2, 0, 0, v.Pn2); };
   add(d, grp(Gn(0), Tn(Zs), v.P));
   for (int k = 0; k < K; ++k) {
     add(d, grp(Gn(1 + k), Tn(WAt + k * slab), v.P));
@@ -510,7 +546,7 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
 
 // w_t <- -polar(Gam - mu |Gam| w_t) by scaled Newton-Schulz blocks.
 void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
-  const LayerView v = view(I, t);
+  const LayerView v = view(I, t, 0);
   const int P = v.P, NJ = v.NJ;
   const ll N = v.n2, PN = v.Pn2, PP = (ll)P * P;
   double* W = I.W[t];
@@ -566,34 +602,37 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     run(h, f, 0);
     std::swap(X, X2);
   }
-  if (!h->measuring) h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
+  if (!h->measuring) {
+    h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
+    if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
+  }
 }
 
 // Adjoints of site layer t from those of t+1 through (new) w_t.
 void descend(ttn_ctx* h, Instance& I, int t, int prec) {
-  const LayerView v = view(I, t);
+  const LayerView v = view(I, t, prec);
   const int K = I.K;
-  const double* W = I.W[t];
+  const TP W = v.W;
   const ll slab = (ll)v.NJ * v.Pn2;
   const ll PP = (ll)v.P * v.P;
-  double* Yt = h->Yt;     // [j][J] G_j W
+  const TP Yt = scratch(h->Yt, v);     // [j][J] G_j W
   {
     GemmDesc d = desc(v.P, (int)v.n2, 1 + 2 * K, v.NJ, Yt, v.n2, 1, slab, v.Pn2);
-    add(d, grp(op(I.adj[t + 1], v.P, 1, 0, PP, v.adj_ss), op(W, 1, v.n2, 0, 0, v.Pn2), v.P));
+    add(d, grp(op(v.adj, v.P, 1, 0, PP, v.adj_ss), op(W, 1, v.n2, 0, 0, v.Pn2), v.P));
     run(h, d, prec);
   }
-  double* WB = h->M1;              // W B_{k,R}
-  double* AW = h->M1 + K * slab;   // A_{k,L}^T W
+  const TP WB = scratch(h->M1, v);     // W B_{k,R}
+  const TP AW = WB + K * slab;         // A_{k,L}^T W
   right_mult(h, v, W, v.opsR, 1 + K, K, false, WB, slab, prec);
   left_mult(h, v, W, v.opsL, 1, K, false, AW, slab, prec);
   // trace_r(T, Y)[l,l'] = sum_{p,r} T[p,l,r] Y[p,l',r];  trace_l(T, Y)[r,r'] = sum_{p,l} T[p,l,r] Y[p,l,r']
-  auto tr_r = [&](const double* Tt, ll tb0, const double* Y, ll yb0) {
+  auto tr_r = [&](TP Tt, ll tb0, TP Y, ll yb0) {
     return grp(op(Tt, v.n, 1, v.n2, tb0, v.Pn2), op(Y, v.n, 1, v.n2, yb0, v.Pn2), v.n, v.P);
   };
-  auto tr_l = [&](const double* Tt, ll tb0, const double* Y, ll yb0) {
+  auto tr_l = [&](TP Tt, ll tb0, TP Y, ll yb0) {
     return grp(op(Tt, 1, v.n, v.n2, tb0, v.Pn2), op(Y, 1, v.n, v.n2, yb0, v.Pn2), v.n, v.P);
   };
-  double* out = I.adj[t];
+  double* out = I.adj[t];    // FP64 output
   const ll n2 = v.n2;
   if (!I.per_node) {
     GemmDesc r = desc(v.n, v.n, 1, 1, out, v.n, 1, 0, 0);
@@ -632,9 +671,15 @@ void descend(ttn_ctx* h, Instance& I, int t, int prec) {
     add(q2, tr_r(W, 0, Yt + (1 + K) * slab, slab));
     run(h, q2, prec);
   }
+  if (v.f32 && !h->measuring) h->launches += to_f32(I.adj[t], I.adj32[t], I.op_elems(t), h->stream);
 }
 
 void forward(ttn_ctx* h, Instance& I, int prec) {
+  if (prec != 0 && !h->measuring) {
+    // FP32 copies of the layer-0 operators and of every isometry
+    h->launches += to_f32(I.ops[0], I.ops32[0], I.op_elems(0), h->stream);
+    for (int t = 0; t < I.T; ++t) h->launches += to_f32(I.W[t], I.w32[t], I.w_elems(t), h->stream);
+  }
   for (int t = 0; t < I.T; ++t) ascend_layer(h, I, t, prec);
 }
 
@@ -643,6 +688,8 @@ void sweep_instance(ttn_ctx* h, Instance& I) {
   forward(h, I, prec);
   top_solve(h, I, I.E);
   top_adjoints(h, I);
+  if (prec != 0 && !h->measuring)
+    h->launches += to_f32(I.adj[I.T], I.adj32[I.T], I.op_elems(I.T), h->stream);
   for (int t = I.T - 1; t >= 0; --t) {
     environment(h, I, t, prec, h->Gam);
     polar(h, I, t, prec, h->Gam);
@@ -665,8 +712,12 @@ void layout(ttn_ctx* h, Arena& ar) {
     I.W.assign(I.T, nullptr);
     I.ops.assign(I.T + 1, nullptr);
     I.adj.assign(I.T + 1, nullptr);
+    I.w32.assign(I.T, nullptr);
+    I.ops32.assign(I.T + 1, nullptr);
+    I.adj32.assign(I.T + 1, nullptr);
     for (int t = 0; t < I.T; ++t) {
       I.W[t] = ar.take(I.w_elems(t));
+      if (h->opt.prec != 0) I.w32[t] = reinterpret_cast<float*>(ar.take((I.w_elems(t) + 1) / 2));
       slab_max = std::max(slab_max, I.w_elems(t));
       pp_max = std::max(pp_max, (size_t)I.nodes(t) * I.chis[t + 1] * I.chis[t + 1]);
       nj_max = std::max(nj_max, (size_t)I.nodes(t));
@@ -676,6 +727,10 @@ void layout(ttn_ctx* h, Arena& ar) {
       I.ops[t] = ar.take(I.op_elems(t));
       I.adj[t] = ar.take(I.op_elems(t));
       I.eoff[t] = ar.take(I.sites(t));
+      if (h->opt.prec != 0) {
+        I.ops32[t] = reinterpret_cast<float*>(ar.take((I.op_elems(t) + 1) / 2));
+        I.adj32[t] = reinterpret_cast<float*>(ar.take((I.op_elems(t) + 1) / 2));
+      }
     }
     const int c = I.chis[I.T];
     I.V = ar.take((size_t)c * c);
@@ -911,12 +966,12 @@ int ttn_set_isometries(ttn_t h, int inst, const double* w, const double* v) {
   size_t off = 0;
   for (int t = 0; t < I.T; ++t) {
     int rc = check_cuda(h, cudaMemcpyAsync(I.W[t], w + off, I.w_elems(t) * sizeof(double),
-                                           cudaMemcpyHostToDevice, h->stream), "set w");
+                                           cudaMemcpyDefault, h->stream), "set w");
     if (rc) return rc;
     off += I.w_elems(t);
   }
   const size_t c2 = (size_t)I.chis[I.T] * I.chis[I.T];
-  int rc = check_cuda(h, cudaMemcpyAsync(I.V, v, c2 * sizeof(double), cudaMemcpyHostToDevice,
+  int rc = check_cuda(h, cudaMemcpyAsync(I.V, v, c2 * sizeof(double), cudaMemcpyDefault,
                                          h->stream), "set v");
   if (rc) return rc;
   return check_cuda(h, cudaStreamSynchronize(h->stream), "set sync");
@@ -928,13 +983,13 @@ int ttn_get_isometries(ttn_t h, int inst, double* w, double* v) {
   size_t off = 0;
   for (int t = 0; t < I.T && w; ++t) {
     int rc = check_cuda(h, cudaMemcpyAsync(w + off, I.W[t], I.w_elems(t) * sizeof(double),
-                                           cudaMemcpyDeviceToHost, h->stream), "get w");
+                                           cudaMemcpyDefault, h->stream), "get w");
     if (rc) return rc;
     off += I.w_elems(t);
   }
   if (v) {
     const size_t c2 = (size_t)I.chis[I.T] * I.chis[I.T];
-    int rc = check_cuda(h, cudaMemcpyAsync(v, I.V, c2 * sizeof(double), cudaMemcpyDeviceToHost,
+    int rc = check_cuda(h, cudaMemcpyAsync(v, I.V, c2 * sizeof(double), cudaMemcpyDefault,
                                            h->stream), "get v");
     if (rc) return rc;
   }
@@ -1085,7 +1140,7 @@ int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
     run(h, d, 0);
   }
   for (int t = I.T - 1; t >= site_layer; --t) {
-    const LayerView v = view(I, t);
+    const LayerView v = view(I, t, 0);
     GemmDesc g = desc(v.P, (int)v.n2, 1, 1, h->Yt, v.n2, 1, 0, 0);
     add(g, grp(op(rho, v.P, 1), op(I.W[t], 1, v.n2), v.P));
     run(h, g, 0);
@@ -1101,13 +1156,36 @@ int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
 int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
   if (!h || !d_out || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
   Instance& I = h->inst[inst];
-  if (layer < 0 || layer >= I.T) return fail(h, TTN_EINVAL, "bad layer");
+  if (layer < -1 || layer > I.T) return fail(h, TTN_EINVAL, "bad layer");
   sync_user(h);
-  adjoints_only(h, I, layer + 1);
-  environment(h, I, layer, 0, h->Gam);
-  int rc = check_cuda(h, cudaMemcpyAsync(d_out, h->Gam, I.w_elems(layer) * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, h->stream), "env");
-  if (rc) return rc;
+  const int c = I.chis[I.T];
+  const ll c2 = (ll)c * c;
+  if (layer == I.T) {
+    // top: dE/dV = 2 H_top V (H_top symmetric)
+    forward(h, I, 0);
+    top_matvec(h, I, I.V, h->lz_w, nullptr);
+    h->launches += axpby(h->lz_w, d_out, c2, 2.0, 0.0, h->stream);
+    return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+  }
+  adjoints_only(h, I, layer < 0 ? 0 : layer + 1);
+  if (layer >= 0) {
+    environment(h, I, layer, 0, h->Gam);
+    int rc = check_cuda(h, cudaMemcpyAsync(d_out, h->Gam, I.w_elems(layer) * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, h->stream), "env");
+    if (rc) return rc;
+    return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+  }
+  // all layers, concatenated as ttn_set_isometries lays them out, then the top
+  size_t off = 0;
+  for (int t = 0; t < I.T; ++t) {
+    environment(h, I, t, 0, h->Gam);
+    int rc = check_cuda(h, cudaMemcpyAsync(d_out + off, h->Gam, I.w_elems(t) * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, h->stream), "env");
+    if (rc) return rc;
+    off += I.w_elems(t);
+  }
+  top_matvec(h, I, I.V, h->lz_w, nullptr);
+  h->launches += axpby(h->lz_w, d_out + off, c2, 2.0, 0.0, h->stream);
   return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
 }
 

@@ -23,9 +23,9 @@ def test_tensor_core_engine_matches_fp64(prec):
     lib = _abi.load()
     nbytes = lib.ttn_selftest_bytes()
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    out = np.zeros(9)
+    out = np.zeros(11)
     rc = lib.ttn_selftest_gemm(ctypes.c_void_p(ws.data_ptr()), nbytes, prec,
-                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 9,
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 11,
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     print("prec", prec, "relative errors per case", out)
     assert rc == 0
