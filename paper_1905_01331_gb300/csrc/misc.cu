@@ -179,8 +179,12 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
 __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const int* tdim, int jmax,
                                double* y, double* theta, double* res, int* conv, double tol,
                                const int* skip_before) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // one warp: 32-way multisection of the Gershgorin interval for the lowest
+  // eigenvalue (each lane counts eigenvalues below its own point), then lane 0
+  // runs the inverse iteration
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   if (*conv) return;
+  const int lane = threadIdx.x;
   const int m = *tdim;
   double lo = alpha[0], hi = alpha[0];
   for (int i = 0; i < m; ++i) {
@@ -188,11 +192,18 @@ __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const in
     lo = fmin(lo, alpha[i] - r);
     hi = fmax(hi, alpha[i] + r);
   }
-  for (int it = 0; it < 120; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi || hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
-    if (sturm_count(alpha, beta, m, mid) >= 1) hi = mid; else lo = mid;
+  for (int it = 0; it < 16; ++it) {
+    if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    const double pt = lo + (hi - lo) * (lane + 1) / 33.0;
+    const unsigned below = __ballot_sync(0xffffffffu, sturm_count(alpha, beta, m, pt) >= 1);
+    // first lane whose point has the lowest eigenvalue below it
+    const int f = below ? __ffs(below) - 1 : 32;
+    const double nlo = f == 0 ? lo : lo + (hi - lo) * f / 33.0;
+    const double nhi = f == 32 ? hi : lo + (hi - lo) * (f + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double th = 0.5 * (lo + hi);
   // inverse iteration on (T - th I) x = x_prev, 3 rounds
   double x[128], dd[128], du[128], du2[128], rhs[128];

@@ -1073,6 +1073,11 @@ int ttn_ascend(ttn_t h, int inst, int site_layer, int prec, double* host_out) {
   Instance& I = h->inst[inst];
   if (site_layer < 0 || site_layer > I.T || prec < 0 || prec > 4) return fail(h, TTN_EINVAL, "bad layer");
   sync_user(h);
+  if (prec != 0) {
+    if (I.w32.empty() || !I.w32[0]) return fail(h, TTN_EINVAL, "context was created for FP64 only");
+    h->launches += to_f32(I.ops[0], I.ops32[0], I.op_elems(0), h->stream);
+    for (int t = 0; t < site_layer; ++t) h->launches += to_f32(I.W[t], I.w32[t], I.w_elems(t), h->stream);
+  }
   for (int t = 0; t < site_layer; ++t) ascend_layer(h, I, t, prec);
   std::vector<double> e(I.sites(site_layer));
   int rc = check_cuda(h, cudaMemcpyAsync(host_out, I.ops[site_layer], I.op_elems(site_layer) * sizeof(double),
