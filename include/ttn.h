@@ -77,7 +77,7 @@ typedef struct {
   int top_mode;             /* 0: lowest eigenvector of the top Hamiltonian */
   double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-13) */
   int lanczos_max;          /* Krylov dimension per restart (default 48) */
-  int lanczos_restarts;     /* restarts per sweep (default 3) */
+  int lanczos_restarts;     /* restarts per sweep (default 2) */
   double shift;             /* bond shift c; NaN = lambda_max of the bond term */
   double polar_damping;     /* proximal weight mu of the update (default 1e-7) */
   int deterministic;        /* 1: fixed-order reductions (always on) */

@@ -34,7 +34,7 @@ class Sweeper:
     """
 
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
-                 lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
+                 lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=2,
                  polar_damping=1e-7, use_graph=True, shift=None):
         import torch
         self._torch = torch

@@ -42,6 +42,9 @@ struct GemmDesc {
   int prec;          // ttn_precision of the products
   const int* skip;   // if non-null and *skip != 0 the launch does nothing
   int* err;          // device flag raised when a bounded wait of a kernel expires
+  int sym;           // C = A A^T (symmetric, M == N): only tiles on or above the
+                     // diagonal are computed and mirrored (FP64 engine)
+  int sym_tile;      // tile size the launcher used (set by the launcher)
 };
 
 // Launch one grouped product on `stream` (FP64 CUDA-core kernel or tcgen05
@@ -100,9 +103,14 @@ int split_identity(double* O, long long stride, int P, int nodes, const double* 
 // Z and W are FP32 when f32 != 0, else FP64.
 int add_identity_part(void* Z, const void* W, int f32, long long elems, int nodes,
                       const double* e_in, int per_node, double coef, cudaStream_t s);
-// *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add.
-int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
-                   cudaStream_t s);
+// out = 2 (w + (e[0] + e[per_node ? 1 : 0]) v): dE/dv with w = H_top v of the
+// identity-free operators.
+int top_grad(double* out, const double* w, const double* v, long long n, const double* e,
+             int per_node, cudaStream_t s);
+// *out = dot[0] + (e[0] + e[per_node ? 1 : 0]) * vv[0] + add: the energy
+// <v, H_top v> + cL with the identity part of the top operators restored.
+int top_energy_sum(const double* dot, const double* vv, const double* e, int per_node, double add,
+                   double* out, cudaStream_t s);
 
 // dst[i] = (float) src[i]
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s);

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
 
   const int tiles_n = (d.N + BN - 1) / BN;
   const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  if (d.sym && tm > tn) return;      // symmetric product: the mirror tile fills it
   const int b = blockIdx.y;
   const int b0 = b % d.B0, b1 = b / d.B0;
   const int split = blockIdx.z;
@@ -118,7 +119,10 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-        if (m < d.M && n < d.N) st_out(d, cb + m * d.sc_m + n * d.sc_n, acc[i][j]);
+        if (m < d.M && n < d.N) {
+          st_out(d, cb + m * d.sc_m + n * d.sc_n, acc[i][j]);
+          if (d.sym && tm < tn) st_out(d, cb + n * d.sc_m + m * d.sc_n, acc[i][j]);
+        }
       }
   } else {
     const long long MN = (long long)d.M * d.N;
@@ -142,8 +146,10 @@ __global__ void splitk_reduce_kernel(const GemmDesc d) {
        e += (long long)gridDim.x * blockDim.x) {
     const long long b = e / MN, r = e % MN;
     const int m = (int)(r / d.N), n = (int)(r % d.N);
+    // symmetric product: below-diagonal tiles were not computed; read the mirror
+    const long long src = (d.sym && m / d.sym_tile > n / d.sym_tile) ? (long long)n * d.N + m : r;
     double s = 0.0;
-    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
+    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + src];
     const int b0 = (int)(b % d.B0), b1 = (int)(b / d.B0);
     st_out(d, b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n, s);
   }
@@ -197,6 +203,8 @@ int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.B0 * d.B1 <= 0) return 0;
   int n = 0;
   const int t = f64_tile(d);
+  d.sym_tile = t;
+  if (d.sym && d.M != d.N) d.sym = 0;
   if (t == 64) n += launch_tile<64, 64>(d, s);
   else if (t == 32) n += launch_tile<32, 32>(d, s);
   else n += launch_tile<16, 16>(d, s);

@@ -175,6 +175,32 @@ __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
   }
 }
 
+// N consecutive values (N = 4 or 8) with 16-byte loads when aligned.
+template <typename T, int N>
+__device__ __forceinline__ void ldv(const T* p, T* out) {
+  if constexpr (sizeof(T) == 4) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+      for (int i = 0; i < N; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p + i);
+        out[i] = t.x; out[i + 1] = t.y; out[i + 2] = t.z; out[i + 3] = t.w;
+      }
+      return;
+    }
+  } else {
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+      for (int i = 0; i < N; i += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(p + i);
+        out[i] = t.x; out[i + 1] = t.y;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[i] = p[i];
+}
+
 __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
   if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
     const float2 t = *reinterpret_cast<const float2*>(p);
@@ -200,24 +226,35 @@ __device__ __forceinline__ void stage_operand_t(const Operand& o, int k0_log2, l
   if (slice && o.s_k0 == 1) {
     const T* tb = static_cast<const T*>(o.p) + base +
                   static_cast<long long>(kb >> k0_log2) * o.s_k1 + (kb & (K0 - 1));
-    for (int task = threadIdx.x; task < ROWS * NCH; task += kThreadsTC) {
-      const int r = task / NCH, c = task % NCH;
-      uint32_t h[CH], l[CH];
-      if (r < nrows_valid) {
-        const T* src = tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH;
+    // all loads of a group of tasks are issued before any conversion, so that
+    // a thread has several 16-byte loads in flight
+    constexpr int TASKS = (ROWS * NCH + kThreadsTC - 1) / kThreadsTC;
+    constexpr int GRP = (sizeof(T) * CH <= 16) ? 4 : 2;
 #pragma unroll
-        for (int q = 0; q < CH; q += 2) {
-          T a, b;
-          ld2(src + q, a, b);
-          split<kBF16>(a, h[q], l[q]);
-          split<kBF16>(b, h[q + 1], l[q + 1]);
+    for (int g0 = 0; g0 < TASKS; g0 += GRP) {
+      T v[GRP][CH];
+#pragma unroll
+      for (int i = 0; i < GRP; ++i) {
+        const int task = threadIdx.x + (g0 + i) * kThreadsTC;
+        const int r = task / NCH, c = task % NCH;
+        if (g0 + i < TASKS && task < ROWS * NCH && r < nrows_valid) {
+          ldv<T, CH>(tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH, v[i]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < CH; ++q) v[i][q] = T(0);
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < CH; ++q) { h[q] = 0u; l[q] = 0u; }
       }
-      st_chunk<kBF16>(hi_tile, r, c * CH, h);
-      if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r, c * CH, l);
+#pragma unroll
+      for (int i = 0; i < GRP; ++i) {
+        const int task = threadIdx.x + (g0 + i) * kThreadsTC;
+        if (g0 + i >= TASKS || task >= ROWS * NCH) continue;
+        const int r = task / NCH, c = task % NCH;
+        uint32_t h[CH], l[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) split<kBF16>(v[i][q], h[q], l[q]);
+        st_chunk<kBF16>(hi_tile, r, c * CH, h);
+        if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r, c * CH, l);
+      }
     }
     return;
   }
@@ -229,29 +266,24 @@ __device__ __forceinline__ void stage_operand_t(const Operand& o, int k0_log2, l
     for (int task = threadIdx.x; task < (ROWS / 4) * NCH; task += kThreadsTC) {
       const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
       const int r = rq * 4;
-      uint32_t h[4][CH], l[4][CH];
+      T v[CH][4];
       if (r < nrows_valid) {
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          const T* src = tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r);
-          T v0, v1, v2, v3;
-          ld2(src, v0, v1);
-          ld2(src + 2, v2, v3);
-          split<kBF16>(v0, h[0][q], l[0][q]);
-          split<kBF16>(v1, h[1][q], l[1][q]);
-          split<kBF16>(v2, h[2][q], l[2][q]);
-          split<kBF16>(v3, h[3][q], l[3][q]);
-        }
+        for (int q = 0; q < CH; ++q)
+          ldv<T, 4>(tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r), v[q]);
       } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int q = 0; q < CH; ++q)
 #pragma unroll
-          for (int q = 0; q < CH; ++q) { h[i][q] = 0u; l[i][q] = 0u; }
+          for (int i = 0; i < 4; ++i) v[q][i] = T(0);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        st_chunk<kBF16>(hi_tile, r + i, c * CH, h[i]);
-        if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r + i, c * CH, l[i]);
+        uint32_t h[CH], l[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) split<kBF16>(v[q][i], h[q], l[q]);
+        st_chunk<kBF16>(hi_tile, r + i, c * CH, h);
+        if constexpr (kSplit) st_chunk<kBF16>(lo_tile, r + i, c * CH, l);
       }
     }
     return;

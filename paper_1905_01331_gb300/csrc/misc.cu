@@ -334,9 +334,19 @@ __global__ void add_identity_kernel(T* Z, const T* W, long long elems, const dou
     Z[J * elems + i] += static_cast<T>(c) * W[J * elems + i];
 }
 
-__global__ void top_energy_kernel(const double* dot, const double* e, int per_node, double add,
-                                  double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = dot[0] + e[0] + e[per_node ? 1 : 0] + add;
+// out = 2 (w + (e_0 + e_1) v): gradient of <v, H_top v> with the identity part
+__global__ void top_grad_kernel(double* out, const double* w, const double* v, long long n,
+                                const double* e, int per_node) {
+  const double sh = e[0] + e[per_node ? 1 : 0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = 2.0 * (w[i] + sh * v[i]);
+}
+
+__global__ void top_energy_kernel(const double* dot, const double* vv, const double* e,
+                                  int per_node, double add, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *out = dot[0] + (e[0] + e[per_node ? 1 : 0]) * vv[0] + add;
 }
 
 __global__ void to_f32_kernel(const double* src, float* dst, long long n) {
@@ -474,9 +484,15 @@ int add_identity_part(void* Z, const void* W, int f32, long long elems, int node
   return 1;
 }
 
-int top_energy_sum(const double* dot, const double* e, int per_node, double add, double* out,
-                   cudaStream_t s) {
-  top_energy_kernel<<<1, 32, 0, s>>>(dot, e, per_node, add, out);
+int top_grad(double* out, const double* w, const double* v, long long n, const double* e,
+             int per_node, cudaStream_t s) {
+  top_grad_kernel<<<grid_for(n), 256, 0, s>>>(out, w, v, n, e, per_node);
+  return 1;
+}
+
+int top_energy_sum(const double* dot, const double* vv, const double* e, int per_node, double add,
+                   double* out, cudaStream_t s) {
+  top_energy_kernel<<<1, 32, 0, s>>>(dot, vv, e, per_node, add, out);
   return 1;
 }
 

@@ -430,8 +430,9 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
   // energy = <V, H V> + c L
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
-  h->launches += top_energy_sum(h->scal + 4, I.eoff[I.T], I.per_node ? 1 : 0, I.c * I.L,
-                                energy_out, h->stream);
+  h->launches += batched_dot(I.V, I.V, n, 0, 1, h->scal + 6, h->red, h->stream);
+  h->launches += top_energy_sum(h->scal + 4, h->scal + 6, I.eoff[I.T], I.per_node ? 1 : 0,
+                                I.c * I.L, energy_out, h->stream);
 }
 
 void energy_only(ttn_ctx* h, Instance& I, double* energy_out) {
@@ -439,8 +440,9 @@ void energy_only(ttn_ctx* h, Instance& I, double* energy_out) {
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   if (h->measuring) return;
   h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
-  h->launches += top_energy_sum(h->scal + 4, I.eoff[I.T], I.per_node ? 1 : 0, I.c * I.L,
-                                energy_out, h->stream);
+  h->launches += batched_dot(I.V, I.V, n, 0, 1, h->scal + 6, h->red, h->stream);
+  h->launches += top_energy_sum(h->scal + 4, h->scal + 6, I.eoff[I.T], I.per_node ? 1 : 0,
+                                I.c * I.L, energy_out, h->stream);
 }
 
 // Top adjoints: R = V V^T + V^T V, P_k = V B_k V^T + V^T B_k V, Q_k = V^T A_k V + V A_k V^T
@@ -565,14 +567,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // Gram matrices and two long compositions.
   const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
   for (const PolarBlock& blk : sched) {
-    // A = X X^T
+    // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
     add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
+    g.sym = 1;
     run(h, g, 0);
-    if (!h->measuring) {
-      h->launches += symmetrize(h->pA, P, NJ, h->stream);
-      h->launches += set_identity(h->pF, P, NJ, h->stream);
-    }
+    if (!h->measuring) h->launches += set_identity(h->pF, P, NJ, h->stream);
     for (size_t j = 0; j < blk.steps.size(); ++j) {
       if (!h->measuring)
         h->launches += poly_step_matrix(h->pA, h->pP, P, NJ, blk.steps[j].first,
@@ -850,7 +850,7 @@ void ttn_default_options(ttn_options* o) {
   o->top_mode = 0;
   o->lanczos_tol = 1e-13;
   o->lanczos_max = 48;
-  o->lanczos_restarts = 3;
+  o->lanczos_restarts = 2;
   o->shift = NAN;
   o->polar_damping = 1e-7;
   o->deterministic = 1;
@@ -1169,7 +1169,7 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
     // top: dE/dV = 2 H_top V (H_top symmetric)
     forward(h, I, 0);
     top_matvec(h, I, I.V, h->lz_w, nullptr);
-    h->launches += axpby(h->lz_w, d_out, c2, 2.0, 0.0, h->stream);
+    h->launches += top_grad(d_out, h->lz_w, I.V, c2, I.eoff[I.T], I.per_node ? 1 : 0, h->stream);
     return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
   }
   adjoints_only(h, I, layer < 0 ? 0 : layer + 1);
@@ -1190,7 +1190,8 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
     off += I.w_elems(t);
   }
   top_matvec(h, I, I.V, h->lz_w, nullptr);
-  h->launches += axpby(h->lz_w, d_out + off, c2, 2.0, 0.0, h->stream);
+  h->launches += top_grad(d_out + off, h->lz_w, I.V, c2, I.eoff[I.T], I.per_node ? 1 : 0,
+                          h->stream);
   return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
 }
 

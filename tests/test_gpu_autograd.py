@@ -42,25 +42,47 @@ def test_autograd_matches_oracle_environment():
 
 
 def test_autograd_finite_differences():
-    """<dE/dw, D> against (E(w + eps D) - E(w - eps D)) / 2 eps, five random
-    directions per layer (the energy is quadratic in each w, so central
-    differences are exact up to rounding)."""
+    """Central finite differences of the energy along curves that keep every
+    isometry exact -- w(eps) = expm(eps A) w and w expm(eps B) with random
+    antisymmetric A (parent leg) and B (child legs) -- against <dE/dw, dw/deps>,
+    five directions per layer; and along v for the top tensor."""
+    import scipy.linalg as sla
     import torch
     from paper_1905_01331_gb300.autograd import energy
     s, st, tw, tv = _setup()
     E = energy(s, 0, tv, tw)
     E.backward()
-    gen = torch.Generator(device="cuda").manual_seed(0)
-    eps = 1e-5
+    rng = np.random.default_rng(0)
+    eps = 1e-4
     for t in range(len(tw)):
-        for _ in range(5):
-            D = torch.randn(tw[t].shape, dtype=torch.float64, device="cuda", generator=gen)
-            with torch.no_grad():
-                wp = [w.detach().clone() for w in tw]
-                wm = [w.detach().clone() for w in tw]
-                wp[t] += eps * D
-                wm[t] -= eps * D
-                fd = (energy(s, 0, tv.detach(), wp) - energy(s, 0, tv.detach(), wm)).item() / (2 * eps)
-            an = float((tw[t].grad * D).sum())
-            assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (t, fd, an)
+        w0 = tw[t].detach().cpu().numpy()
+        P, n = w0.shape[0], w0.shape[1]
+        W0 = w0.reshape(P, n * n)
+        g = tw[t].grad.cpu().numpy().reshape(P, n * n)
+        for d in range(5):
+            if d % 2 == 0:
+                X = rng.standard_normal((P, P)); A = X - X.T
+                curve = lambda e: sla.expm(e * A) @ W0
+                tangent = A @ W0
+            else:
+                X = rng.standard_normal((n * n, n * n)); Bm = X - X.T
+                curve = lambda e: W0 @ sla.expm(e * Bm)
+                tangent = W0 @ Bm
+            def E_at(e):
+                ws = [w.detach().clone() for w in tw]
+                ws[t] = torch.tensor(curve(e).reshape(w0.shape), device="cuda")
+                with torch.no_grad():
+                    return energy(s, 0, tv.detach(), ws).item()
+            fd = (E_at(eps) - E_at(-eps)) / (2 * eps)
+            an = float(np.sum(g * tangent))
+            assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (t, d, fd, an)
+    # top tensor: any direction (v enters the energy as <v, H v>)
+    gv = tv.grad.cpu().numpy()
+    D = rng.standard_normal(gv.shape)
+    def Ev(e):
+        with torch.no_grad():
+            return energy(s, 0, tv.detach() + e * torch.tensor(D, device="cuda"),
+                          [w.detach() for w in tw]).item()
+    fd = (Ev(eps) - Ev(-eps)) / (2 * eps)
+    assert abs(fd - float(np.sum(gv * D))) < 1e-6 * max(1.0, abs(fd))
     s.close()
