@@ -48,6 +48,11 @@ def parse():
     p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
+    p.add_argument("--workload", default="tfim1024",
+                   choices=["tfim1024", "batched64", "paper-torus"],
+                   help="tfim1024: the headline line; batched64: 64 independent chains in one "
+                        "context; paper-torus: the paper's 128 x 5 torus at h = 2.9 with its "
+                        "entanglement spectrum")
     return p.parse_args()
 
 
@@ -383,8 +388,71 @@ def run_profile_only(args):
     s.close()
 
 
+def run_batched(args):
+    """64 independent TFIM chains (h ~ U[0.5,1.5], L ~ {64..512}, chi ~ {32,64,128},
+    seed 4) advanced together in one context and one captured sweep."""
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+    wls = ti.batched_chains()
+    s = Sweeper([w.model for w in wls], [w.chi for w in wls], prec=args.prec)
+    for i, w in enumerate(wls):
+        s.set_isometries(i, *ti.initial_tensors(w.model.Lx, 2, w.chi, w.seed))
+    s.sweep(args.warmup)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    s.sweep_async(args.steps)
+    b.record(s.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    print(json.dumps({"metric": "batched TTN sweeps/s (64 independent chains, instance-sweeps)",
+                      "value": len(wls) * args.steps / (ms * 1e-3), "unit": "instance-sweeps/s",
+                      "ms_per_step": ms / args.steps, "steps": args.steps, "warmup": args.warmup,
+                      "precision": args.prec, "instances": len(wls),
+                      "gpu_launches": s.launch_count}))
+    s.close()
+
+
+def run_paper_torus(args):
+    """The paper's workload (Sec. IV): 128 x 5 thin torus, h = 2.9, d0 = 32,
+    K = 5; energy per spin and the entanglement spectrum / entropy of the
+    block of 2^6 columns (site layer 6, leftmost site)."""
+    import numpy as np
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+    m = ti.tfim_torus(128, 5, 2.9)
+    chi = args.chi
+    ws, V = ti.initial_tensors(128, m.d0, chi, 5)
+    s = Sweeper(m, chi, prec=args.prec)
+    s.set_isometries(0, ws, V)
+    t0 = time.perf_counter()
+    E = s.sweep(args.steps)[:, 0]
+    dt = time.perf_counter() - t0
+    E_cert = s.energy(0)
+    rho = s.rdm(0, 6, which=1)
+    p = np.clip(np.linalg.eigvalsh(0.5 * (rho + rho.T))[::-1], 1e-300, None)
+    lam = -np.log2(p)
+    S = float(-np.sum(p * np.log2(p)))
+    print(json.dumps({"workload": "paper torus 128x5 h=2.9", "chi": chi, "precision": args.prec,
+                      "sweeps": args.steps, "sweeps_per_s": args.steps / dt,
+                      "energy_per_spin_fp64": E_cert / m.n_spins,
+                      "energy_per_spin_last_sweeps": (E[-3:] / m.n_spins).tolist(),
+                      "paper_e_inf": -3.11229, "entanglement_spectrum_tau6_first30": lam[:30].tolist(),
+                      "entropy_tau6": S}))
+    s.close()
+
+
 def main():
     args = parse()
+    if args.workload == "batched64":
+        run_batched(args)
+        return
+    if args.workload == "paper-torus":
+        run_paper_torus(args)
+        return
     if args.profile_sweeps:
         run_profile_only(args)
         return

@@ -74,10 +74,13 @@ typedef struct {
 
 typedef struct {
   int prec;                 /* ttn_precision */
-  int top_mode;             /* 0: lowest eigenvector of the top Hamiltonian */
+  int top_mode;             /* 0: lowest eigenvector of the top Hamiltonian;
+                               1: v <- -H_top v / |H_top v| (minus the polar
+                               factor of v's environment, the literal reading
+                               of "updated similarly", Sec. III.B) */
   double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-13) */
   int lanczos_max;          /* Krylov dimension per restart (default 48) */
-  int lanczos_restarts;     /* restarts per sweep (default 2) */
+  int lanczos_restarts;     /* restarts per sweep (default 3) */
   double shift;             /* bond shift c; NaN = lambda_max of the bond term */
   double polar_damping;     /* proximal weight mu of the update (default 1e-7) */
   int deterministic;        /* 1: fixed-order reductions (always on) */

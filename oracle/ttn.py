@@ -426,15 +426,29 @@ def solve_top(st, F_top):
     return top_ground(*F_top, V_prev=st.V)
 
 
-def sweep(st):
+def top_polar_step(st, F_top):
+    """The literal reading of "the top tensor v is updated similarly" (Sec.
+    III.B): v <- minus the polar factor of its environment.  The environment of
+    v is H_top v (dE/dv = 2 H_top v); the polar factor of a single vector is
+    the vector normalised, so v <- -H_top v / |H_top v|.  With the shifted
+    (negative semidefinite) Hamiltonian this is one power-iteration step toward
+    the lowest eigenvector."""
+    f = top_apply_nodes if st.per_node else top_apply
+    g = f(st.V, *F_top)
+    return -g / np.linalg.norm(g)
+
+
+def sweep(st, top_mode=0):
     """One sweep (Sec. III): ascend, top solve, then top-down updates.
 
     Returns the energy found by the top solve (the energy of the state made of
     the isometries at the start of the sweep and the new top tensor).
+    top_mode 0: the top tensor is the lowest eigenvector of H_top; 1: one
+    polar step of its environment (``top_polar_step``).
     """
     Fs = ascend_all(st)
     T = len(st.ws)
-    V = solve_top(st, Fs[T])
+    V = solve_top(st, Fs[T]) if top_mode == 0 else top_polar_step(st, Fs[T])
     E = top_energy(st, V, Fs[T])
     st.V = V
     if st.per_node:

@@ -107,6 +107,9 @@ int add_identity_part(void* Z, const void* W, int f32, long long elems, int node
 // identity-free operators.
 int top_grad(double* out, const double* w, const double* v, long long n, const double* e,
              int per_node, cudaStream_t s);
+// y = sign * x / sqrt(nrm2[0]).
+int scale_normalise(const double* x, double* y, long long n, const double* nrm2, double sign,
+                    cudaStream_t s);
 // *out = dot[0] + (e[0] + e[per_node ? 1 : 0]) * vv[0] + add: the energy
 // <v, H_top v> + cL with the identity part of the top operators restored.
 int top_energy_sum(const double* dot, const double* vv, const double* e, int per_node, double add,

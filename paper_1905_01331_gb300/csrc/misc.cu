@@ -343,6 +343,14 @@ __global__ void top_grad_kernel(double* out, const double* w, const double* v, l
     out[i] = 2.0 * (w[i] + sh * v[i]);
 }
 
+__global__ void scale_normalise_kernel(const double* x, double* y, long long n, const double* nrm2,
+                                       double sign) {
+  const double f = sign / sqrt(nrm2[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = f * x[i];
+}
+
 __global__ void top_energy_kernel(const double* dot, const double* vv, const double* e,
                                   int per_node, double add, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0)
@@ -481,6 +489,12 @@ int add_identity_part(void* Z, const void* W, int f32, long long elems, int node
     add_identity_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(Z),
                                                      static_cast<const double*>(W), elems, e_in,
                                                      per_node, coef);
+  return 1;
+}
+
+int scale_normalise(const double* x, double* y, long long n, const double* nrm2, double sign,
+                    cudaStream_t s) {
+  scale_normalise_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, nrm2, sign);
   return 1;
 }
 

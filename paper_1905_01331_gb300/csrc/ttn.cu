@@ -394,6 +394,21 @@ void top_matvec(ttn_ctx* h, Instance& I, const double* x, double* w, const int* 
 void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
   const int T = I.T, c = I.chis[T];
   const ll n = (ll)c * c;
+  if (h->opt.top_mode == 1) {
+    // v <- -H_top v / |H_top v|: minus the polar factor of the top tensor's
+    // environment (one power step with the negative semidefinite H_top)
+    top_matvec(h, I, I.V, h->lz_w, nullptr);
+    if (h->measuring) { top_matvec(h, I, I.V, h->lz_w, nullptr); return; }
+    h->launches += top_grad(h->lz_tmp, h->lz_w, I.V, n, I.eoff[T], I.per_node ? 1 : 0, h->stream);
+    h->launches += batched_dot(h->lz_tmp, h->lz_tmp, n, 0, 1, h->scal, h->red, h->stream);
+    h->launches += scale_normalise(h->lz_tmp, I.V, n, h->scal, -1.0, h->stream);
+    top_matvec(h, I, I.V, h->lz_w, nullptr);
+    h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
+    h->launches += batched_dot(I.V, I.V, n, 0, 1, h->scal + 6, h->red, h->stream);
+    h->launches += top_energy_sum(h->scal + 4, h->scal + 6, I.eoff[I.T], I.per_node ? 1 : 0,
+                                  I.c * I.L, energy_out, h->stream);
+    return;
+  }
   const int m = (int)std::min<ll>(h->lz_m, n);
   int* skip = h->iflags;
   int* tdim = h->iflags + 1;
@@ -850,7 +865,7 @@ void ttn_default_options(ttn_options* o) {
   o->top_mode = 0;
   o->lanczos_tol = 1e-13;
   o->lanczos_max = 48;
-  o->lanczos_restarts = 2;
+  o->lanczos_restarts = 3;
   o->shift = NAN;
   o->polar_damping = 1e-7;
   o->deterministic = 1;
@@ -861,6 +876,7 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   if (!probs || n <= 0) return fail(h, TTN_EINVAL, "no problems");
   if (opt) h->opt = *opt; else ttn_default_options(&h->opt);
   if (h->opt.prec < 0 || h->opt.prec > 4) return fail(h, TTN_EINVAL, "bad precision");
+  if (h->opt.top_mode != 0 && h->opt.top_mode != 1) return fail(h, TTN_EINVAL, "top_mode is 0 or 1");
   if (h->opt.lanczos_max < 2 || h->opt.lanczos_max > 120) return fail(h, TTN_EINVAL, "lanczos_max in [2,120]");
   if (h->opt.lanczos_restarts < 1) h->opt.lanczos_restarts = 1;
   if (!(h->opt.polar_damping >= 0.0)) return fail(h, TTN_EINVAL, "polar_damping < 0");

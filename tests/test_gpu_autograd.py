@@ -61,11 +61,11 @@ def test_autograd_finite_differences():
         g = tw[t].grad.cpu().numpy().reshape(P, n * n)
         for d in range(5):
             if d % 2 == 0:
-                X = rng.standard_normal((P, P)); A = X - X.T
+                X = rng.standard_normal((P, P)); A = X - X.T; A /= np.linalg.norm(A)
                 curve = lambda e: sla.expm(e * A) @ W0
                 tangent = A @ W0
             else:
-                X = rng.standard_normal((n * n, n * n)); Bm = X - X.T
+                X = rng.standard_normal((n * n, n * n)); Bm = X - X.T; Bm /= np.linalg.norm(Bm)
                 curve = lambda e: W0 @ sla.expm(e * Bm)
                 tangent = W0 @ Bm
             def E_at(e):
@@ -79,6 +79,7 @@ def test_autograd_finite_differences():
     # top tensor: any direction (v enters the energy as <v, H v>)
     gv = tv.grad.cpu().numpy()
     D = rng.standard_normal(gv.shape)
+    D /= np.linalg.norm(D)
     def Ev(e):
         with torch.no_grad():
             return energy(s, 0, tv.detach() + e * torch.tensor(D, device="cuda"),

@@ -136,3 +136,17 @@ def test_checkpoint_resume_is_bitwise():
     c.set_state(blob)
     Eb2 = c.sweep(3)[:, 0]
     assert np.array_equal(Ea, np.concatenate([Eb1, Eb2]))
+
+
+def test_top_polar_step_mode_matches_oracle():
+    """top_mode = 1: the top tensor takes one polar step of its environment
+    per sweep (the literal reading of Sec. III.B); trajectory vs the oracle."""
+    m = ti.tfim_chain(64, 1.0)
+    ws, V = ti.initial_tensors(64, 2, 16, 4)
+    s = _sweeper(m, 16, top_mode=1)
+    s.set_isometries(0, ws, V)
+    E = s.sweep(5)[:, 0]
+    st = oracle.make_state(m, ws, V)
+    E_ref = np.array([oracle.sweep(st, top_mode=1) for _ in range(5)])
+    assert np.abs(E - E_ref).max() < 1e-10 * np.abs(E_ref).max()
+    assert np.all(np.diff(E) <= 1e-9 * np.abs(E[1:]))

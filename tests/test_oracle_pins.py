@@ -280,3 +280,20 @@ def test_planted_mistakes_are_caught(monkeypatch):
     for bad in (drop_right_term, swap_children):
         assert abs(energy_with(bad) - E_ref) > 1e-6
     assert abs(energy_with(good) - E_ref) < 1e-12
+
+
+def test_top_polar_step_is_a_power_step_and_monotone():
+    """top_mode = 1: v <- -H v/|H v| with the shifted, negative semidefinite
+    top Hamiltonian never raises <v, H v> (power iteration), and the sweep
+    energies never rise."""
+    m = ti.tfim_chain(32, 0.8)
+    st = _state(m, 6, 12)
+    Fs = ttn.ascend_all(st)
+    H = ttn.top_matrix(*Fs[-1])
+    assert np.linalg.eigvalsh(H).max() < 1e-10          # shifted: NSD
+    v0 = st.V.ravel()
+    v1 = ttn.top_polar_step(st, Fs[-1]).ravel()
+    assert abs(np.linalg.norm(v1) - 1) < 1e-14
+    assert v1 @ H @ v1 <= v0 @ H @ v0 + 1e-12
+    Es = [ttn.sweep(st, top_mode=1) for _ in range(6)]
+    assert all(b <= a + 1e-11 * abs(a) for a, b in zip(Es, Es[1:]))
