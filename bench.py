@@ -49,10 +49,10 @@ def parse():
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
     p.add_argument("--workload", default="tfim1024",
-                   choices=["tfim1024", "batched64", "paper-torus"],
+                   choices=["tfim1024", "batched64", "paper-torus", "top-mode"],
                    help="tfim1024: the headline line; batched64: 64 independent chains in one "
                         "context; paper-torus: the paper's 128 x 5 torus at h = 2.9 with its "
-                        "entanglement spectrum")
+                        "entanglement spectrum; top-mode: eigensolver vs polar-step top update")
     return p.parse_args()
 
 
@@ -445,8 +445,50 @@ def run_paper_torus(args):
     s.close()
 
 
+def run_top_mode_study(args):
+    """Top update read two ways (Sec. III.B, "updated similarly"): the exact
+    lowest eigenvector (top_mode 0) against minus the polar factor of the top
+    tensor's environment (top_mode 1), FP64, from the same seeded start:
+    energies along the sweeps and sweeps needed to come within 1e-6 (relative)
+    of the eigensolver's final energy."""
+    import numpy as np
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+    L, chi, n = 256, args.chi, args.steps
+    model = ti.tfim_chain(L, 1.0)
+    ws, V = ti.initial_tensors(L, 2, chi, 1)
+    out = {"workload": f"tfim_chain_L{L}_h1_chi{chi}", "precision": "fp64", "sweeps": n}
+    Es = {}
+    for mode in (0, 1):
+        s = Sweeper(model, chi, prec="fp64", top_mode=mode)
+        s.set_isometries(0, ws, V)
+        t0 = time.perf_counter()
+        s.sweep(n)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s.set_isometries(0, ws, V)
+        E = []
+        for _ in range(n):
+            s.sweep(1)
+            E.append(s.energy(0))
+        s.close()
+        Es[mode] = np.array(E)
+        out[f"top_mode_{mode}"] = {"sweeps_per_s": n / dt,
+                                   "energy_at": {str(k): float(Es[mode][k - 1]) for k in
+                                                 (1, 5, 10, 25, 50, 100, 200, n) if k <= n}}
+    ref = Es[0][-1]
+    for mode in (0, 1):
+        hit = np.nonzero(np.abs(Es[mode] - ref) / abs(ref) < 1e-6)[0]
+        out[f"top_mode_{mode}"]["sweeps_to_1e-6_of_eig_final"] = int(hit[0]) + 1 if len(hit) else None
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.workload == "top-mode":
+        run_top_mode_study(args)
+        return
     if args.workload == "batched64":
         run_batched(args)
         return

@@ -62,7 +62,8 @@ typedef enum {
 } ttn_precision;
 
 /* One Hamiltonian.  onesite: d0 x d0, A and B: K x d0 x d0, d0 = d^Ly, all
- * host FP64, row-major; the library copies them in ttn_create. */
+ * host FP64, row-major; the library copies them in ttn_create.  Lx and d0
+ * powers of two, d0 <= 4096, 1 <= K <= 7 product terms per bond. */
 typedef struct {
   int Lx, Ly, d, chi, K;
   int per_node;             /* 0: one isometry per layer (translation
@@ -85,6 +86,19 @@ typedef struct {
   double polar_damping;     /* proximal weight mu of the update (default 1e-7) */
   int deterministic;        /* 1: fixed-order reductions (always on) */
   int use_graph;            /* 1: capture a sweep as a CUDA graph and replay */
+  int persistent;           /* bit 0: the P x P Newton-Schulz composition of each
+                               polar block, bit 1: the Lanczos top solve, as one
+                               persistent cooperative kernel each (all SMs, grid
+                               barriers with bounded waits); a clear bit runs
+                               that step as separate launches.  Default 3 */
+  int streams;              /* instances run on min(streams, instances) concurrent
+                               streams (graph branches), each with its own
+                               scratch; default 8 */
+  int polar_blocks;         /* Newton-Schulz schedule of the polar factor: 1 = a
+                               fresh Gram matrix every <= 4 steps (accurate to
+                               FP64 rounding), 2 = two long blocks (one Gram
+                               matrix per ~1e5 of growth: half the FP64 work),
+                               0 (default) = 1 in FP64 mode, 2 in mixed modes */
 } ttn_options;
 
 /* Fill *opt with the defaults above. */

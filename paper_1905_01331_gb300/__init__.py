@@ -35,7 +35,8 @@ class Sweeper:
 
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
                  lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
-                 polar_damping=1e-7, use_graph=True, shift=None, top_mode=0):
+                 polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
+                 persistent=True, streams=8, polar_blocks=0):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -62,6 +63,9 @@ class Sweeper:
         opt.lanczos_restarts = lanczos_restarts
         opt.polar_damping = polar_damping
         opt.use_graph = int(bool(use_graph))
+        opt.persistent = 3 if persistent is True else (0 if persistent is False else int(persistent))
+        opt.streams = int(streams)
+        opt.polar_blocks = int(polar_blocks)
         opt.top_mode = int(top_mode)
         if shift is not None:
             opt.shift = float(shift)

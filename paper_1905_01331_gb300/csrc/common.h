@@ -23,7 +23,7 @@ struct Group {
   int k0_log2;  // log2 K0
 };
 
-constexpr int kMaxGroups = 20;
+constexpr int kMaxGroups = 32;   // the environment product has 1 + 4K groups: K <= 7
 
 // C[b] = alpha * sum_g A_g[b] B_g[b] + beta * C[b] for every batch b = (b0, b1).
 // The K ranges of the groups are concatenated into one reduction; `splits`
@@ -46,6 +46,8 @@ struct GemmDesc {
                      // diagonal are computed and mirrored (FP64 engine)
   int sym_tile;      // tile size the launcher used (set by the launcher)
 };
+// passed by value as a kernel parameter (limit 32764 bytes)
+static_assert(sizeof(GemmDesc) + 64 < 32764, "GemmDesc too large for a kernel parameter");
 
 // Launch one grouped product on `stream` (FP64 CUDA-core kernel or tcgen05
 // kernel by desc.prec).  Returns the number of kernel launches.
@@ -114,6 +116,70 @@ int scale_normalise(const double* x, double* y, long long n, const double* nrm2,
 // <v, H_top v> + cL with the identity part of the top operators restored.
 int top_energy_sum(const double* dot, const double* vv, const double* e, int per_node, double add,
                    double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Polar composition (polar.cu): one block of scaled Newton-Schulz steps on the
+// P x P level, F = prod_j p_j(A_j) from the Gram matrix A_0, in one
+// cooperative launch.  A0 holds A_0 on entry (exactly symmetric); A0, A1, T
+// and S are overwritten; F receives the composed polynomial.  Each of the five
+// buffers holds NJ P x P blocks.  bar is a device counter the launcher zeroes;
+// err is raised (|= 2) if a grid barrier wait expires.
+// ---------------------------------------------------------------------------
+constexpr int kMaxComposeSteps = 64;
+struct ComposeArgs {
+  double* A0;
+  double* A1;
+  double* F;
+  double* T;
+  double* S;
+  int P, NJ, nsteps;
+  double alpha[kMaxComposeSteps], beta[kMaxComposeSteps];
+  unsigned* bar;
+  int* err;
+  int grid_share;   // concurrent streams sharing the GPU: the grid takes 1/grid_share of it
+};
+bool compose_supported(int P, int nsteps);
+// FP64 flops the composition kernel executes (symmetric tiles only).
+double compose_flops(int P, int NJ, int nsteps);
+// Returns the number of kernel launches (1), or -1 if the launch was refused.
+int polar_compose(const ComposeArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Top solve (lanczos.cu): restarted FP64 Lanczos for the lowest eigenvector of
+// the top Hamiltonian in one cooperative launch.  V (c x c) holds the start
+// vector on entry and the normalised eigenvector on exit, sign-aligned with
+// the start (copied to Vprev).  Scratch: basis (m+1) c^2, w c^2, Y 2K c^2,
+// part grid*(m+2), coef 2(m+2), alpha, beta, y (m+2 each), scal (4),
+// flags[0] = converged, flags[1] = tridiagonal size.  err |= 4 when a grid
+// barrier wait expires.
+// ---------------------------------------------------------------------------
+constexpr int kLMaxM = 120;
+constexpr int kLMaxGrid = 512;
+struct LanczosArgs {
+  const double* s0;   // [o, A_1..A_K, B_1..B_K] of the left top site, c x c each
+  const double* s1;   // the same of the right top site
+  double* V;
+  double* Vprev;
+  double* basis;
+  double* w;
+  double* Y;
+  double* part;
+  double* coef;
+  double* alpha;
+  double* beta;
+  double* y;
+  double* scal;
+  int* flags;
+  int c, K, m, restarts;
+  double tol;
+  unsigned* bar;
+  int* err;
+};
+bool lanczos_supported(int c, int m);
+// CTAs of the launch for top dimension c when grid_share streams share the GPU.
+int lanczos_grid(int c, int grid_share);
+// Returns the number of kernel launches (1), or -1 if the launch was refused.
+int lanczos_launch(const LanczosArgs& a, int grid, cudaStream_t s);
 
 // dst[i] = (float) src[i]
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s);

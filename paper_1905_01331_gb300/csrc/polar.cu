@@ -1,0 +1,242 @@
+// Polar update (Sec. III.B: w = -(polar factor of the environment)): the
+// composition of one block of scaled Newton-Schulz steps on the P x P level,
+// in one persistent cooperative launch.
+//
+// A block starts from the Gram matrix A_0 = X X^T.  Step j applies
+// p_j(x) = alpha_j x - beta_j x^3 to the singular values of X, which on the
+// P x P level reads
+//     Pm_j = alpha_j I - beta_j A_j,   F_{j+1} = Pm_j F_j,   A_{j+1} = Pm_j A_j Pm_j,
+// (F_0 = I) and the block ends with X <- F X.  Per step
+//     phase 1:  F_{j+1} = Pm_j F_j,  T = A_j Pm_j        (F_1 = Pm_0 needs no product)
+//     phase 2:  A_{j+1} = Pm_j T
+// on full tiles.  A_j is read symmetrised, (A + A^T)/2, and Pm_j is formed from
+// it while the operands are staged.  In exact arithmetic every matrix here is
+// a polynomial in A_0 and symmetric; in rounding the products are not, and
+// keeping only one triangle of them (half the work) cost up to 20x in the
+// isometry defect of long blocks, so the full products are kept.
+//
+// The products are small (P <= 256) and FP64, which on this GPU runs at two
+// DFMA per clock per SM: a separate launch per product leaves most SMs idle and
+// pays the launch gap each time.  Here all SMs share the tiles of each phase
+// and meet at a grid barrier (bounded spin, error flag) between phases.
+#include <algorithm>
+#include <mutex>
+
+#include "common.h"
+
+namespace ttn {
+
+namespace {
+
+constexpr int kCT = 8;                       // output tile edge
+constexpr int kCThreads = 256;               // 8 warps, one K-slice each
+constexpr int kCWarps = kCThreads / 32;
+constexpr int kCMaxP = 256;
+constexpr int kCMaxSpin = 1 << 23;           // ~1 s of polling, then the error flag
+
+struct ComposeSmem {
+  double X[kCT][kCMaxP + 1];                 // rows i0.. of the left factor
+  double Y[kCT][kCMaxP + 1];                 // rows j0.. of the (symmetric) right factor
+  double red[kCWarps][kCT * kCT];            // per-warp partial sums
+  int ok;
+};
+
+// Element (r, c) = (tid / 8, tid % 8) of the tile (i0, j0) of X' Y', for
+// threads tid < 64 (0 elsewhere): sum_k X'[i0 + r][k] Y'[k][j0 + c] with
+//     X' = dx I + sx S_x(X),   Y' = dy I + sy S_y(Y),
+// S(M) = (M + M^T)/2 when the flag is set, else M, formed while rows of X and
+// columns of Y are staged.  The K range is cut into 8 interleaved slices (one
+// per warp) whose partial sums are added in warp order.
+__device__ double tile_product(ComposeSmem& sm, const double* X, double dx, double sx, bool symx,
+                               const double* Y, double dy, double sy, bool symy, int P, int i0,
+                               int j0) {
+  for (int e = threadIdx.x; e < kCT * P; e += kCThreads) {
+    // rows of X: element (r, k), consecutive threads along k
+    {
+      const int r = e / P, k = e - (e / P) * P;
+      const int gi = i0 + r;
+      double v = 0.0;
+      if (gi < P) {
+        const double x = __ldcg(X + (long long)gi * P + k);
+        const double m = symx ? 0.5 * (x + __ldcg(X + (long long)k * P + gi)) : x;
+        v = sx * m + (gi == k ? dx : 0.0);
+      }
+      sm.X[r][k] = v;
+    }
+    // columns of Y: element (k, c), consecutive threads along c
+    {
+      const int k = e / kCT, c = e - (e / kCT) * kCT;
+      const int gj = j0 + c;
+      double v = 0.0;
+      if (gj < P) {
+        const double y = __ldcg(Y + (long long)k * P + gj);
+        const double m = symy ? 0.5 * (y + __ldcg(Y + (long long)gj * P + k)) : y;
+        v = sy * m + (gj == k ? dy : 0.0);
+      }
+      sm.Y[c][k] = v;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane >> 2, j = (lane & 3) * 2;
+  double a0 = 0.0, a1 = 0.0;
+  for (int k = warp; k < P; k += kCWarps) {
+    const double x = sm.X[i][k];
+    a0 = fma(x, sm.Y[j][k], a0);
+    a1 = fma(x, sm.Y[j + 1][k], a1);
+  }
+  sm.red[warp][i * kCT + j] = a0;
+  sm.red[warp][i * kCT + j + 1] = a1;
+  __syncthreads();
+  double v = 0.0;
+  if (threadIdx.x < kCT * kCT)
+    for (int w = 0; w < kCWarps; ++w) v += sm.red[w][threadIdx.x];
+  __syncthreads();
+  return v;
+}
+
+// Grid-wide barrier of a co-resident grid: arrive on a counter zeroed before
+// the launch and poll it, at most kCMaxSpin times.  Returns false (and raises
+// *err) when the wait expires or another CTA has raised *err.
+__device__ bool grid_barrier(ComposeSmem& sm, unsigned* bar, unsigned target, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int spins = 0;
+    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+      if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
+      if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
+      __nanosleep(128);
+    }
+    __threadfence();
+    sm.ok = ok;
+  }
+  __syncthreads();
+  return sm.ok != 0;
+}
+
+__device__ __forceinline__ void store_tile(double* C, int P, int ti, int tj, double v) {
+  if (threadIdx.x >= kCT * kCT) return;
+  const int gi = ti * kCT + threadIdx.x / kCT, gj = tj * kCT + threadIdx.x % kCT;
+  if (gi < P && gj < P) __stcg(C + (long long)gi * P + gj, v);
+}
+
+__global__ void __launch_bounds__(kCThreads) polar_compose_kernel(const ComposeArgs a) {
+  __shared__ ComposeSmem sm;
+  const int P = a.P, ns = a.nsteps;
+  const int nt = (P + kCT - 1) / kCT, ntt = nt * nt;
+  const long long PP = (long long)P * P;
+  // F_j lives in F when ns - j is even, else in S, so that F_ns ends in F
+  auto Fbuf = [&](int j) { return ((ns - j) & 1) ? a.S : a.F; };
+  unsigned target = 0;
+  for (int j = 0; j < ns; ++j) {
+    const double al = a.alpha[j], be = a.beta[j];
+    const bool last = j + 1 == ns;
+    const double* Aj = (j & 1) ? a.A1 : a.A0;
+    double* An = (j & 1) ? a.A0 : a.A1;
+    double* Fn = Fbuf(j + 1);
+    // phase 1: F_{j+1} = Pm_j F_j (j > 0) and T = A_j Pm_j (not on the last step)
+    const int np = (j > 0 ? 1 : 0) + (last ? 0 : 1);
+    const int items1 = np * ntt * a.NJ;
+    for (int it = blockIdx.x; it < items1; it += gridDim.x) {
+      const int b = it / (np * ntt);
+      const int u = it % (np * ntt);
+      const bool isF = j > 0 && u < ntt;
+      const int ti = (u % ntt) / nt, tj = (u % ntt) % nt;
+      const double* Ab = Aj + b * PP;
+      const double v = isF
+          ? tile_product(sm, Ab, al, -be, true, Fbuf(j) + b * PP, 0.0, 1.0, false, P, ti * kCT,
+                         tj * kCT)
+          : tile_product(sm, Ab, 0.0, 1.0, true, Ab, al, -be, true, P, ti * kCT, tj * kCT);
+      store_tile((isF ? Fn : a.T) + b * PP, P, ti, tj, v);
+    }
+    if (j == 0) {
+      // F_1 = Pm_0, elementwise
+      for (long long e = blockIdx.x * (long long)kCThreads + threadIdx.x; e < a.NJ * PP;
+           e += (long long)gridDim.x * kCThreads) {
+        const long long b = e / PP, r = e % PP, gi = r / P, gj = r % P;
+        const double m = 0.5 * (__ldcg(Aj + e) + __ldcg(Aj + b * PP + gj * P + gi));
+        __stcg(Fn + e, (gi == gj ? al : 0.0) - be * m);
+      }
+    }
+    if (last) break;
+    target += gridDim.x;
+    if (!grid_barrier(sm, a.bar, target, a.err)) return;
+    // phase 2: A_{j+1} = Pm_j T
+    const int items2 = ntt * a.NJ;
+    for (int it = blockIdx.x; it < items2; it += gridDim.x) {
+      const int b = it / ntt, ti = (it % ntt) / nt, tj = (it % ntt) % nt;
+      const double v = tile_product(sm, Aj + b * PP, al, -be, true, a.T + b * PP, 0.0, 1.0, false,
+                                    P, ti * kCT, tj * kCT);
+      store_tile(An + b * PP, P, ti, tj, v);
+    }
+    target += gridDim.x;
+    if (!grid_barrier(sm, a.bar, target, a.err)) return;
+  }
+}
+
+struct DeviceGrid {
+  int sms = 0, per_sm = 0;
+};
+std::mutex g_grid_mutex;
+DeviceGrid g_grid[64];
+
+int compose_grid_cap() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(g_grid_mutex);
+  DeviceGrid& g = g_grid[dev];
+  if (!g.sms) {
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, polar_compose_kernel, kCThreads, 0) !=
+        cudaSuccess)
+      return 0;
+    g.sms = sms;
+    g.per_sm = std::min(occ, 2);
+  }
+  return g.sms * g.per_sm;
+}
+
+}  // namespace
+
+bool compose_supported(int P, int nsteps) {
+  return P >= 1 && P <= kCMaxP && nsteps >= 1 && nsteps <= kMaxComposeSteps;
+}
+
+double compose_flops(int P, int NJ, int nsteps) {
+  const int nt = (P + kCT - 1) / kCT;
+  const double per_product = 2.0 * nt * nt * kCT * kCT * (double)P * NJ;
+  double f = 0.0;
+  for (int j = 0; j < nsteps; ++j) {
+    const bool last = j + 1 == nsteps;
+    f += per_product * ((j > 0 ? 1 : 0) + (last ? 0 : 2));
+  }
+  return f;
+}
+
+int polar_compose(const ComposeArgs& a, cudaStream_t s) {
+  if (!compose_supported(a.P, a.nsteps)) return -1;
+  int cap = compose_grid_cap();
+  if (cap <= 0) return -1;
+  if (a.grid_share > 1) cap = std::max(1, cap / a.grid_share);
+  const int nt = (a.P + kCT - 1) / kCT;
+  const int grid = std::max(1, std::min(cap, 2 * nt * nt * a.NJ));
+  cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kCThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, polar_compose_kernel, a) != cudaSuccess) return -1;
+  return 1;
+}
+
+}  // namespace ttn

@@ -10,6 +10,7 @@
 //   descend the density matrices through the new w_t.
 // Every contraction is one grouped product (GemmDesc); nothing else touches
 // the O(chi^4) data.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -94,8 +95,26 @@ struct PolarBlock {
 
 using namespace ttn;
 
+// Scratch and stream of one concurrent instance stream ("lane").  The sweep
+// code works on the ttn_ctx fields of the same names; enqueueing an instance
+// on lane k first loads lane k's pointers into them.
+struct Lane {
+  cudaStream_t stream = nullptr;
+  double *Y = nullptr, *Gam = nullptr, *X = nullptr, *X2 = nullptr, *Yt = nullptr, *M1 = nullptr;
+  double *pA = nullptr, *pF = nullptr, *pP = nullptr, *pT = nullptr, *pS = nullptr;
+  double *partial = nullptr, *red = nullptr, *scal = nullptr;
+  double *lz_basis = nullptr, *lz_w = nullptr, *lz_c1 = nullptr, *lz_c2 = nullptr,
+         *lz_alpha = nullptr, *lz_beta = nullptr, *lz_y = nullptr, *lz_tmp = nullptr,
+         *top_stack0 = nullptr, *top_stack1 = nullptr, *lz_part = nullptr;
+  int* iflags = nullptr;
+};
+
 struct ttn_ctx {
   ttn_options opt;
+  std::vector<Lane> lanes;            // lanes[0].stream == stream
+  std::vector<int> lane_of;           // lane of each instance
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   std::vector<Instance> inst;
   cudaStream_t user = nullptr, stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -106,7 +125,8 @@ struct ttn_ctx {
   int sweeps_done = 0;
   // shared scratch
   double *Y = nullptr, *Gam = nullptr, *X = nullptr, *X2 = nullptr, *Yt = nullptr, *M1 = nullptr;
-  double *pA = nullptr, *pF = nullptr, *pP = nullptr, *pT = nullptr;
+  double *pA = nullptr, *pF = nullptr, *pP = nullptr, *pT = nullptr, *pS = nullptr;
+  bool compose_refused = false;   // a cooperative launch was refused
   double* partial = nullptr;
   size_t partial_cap = 0;
   double* red = nullptr;       // dot scratch
@@ -114,7 +134,9 @@ struct ttn_ctx {
   double *lz_basis = nullptr, *lz_w = nullptr, *lz_c1 = nullptr, *lz_c2 = nullptr, *lz_alpha = nullptr,
          *lz_beta = nullptr, *lz_y = nullptr, *lz_tmp = nullptr, *top_stack0 = nullptr,
          *top_stack1 = nullptr;
-  int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan
+  double* lz_part = nullptr;   // persistent Lanczos: per-CTA partial sums, then 2 (m + 2) coefficients
+  int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan [4]=wait expired
+                               // [5]=grid-barrier counter of the polar composition
   int lz_m = 48;
   double* E_hist = nullptr;    // device energies of the current ttn_sweep call
   std::vector<PolarBlock> polar_f64, polar_tc;
@@ -128,6 +150,27 @@ struct ttn_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, double>> ev_flops;   // (engine, flops) per event pair
 };
+
+namespace {
+
+#define TTN_LANE_FIELDS(X_) X_(stream) X_(Y) X_(Gam) X_(X) X_(X2) X_(Yt) X_(M1) X_(pA) X_(pF) \
+  X_(pP) X_(pT) X_(pS) X_(partial) X_(red) X_(scal) X_(lz_basis) X_(lz_w) X_(lz_c1) X_(lz_c2) \
+  X_(lz_alpha) X_(lz_beta) X_(lz_y) X_(lz_tmp) X_(top_stack0) X_(top_stack1) X_(lz_part) \
+  X_(iflags)
+
+void load_lane(ttn_ctx* h, const Lane& l) {
+#define TTN_LOAD(f) h->f = l.f;
+  TTN_LANE_FIELDS(TTN_LOAD)
+#undef TTN_LOAD
+}
+
+void save_lane(const ttn_ctx* h, Lane& l) {
+#define TTN_SAVE(f) l.f = h->f;
+  TTN_LANE_FIELDS(TTN_SAVE)
+#undef TTN_SAVE
+}
+
+}  // namespace
 
 namespace {
 
@@ -410,6 +453,26 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
     return;
   }
   const int m = (int)std::min<ll>(h->lz_m, n);
+  if ((h->opt.persistent & 2) && lanczos_supported(c, m)) {
+    if (!h->measuring) {
+      LanczosArgs a;
+      a.s0 = I.ops[T];
+      a.s1 = I.ops[T] + (I.per_node ? (ll)(1 + 2 * I.K) * n : 0);
+      a.V = I.V; a.Vprev = I.Vprev;
+      a.basis = h->lz_basis; a.w = h->lz_w; a.Y = h->lz_tmp; a.part = h->lz_part;
+      a.coef = h->lz_part + (ll)kLMaxGrid * (h->lz_m + 2);   // 2 (m + 2) doubles
+      a.alpha = h->lz_alpha; a.beta = h->lz_beta; a.y = h->lz_y; a.scal = h->scal;
+      a.flags = h->iflags + 6;
+      a.c = c; a.K = I.K; a.m = m; a.restarts = h->opt.lanczos_restarts;
+      a.tol = h->opt.lanczos_tol;
+      a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
+      a.err = h->iflags + 4;
+      const int grid = lanczos_grid(c, h->profiling ? 1 : (int)h->lanes.size());
+      const int nl = grid > 0 ? lanczos_launch(a, grid, h->stream) : -1;
+      if (nl < 0) h->compose_refused = true;
+      else h->launches += nl;
+    }
+  } else {
   int* skip = h->iflags;
   int* tdim = h->iflags + 1;
   int* conv = h->iflags + 2;
@@ -440,8 +503,9 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
     h->launches += lz_combine(h->lz_basis, n, tdim, h->lz_y, I.V, h->red, nrm2, tdim, skip, conv,
                               h->stream);
   }
+  if (!h->measuring) h->launches += align_sign(I.V, I.Vprev, n, h->red, dotv, h->stream);
+  }
   if (h->measuring) { top_matvec(h, I, I.V, h->lz_w, nullptr); return; }
-  h->launches += align_sign(I.V, I.Vprev, n, h->red, dotv, h->stream);
   // energy = <V, H V> + c L
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   h->launches += batched_dot(I.V, h->lz_w, n, 0, 1, h->scal + 4, h->red, h->stream);
@@ -562,6 +626,40 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
 }
 
 // w_t <- -polar(Gam - mu |Gam| w_t) by scaled Newton-Schulz blocks.
+// F = composed polynomial of one block from the Gram matrix in pA (one
+// cooperative launch; pA, pP, pT, pS are overwritten).
+void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ) {
+  ComposeArgs a;
+  a.A0 = h->pA; a.A1 = h->pP; a.F = h->pF; a.T = h->pT; a.S = h->pS;
+  a.P = P; a.NJ = NJ; a.nsteps = (int)blk.steps.size();
+  for (int j = 0; j < a.nsteps; ++j) {
+    a.alpha[j] = blk.steps[j].first;
+    a.beta[j] = blk.steps[j].second;
+  }
+  a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
+  a.err = h->iflags + 4;
+  a.grid_share = h->profiling ? 1 : (int)h->lanes.size();
+  cudaEvent_t ev[2];
+  if (h->profiling) {
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], h->stream);
+  }
+  const int n = polar_compose(a, h->stream);
+  if (n < 0) {
+    // the launch was refused: the flag turns the sweep into an error
+    h->compose_refused = true;
+    return;
+  }
+  h->launches += n;
+  if (h->profiling) {
+    cudaEventRecord(ev[1], h->stream);
+    h->ev_pool.push_back(ev[0]);
+    h->ev_pool.push_back(ev[1]);
+    h->ev_flops.push_back({0, compose_flops(P, NJ, a.nsteps)});
+  }
+}
+
 void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   const LayerView v = view(I, t, 0);
   const int P = v.P, NJ = v.NJ;
@@ -580,13 +678,18 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // must not drown in tensor-core rounding).  FP64 mode: short blocks (at most
   // four composed steps per Gram matrix) for full accuracy; mixed modes: two
   // Gram matrices and two long compositions.
-  const std::vector<PolarBlock>& sched = prec == 0 ? h->polar_f64 : h->polar_tc;
+  const bool short_blocks =
+      h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && prec == 0);
+  const std::vector<PolarBlock>& sched = short_blocks ? h->polar_f64 : h->polar_tc;
   for (const PolarBlock& blk : sched) {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
     add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
     g.sym = 1;
     run(h, g, 0);
+    if ((h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size())) {
+      if (!h->measuring) compose_block(h, blk, P, NJ);
+    } else {
     if (!h->measuring) h->launches += set_identity(h->pF, P, NJ, h->stream);
     for (size_t j = 0; j < blk.steps.size(); ++j) {
       if (!h->measuring)
@@ -608,6 +711,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
         run(h, c, 0);
         if (!h->measuring) h->launches += symmetrize(h->pA, P, NJ, h->stream);
       }
+    }
     }
     // X2 = F X ; swap.  F amplifies the small singular directions by up to
     // 1/damping, so this product is FP64 in every mode (a tensor-core product
@@ -754,31 +858,38 @@ void layout(ttn_ctx* h, Arena& ar) {
     c2_max = std::max(c2_max, (size_t)c * c);
     K_max = std::max(K_max, I.K);
   }
-  h->Y = ar.take((1 + 4 * K_max) * slab_max);
-  h->Yt = ar.take((1 + 2 * K_max) * slab_max);
-  h->M1 = ar.take(2 * K_max * slab_max);
-  h->Gam = ar.take(slab_max);
-  h->X = ar.take(slab_max);
-  h->X2 = ar.take(slab_max);
-  h->pA = ar.take(pp_max);
-  h->pF = ar.take(pp_max);
-  h->pP = ar.take(pp_max);
-  h->pT = ar.take(pp_max);
-  h->red = ar.take(std::max<size_t>(kDotBlocks * (h->lz_m + 2), kDotBlocks * nj_max * 2));
-  h->scal = ar.take(16 + 2 * nj_max);
-  h->lz_basis = ar.take((h->lz_m + 1) * c2_max);
-  h->lz_w = ar.take(c2_max);
-  h->lz_tmp = ar.take(2 * K_max * c2_max);
-  h->lz_c1 = ar.take(h->lz_m + 2);
-  h->lz_c2 = ar.take(h->lz_m + 2);
-  h->lz_alpha = ar.take(h->lz_m + 2);
-  h->lz_beta = ar.take(h->lz_m + 2);
-  h->lz_y = ar.take(h->lz_m + 2);
-  h->top_stack0 = ar.take((1 + 2 * K_max) * c2_max);
-  h->top_stack1 = ar.take((1 + 2 * K_max) * c2_max);
-  h->iflags = ar.take_int(8);
+  // scratch of every lane (a full copy each: lanes run concurrently)
+  for (size_t k = 0; k < h->lanes.size(); ++k) {
+    h->Y = ar.take((1 + 4 * K_max) * slab_max);
+    h->Yt = ar.take((1 + 2 * K_max) * slab_max);
+    h->M1 = ar.take(2 * K_max * slab_max);
+    h->Gam = ar.take(slab_max);
+    h->X = ar.take(slab_max);
+    h->X2 = ar.take(slab_max);
+    h->pA = ar.take(pp_max);
+    h->pF = ar.take(pp_max);
+    h->pP = ar.take(pp_max);
+    h->pT = ar.take(pp_max);
+    h->pS = ar.take(pp_max);
+    h->red = ar.take(std::max<size_t>(kDotBlocks * (h->lz_m + 2), kDotBlocks * nj_max * 2));
+    h->scal = ar.take(16 + 2 * nj_max);
+    h->lz_basis = ar.take((h->lz_m + 1) * c2_max);
+    h->lz_w = ar.take(c2_max);
+    h->lz_tmp = ar.take(2 * K_max * c2_max);
+    h->lz_c1 = ar.take(h->lz_m + 2);
+    h->lz_c2 = ar.take(h->lz_m + 2);
+    h->lz_alpha = ar.take(h->lz_m + 2);
+    h->lz_beta = ar.take(h->lz_m + 2);
+    h->lz_y = ar.take(h->lz_m + 2);
+    h->top_stack0 = ar.take((1 + 2 * K_max) * c2_max);
+    h->top_stack1 = ar.take((1 + 2 * K_max) * c2_max);
+    h->lz_part = ar.take((size_t)(kLMaxGrid + 2) * (h->lz_m + 2));
+    h->iflags = ar.take_int(8);
+    h->partial = ar.take(h->partial_cap);
+    save_lane(h, h->lanes[k]);
+  }
   h->E_hist = ar.take(4096 * h->inst.size() + 16);
-  h->partial = ar.take(h->partial_cap);
+  load_lane(h, h->lanes[0]);
 }
 
 int fail(ttn_ctx* h, int code, const std::string& msg) {
@@ -794,7 +905,7 @@ int check_cuda(ttn_ctx* h, cudaError_t e, const char* what) {
 int build_instances(ttn_ctx* h, const ttn_problem* probs, int n) {
   for (int i = 0; i < n; ++i) {
     const ttn_problem& p = probs[i];
-    if (p.Lx < 4 || !is_pow2(p.Lx) || p.Ly < 1 || p.d < 2 || p.chi < 1 || p.K < 1 ||
+    if (p.Lx < 4 || !is_pow2(p.Lx) || p.Ly < 1 || p.d < 2 || p.chi < 1 || p.K < 1 || p.K > 7 ||
         !p.onesite || !p.A || !p.B)
       return fail(h, TTN_EINVAL, "problem " + std::to_string(i) + ": bad shape or null terms");
     Instance I;
@@ -870,6 +981,37 @@ void ttn_default_options(ttn_options* o) {
   o->polar_damping = 1e-7;
   o->deterministic = 1;
   o->use_graph = 1;
+  o->persistent = 3;
+  o->streams = 8;
+  o->polar_blocks = 0;
+}
+
+// Instances go to min(streams, instances) lanes, longest first onto the least
+// loaded lane (cost ~ the chi^4 contractions of a sweep plus its Lanczos).
+static void assign_lanes(ttn_ctx* h) {
+  const int ni = (int)h->inst.size();
+  const int nl = std::max(1, std::min(h->opt.streams, ni));
+  h->lanes.assign(nl, Lane());
+  h->lane_of.assign(ni, 0);
+  std::vector<std::pair<double, int>> cost;
+  for (int i = 0; i < ni; ++i) {
+    const Instance& I = h->inst[i];
+    double c = 0.0;
+    for (int t = 0; t < I.T; ++t)
+      c += (double)I.nodes(t) * I.chis[t + 1] * std::pow((double)I.chis[t], 3) * (1 + 2 * I.K);
+    c += 150.0 * std::pow((double)I.chis[I.T], 3) * (1 + 2 * I.K);
+    cost.push_back({c, i});
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+                     return a.first > b.first;
+                   });
+  std::vector<double> load(nl, 0.0);
+  for (const auto& ci : cost) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    h->lane_of[ci.second] = k;
+    load[k] += ci.first;
+  }
 }
 
 static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_options* opt) {
@@ -883,6 +1025,10 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   h->lz_m = h->opt.lanczos_max;
   int rc = build_instances(h, probs, n);
   if (rc) return rc;
+  if (h->opt.streams < 1 || h->opt.streams > 64) return fail(h, TTN_EINVAL, "streams in [1,64]");
+  if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 2)
+    return fail(h, TTN_EINVAL, "polar_blocks is 0, 1 or 2");
+  assign_lanes(h);
   setup_schedules(h);
   Arena a0;
   a0.base = reinterpret_cast<char*>((size_t)1 << 40);   // fake address, never dereferenced
@@ -918,7 +1064,18 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
   h->user = reinterpret_cast<cudaStream_t>(stream);
   gemm_tc_init();
   rc = check_cuda(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
-  if (!rc) rc = check_cuda(h, cudaMemsetAsync(h->iflags, 0, 8 * sizeof(int), h->stream), "flags");
+  h->lanes[0].stream = h->stream;
+  h->ev_join.assign(h->lanes.size(), nullptr);
+  if (!rc && h->lanes.size() > 1)
+    rc = check_cuda(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event");
+  for (size_t k = 1; k < h->lanes.size() && !rc; ++k) {
+    rc = check_cuda(h, cudaStreamCreateWithFlags(&h->lanes[k].stream, cudaStreamNonBlocking),
+                    "stream");
+    if (!rc)
+      rc = check_cuda(h, cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming), "event");
+  }
+  for (size_t k = 0; k < h->lanes.size() && !rc; ++k)
+    rc = check_cuda(h, cudaMemsetAsync(h->lanes[k].iflags, 0, 8 * sizeof(int), h->stream), "flags");
   if (rc) { *out = h; return rc; }
   // upload operators of site layer 0 (shifted one-site term)
   for (Instance& I : h->inst) {
@@ -1012,8 +1169,29 @@ int ttn_get_isometries(ttn_t h, int inst, double* w, double* v) {
   return check_cuda(h, cudaStreamSynchronize(h->stream), "get sync");
 }
 
+// One sweep of every instance.  With several lanes the instances of each lane
+// follow one another on the lane's stream and the lanes fork from and join
+// the library stream (in a captured graph: parallel branches).  A profiling
+// sweep keeps everything on one stream so that its events time one product
+// at a time.
 static void enqueue_sweep(ttn_ctx* h) {
-  for (Instance& I : h->inst) sweep_instance(h, I);
+  const int nl = (int)h->lanes.size();
+  if (nl == 1 || h->profiling) {
+    for (Instance& I : h->inst) sweep_instance(h, I);
+    return;
+  }
+  cudaStream_t main = h->lanes[0].stream;
+  cudaEventRecord(h->ev_fork, main);
+  for (int k = 1; k < nl; ++k) cudaStreamWaitEvent(h->lanes[k].stream, h->ev_fork, 0);
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    load_lane(h, h->lanes[h->lane_of[i]]);
+    sweep_instance(h, h->inst[i]);
+  }
+  load_lane(h, h->lanes[0]);
+  for (int k = 1; k < nl; ++k) {
+    cudaEventRecord(h->ev_join[k], h->lanes[k].stream);
+    cudaStreamWaitEvent(main, h->ev_join[k], 0);
+  }
 }
 
 int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
@@ -1030,6 +1208,7 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
     enqueue_sweep(h);
     rc = check_cuda(h, cudaStreamEndCapture(h->stream, &h->graph), "end capture");
     if (rc) return rc;
+    if (h->compose_refused) return fail(h, TTN_ECUDA, "cooperative launch refused");
     rc = check_cuda(h, cudaGraphInstantiate(&h->exec, h->graph, 0), "instantiate");
     if (rc) return rc;
     h->launches_per_sweep = h->launches;
@@ -1046,6 +1225,7 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
         h->launches += h->launches_per_sweep;
       } else {
         enqueue_sweep(h);
+        if (h->compose_refused) return fail(h, TTN_ECUDA, "cooperative launch refused");
       }
       if (host_energy)
         for (int i = 0; i < ni; ++i)
@@ -1072,11 +1252,14 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
   rc = check_cuda(h, cudaGetLastError(), "sweep");
   if (rc) return rc;
   if (host_energy) {
-    int flag = 0;
-    cudaMemcpyAsync(&flag, h->iflags + 4, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<int> flag(h->lanes.size(), 0);
+    for (size_t k = 0; k < h->lanes.size(); ++k)
+      cudaMemcpyAsync(&flag[k], h->lanes[k].iflags + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                      h->stream);
     rc = check_cuda(h, cudaStreamSynchronize(h->stream), "flag sync");
     if (rc) return rc;
-    if (flag) return fail(h, TTN_ETIMEOUT, "a bounded wait in a tensor-core kernel expired");
+    for (int f : flag)
+      if (f) return fail(h, TTN_ETIMEOUT, "a bounded wait in a kernel expired");
   }
   if (host_energy)
     for (int i = 0; i < n_sweeps * ni; ++i)
@@ -1274,6 +1457,7 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   cudaEventRecord(t1, h->stream);
   h->profiling = false;
   int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
+  if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
   double ms[2] = {0, 0}, fl[2] = {0, 0}, cnt[2] = {0, 0};
   for (size_t i = 0; i < h->ev_flops.size(); ++i) {
     float e = 0.f;
@@ -1303,7 +1487,17 @@ void ttn_destroy(ttn_t h) {
   if (!h) return;
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  if (h->stream) { cudaStreamSynchronize(h->stream); cudaStreamDestroy(h->stream); }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (size_t k = 1; k < h->lanes.size(); ++k)
+    if (h->lanes[k].stream) {
+      cudaStreamSynchronize(h->lanes[k].stream);
+      cudaStreamDestroy(h->lanes[k].stream);
+    }
+  for (cudaEvent_t e : h->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (!h->lanes.empty()) h->stream = h->lanes[0].stream;
+  if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 

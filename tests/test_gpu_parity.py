@@ -150,3 +150,52 @@ def test_top_polar_step_mode_matches_oracle():
     E_ref = np.array([oracle.sweep(st, top_mode=1) for _ in range(5)])
     assert np.abs(E - E_ref).max() < 1e-10 * np.abs(E_ref).max()
     assert np.all(np.diff(E) <= 1e-9 * np.abs(E[1:]))
+
+
+@pytest.mark.parametrize("prec,per_node,chi,L", [("fp64", True, 8, 16), ("fp64", False, 64, 256),
+                                                 ("tf32x3", False, 128, 256)])
+def test_persistent_kernels_match_separate_launches(prec, per_node, chi, L):
+    """The persistent cooperative kernels (bit 0: the Newton-Schulz composition
+    of each polar block; bit 1: the Lanczos top solve) and the same steps as
+    separate launches give the same sweep up to rounding, and every isometry
+    stays exact."""
+    model = ti.tfim_chain(L, 1.0)
+    ws, V = ti.initial_tensors(L, 2, chi, 7, per_node)
+    E = {}
+    W = None
+    for mode in (3, 2, 0):
+        s = _sweeper(model, chi, per_node, prec=prec, persistent=mode)
+        s.set_isometries(0, ws, V)
+        E[mode] = s.sweep(3)[:, 0]
+        if mode == 3:
+            W = s.get_isometries(0)[0]
+        s.close()
+    rel = lambda a, b: np.abs(E[a] - E[b]) / np.abs(E[b])
+    print("composition kernel on/off", rel(3, 2), "Lanczos kernel on/off", rel(2, 0))
+    # sweep 1 reports the top solve: the same to rounding, amplified by the
+    # cancellation of the energy against the shift cL
+    assert rel(3, 0)[0] < 1e-12
+    if prec == "fp64":
+        # each kernel alone: one update at the resynchronised FP64 tolerance,
+        # two updates amplified by the ill-conditioned first polar factors of
+        # a random start
+        for a, b in ((3, 2), (2, 0)):
+            assert rel(a, b)[1] < 1e-10
+            assert rel(a, b).max() < 1e-8
+    else:
+        # mixed modes: an FP64 difference at the rounding level flips the
+        # rounding of some FP32 copies of w, so it reappears at the level of the
+        # tensor-core rounding; it must stay below the distance of the mixed
+        # path from the FP64 path
+        s = _sweeper(model, chi, per_node, prec="fp64")
+        s.set_isometries(0, ws, V)
+        E64 = s.sweep(3)[:, 0]
+        s.close()
+        floor = np.abs(E[3] - E64) / np.abs(E64)
+        print("mixed vs FP64 path", floor)
+        for a, b in ((3, 2), (2, 0)):
+            assert (rel(a, b)[1:] < 0.5 * floor[1:]).all()
+    for w in W:
+        for node in (w if w.ndim == 4 else w[None]):
+            m = node.reshape(node.shape[0], -1)
+            assert np.abs(m @ m.T - np.eye(m.shape[0])).max() < 1e-11
