@@ -49,10 +49,11 @@ def parse():
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
     p.add_argument("--workload", default="tfim1024",
-                   choices=["tfim1024", "batched64", "paper-torus", "top-mode"],
+                   choices=["tfim1024", "batched64", "paper-torus", "top-mode", "configs"],
                    help="tfim1024: the headline line; batched64: 64 independent chains in one "
                         "context; paper-torus: the paper's 128 x 5 torus at h = 2.9 with its "
-                        "entanglement spectrum; top-mode: eigensolver vs polar-step top update")
+                        "entanglement spectrum; top-mode: eigensolver vs polar-step top update; "
+                        "configs: the five configurations' table")
     return p.parse_args()
 
 
@@ -270,7 +271,9 @@ def run_gpu(args):
     e2e = {"value": world * e2e_steps / e2e_dt, "unit": "sweeps/s",
            "h2d_bytes_per_step": 8 * (n_w + V.size), "d2h_bytes_per_step": 8}
 
-    # roofline of the dominant kernel family (grouped products)
+    # roofline of the dominant kernel family: the FP64 engine (grouped FP64
+    # products and the persistent polar composition, executed flops) or the
+    # tensor-core products (algorithmic flops)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -289,7 +292,7 @@ def run_gpu(args):
         peak = 1.10   # measured torch float64 8192^3 matmul on GB300 (cuBLAS DGEMM)
         peak_src = "measured cuBLAS DGEMM 8192^3 on this pool's GB300 (1.10 TFLOP/s)"
         bound = "alu"
-        kernel = "gemm_f64_kernel (FP64 grouped products)"
+        kernel = "FP64 engine: gemm_f64_kernel (grouped products) + polar_compose_kernel"
     achieved = dom_fl / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
@@ -445,6 +448,93 @@ def run_paper_torus(args):
     s.close()
 
 
+def _oracle_sweep_seconds(workload_expr, threads, sweeps=1):
+    """Seconds per oracle sweep of a workload in a fresh process with the BLAS
+    limited to `threads` threads (the CPU baseline of the config table)."""
+    code = ("import time, ttn_inputs as ti\n"
+            "from oracle import ttn as oracle\n"
+            f"w = {workload_expr}\n"
+            "ws, V = ti.initial_tensors(w.model.Lx, w.model.d0, w.chi, w.seed, w.per_node)\n"
+            "st = oracle.make_state(w.model, ws, V, per_node=w.per_node)\n"
+            "oracle.sweep(st)\n"
+            "t0 = time.perf_counter()\n"
+            f"for _ in range({sweeps}): oracle.sweep(st)\n"
+            f"print((time.perf_counter() - t0) / {sweeps})\n")
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=1800)
+    return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+
+
+def run_configs(args):
+    """The five configurations: GPU FP64 and mixed-precision sweeps/s, FP64
+    parity against the oracle's stored trajectories, FP64-certified energies
+    of the mixed paths, and the oracle's seconds per sweep on the host cores.
+    One JSON line per configuration."""
+    import numpy as np
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+
+    def golden(name):
+        path = os.path.join(ROOT, "tests", "golden", f"oracle_{name}.json")
+        if not os.path.exists(path):
+            return None
+        with open(path) as f:
+            return json.load(f)
+
+    def timed(s, n):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.sweep_async(n)
+        b.record(s.stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
+    def gpu_run(w, prec, n):
+        s = Sweeper(w.model, w.chi, per_node=w.per_node, prec=prec)
+        s.set_isometries(0, *ti.initial_tensors(w.model.Lx, w.model.d0, w.chi, w.seed, w.per_node))
+        E = s.sweep(n)[:, 0]                      # trajectory from the seeded start
+        cert = s.energy(0)
+        k = min(n, 20)
+        dt = timed(s, k)                          # throughput, warm
+        s.close()
+        return E, cert, k / dt
+
+    ncores = os.cpu_count()
+    rows = [("ti.tfim_l16_pernode()", ti.tfim_l16_pernode(), ["fp64", "tf32x3"], True),
+            ("ti.tfim_l1024(32)", ti.tfim_l1024(32), ["fp64", "tf32x3", "tf32"], True),
+            ("ti.tfim_l1024(64)", ti.tfim_l1024(64), ["fp64", "tf32x3", "tf32"], False),
+            ("ti.tfim_l1024(128)", ti.tfim_l1024(128), ["fp64", "tf32x3", "tf32"], False),
+            ("ti.heisenberg_l256(256)", ti.heisenberg_l256(256), ["fp64", "bf16x3"], False),
+            ("ti.torus_64x4(128)", ti.torus_64x4(128), ["fp64", "tf32", "tf32x3"], False)]
+    for expr, w, precs, one_core in rows:
+        g = golden(w.name)
+        line = {"config": w.name, "chi": w.chi, "K": w.model.K, "d0": w.model.d0}
+        for prec in precs:
+            if prec == "fp64":
+                n = g["sweeps"] if g else 4
+            else:
+                n = 20 if w.name.startswith("heisenberg") else w.sweeps
+            E, cert, sps = gpu_run(w, prec, n)
+            r = {"sweeps": n, "sweeps_per_s": sps, "E_certified_fp64": cert,
+                 "energy_per_spin": cert / w.model.n_spins}
+            if g and len(g["energies"]) >= n:
+                ref = np.array(g["energies"][:n])
+                r["max_rel_err_vs_oracle_trajectory"] = float((np.abs(E - ref) / np.abs(ref)).max())
+                if n == g["sweeps"]:
+                    r["rel_err_certified_vs_oracle"] = abs(cert - g["final_energy"]) / abs(g["final_energy"])
+            line[prec] = r
+        line["oracle_s_per_sweep"] = {f"{ncores}_threads": _oracle_sweep_seconds(expr, ncores)}
+        if one_core:
+            line["oracle_s_per_sweep"]["1_thread"] = _oracle_sweep_seconds(expr, 1)
+        print(json.dumps(line), flush=True)
+
+
 def run_top_mode_study(args):
     """Top update read two ways (Sec. III.B, "updated similarly"): the exact
     lowest eigenvector (top_mode 0) against minus the polar factor of the top
@@ -488,6 +578,9 @@ def main():
     args = parse()
     if args.workload == "top-mode":
         run_top_mode_study(args)
+        return
+    if args.workload == "configs":
+        run_configs(args)
         return
     if args.workload == "batched64":
         run_batched(args)
