@@ -439,10 +439,14 @@ def run_paper_torus(args):
     p = np.clip(np.linalg.eigvalsh(0.5 * (rho + rho.T))[::-1], 1e-300, None)
     lam = -np.log2(p)
     S = float(-np.sum(p * np.log2(p)))
+    marks = sorted({k for k in (1, 10, 50, 100, 200, 500, 1000, 2000, 5000) if k <= args.steps}
+                   | {args.steps})
     print(json.dumps({"workload": "paper torus 128x5 h=2.9", "chi": chi, "precision": args.prec,
                       "sweeps": args.steps, "sweeps_per_s": args.steps / dt,
                       "energy_per_spin_fp64": E_cert / m.n_spins,
-                      "energy_per_spin_last_sweeps": (E[-3:] / m.n_spins).tolist(),
+                      "energy_per_spin_at_sweep": {str(k): float(E[k - 1] / m.n_spins) for k in marks},
+                      "last_delta_e_per_spin": float(abs(E[-1] - E[-2]) / m.n_spins)
+                      if len(E) > 1 else None,
                       "paper_e_inf": -3.11229, "entanglement_spectrum_tau6_first30": lam[:30].tolist(),
                       "entropy_tau6": S}))
     s.close()
