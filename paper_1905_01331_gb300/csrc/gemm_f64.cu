@@ -51,8 +51,15 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
   __shared__ double Bs[kBK][BN + 1];
 
   const int tiles_n = (d.N + BN - 1) / BN;
-  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-  if (d.sym && tm > tn) return;      // symmetric product: the mirror tile fills it
+  int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  if (d.sym) {
+    // symmetric product: only tiles on or above the diagonal are launched
+    // (blockIdx.x counts them row by row); the mirror tile fills the rest
+    int u = blockIdx.x, row = tiles_n;
+    tm = 0;
+    while (u >= row) { u -= row; ++tm; --row; }
+    tn = tm + u;
+  }
   const int b = blockIdx.y;
   const int b0 = b % d.B0, b1 = b / d.B0;
   const int split = blockIdx.z;
@@ -163,7 +170,8 @@ int total_k_tiles(const GemmDesc& d) {
 
 template <int BM, int BN>
 int launch_tile(const GemmDesc& d, cudaStream_t s) {
-  const int tiles = ((d.M + BM - 1) / BM) * ((d.N + BN - 1) / BN);
+  const int tn = (d.N + BN - 1) / BN;
+  const int tiles = d.sym ? tn * (tn + 1) / 2 : ((d.M + BM - 1) / BM) * tn;
   dim3 grid(tiles, d.B0 * d.B1, d.splits);
   gemm_f64_kernel<BM, BN><<<grid, kThreads, 0, s>>>(d, total_k_tiles(d));
   return 1;
@@ -185,7 +193,10 @@ int f64_tile(const GemmDesc& d) {
 int gemm_pick_splits(const GemmDesc& d) {
   if (d.prec != 0 && gemm_tc_supported(d)) return tc_pick_splits(d);
   const int bm = f64_tile(d);
-  const long long base = (long long)((d.M + bm - 1) / bm) * ((d.N + bm - 1) / bm) * d.B0 * d.B1;
+  const long long tm = (d.M + bm - 1) / bm, tn = (d.N + bm - 1) / bm;
+  // a symmetric product launches only the tiles on or above the diagonal
+  const long long tiles = (d.sym && d.M == d.N) ? tm * (tm + 1) / 2 : tm * tn;
+  const long long base = tiles * d.B0 * d.B1;
   const int kt = total_k_tiles(d);
   if (base >= 296 || kt < 4) return 1;
   int s = (int)std::min<long long>((296 + base - 1) / base, kt / 2);

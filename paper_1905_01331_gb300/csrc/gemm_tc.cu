@@ -316,6 +316,95 @@ __device__ __forceinline__ void stage_operand(const Operand& o, int k0_log2, lon
                                                      hi_tile, lo_tile);
 }
 
+// TF32 modes with FP32 operands: the global loads of both operand tiles are
+// issued before any of them is split and stored, so that a K tile costs one
+// load latency instead of two.  load_f32 fills v (16 values per thread for
+// ROWS <= 128) on the two fast paths of stage_operand_t and returns the path
+// (1: K-major, 2: MN-major) or 0 when neither applies (the caller then stages
+// that operand with stage_operand).
+template <int ROWS>
+__device__ __forceinline__ int load_f32(const Operand& o, int k0_log2, long long base, int r0,
+                                        int nrows_valid, int kb, int Kg, float* v) {
+  constexpr int BK = 32, CH = 4, NCH = BK / CH;
+  const int K0 = 1 << k0_log2;
+  if (!(K0 >= BK && Kg - kb >= BK)) return 0;
+  const float* tb = static_cast<const float*>(o.p) + base +
+                    static_cast<long long>(kb >> k0_log2) * o.s_k1 + (kb & (K0 - 1)) * o.s_k0;
+  if (o.s_k0 == 1) {
+    constexpr int TASKS = (ROWS * NCH + kThreadsTC - 1) / kThreadsTC;
+#pragma unroll
+    for (int g = 0; g < TASKS; ++g) {
+      const int task = threadIdx.x + g * kThreadsTC;
+      const int r = task / NCH, c = task % NCH;
+      if (task < ROWS * NCH && r < nrows_valid) {
+        ldv<float, CH>(tb + static_cast<long long>(r0 + r) * o.s_mn + c * CH, v + g * CH);
+      } else {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) v[g * CH + q] = 0.f;
+      }
+    }
+    return 1;
+  }
+  if (o.s_mn == 1 && (nrows_valid & 3) == 0) {
+    constexpr int TASKS = ((ROWS / 4) * NCH + kThreadsTC - 1) / kThreadsTC;
+#pragma unroll
+    for (int g = 0; g < TASKS; ++g) {
+      const int task = threadIdx.x + g * kThreadsTC;
+      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int r = rq * 4;
+      if (task < (ROWS / 4) * NCH && r < nrows_valid) {
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+          ldv<float, 4>(tb + static_cast<long long>(c * CH + q) * o.s_k0 + (r0 + r),
+                        v + g * 16 + q * 4);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[g * 16 + q] = 0.f;
+      }
+    }
+    return 2;
+  }
+  return 0;
+}
+
+// Split and store what load_f32 loaded (same task mapping).
+template <bool kSplit, int ROWS>
+__device__ __forceinline__ void store_f32(int path, const float* v, uint8_t* hi_tile,
+                                          uint8_t* lo_tile) {
+  constexpr int BK = 32, CH = 4, NCH = BK / CH;
+  if (path == 1) {
+    constexpr int TASKS = (ROWS * NCH + kThreadsTC - 1) / kThreadsTC;
+#pragma unroll
+    for (int g = 0; g < TASKS; ++g) {
+      const int task = threadIdx.x + g * kThreadsTC;
+      if (task >= ROWS * NCH) continue;
+      const int r = task / NCH, c = task % NCH;
+      uint32_t h[CH], l[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) split<false>(v[g * CH + q], h[q], l[q]);
+      st_chunk<false>(hi_tile, r, c * CH, h);
+      if constexpr (kSplit) st_chunk<false>(lo_tile, r, c * CH, l);
+    }
+  } else if (path == 2) {
+    constexpr int TASKS = ((ROWS / 4) * NCH + kThreadsTC - 1) / kThreadsTC;
+#pragma unroll
+    for (int g = 0; g < TASKS; ++g) {
+      const int task = threadIdx.x + g * kThreadsTC;
+      if (task >= (ROWS / 4) * NCH) continue;
+      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int r = rq * 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t h[CH], l[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) split<false>(v[g * 16 + q * 4 + i], h[q], l[q]);
+        st_chunk<false>(hi_tile, r + i, c * CH, h);
+        if constexpr (kSplit) st_chunk<false>(lo_tile, r + i, c * CH, l);
+      }
+    }
+  }
+}
+
 struct TCParams {
   int total_tiles;
   int* err;
@@ -406,8 +495,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1) gemm_tc_kernel(const GemmDesc d
       uint8_t* a_lo = st + kA + kB;
       uint8_t* b_lo = st + 2 * kA + kB;
       const int kb = t * BK;
-      stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, a_hi, a_lo);
-      stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, b_hi, b_lo);
+      if constexpr (!kBF16) {
+        if (G.a.f32 && G.b.f32) {
+          float va[16], vb[16];
+          const int pa = load_f32<kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, va);
+          const int pb = load_f32<BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, vb);
+          store_f32<kSplit, kBM>(pa, va, a_hi, a_lo);
+          store_f32<kSplit, BN>(pb, vb, b_hi, b_lo);
+          if (!pa)
+            stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K,
+                                                  a_hi, a_lo);
+          if (!pb)
+            stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K,
+                                                 b_hi, b_lo);
+        } else {
+          stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, a_hi,
+                                                a_lo);
+          stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, b_hi,
+                                               b_lo);
+        }
+      } else {
+        stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, a_hi,
+                                              a_lo);
+        stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, b_hi,
+                                             b_lo);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (threadIdx.x == 0) {

@@ -78,25 +78,6 @@ __device__ double cta_ordered_sum(LzSmem& sm, const double* x, int count, long l
   return v;
 }
 
-// Per-CTA sum of a[e] * b[e] over [lo, hi), reduced in a fixed order.
-__device__ double cta_dot(LzSmem& sm, const double* a, const double* b, long long lo,
-                          long long hi) {
-  double s = 0.0;
-  for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) s = fma(__ldcg(a + e), __ldcg(b + e), s);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sm.red[0][threadIdx.x >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kLWarps; ++w) t += sm.red[0][w];
-  if (threadIdx.x == 0) sm.bcast[1] = t;
-  __syncthreads();
-  const double v = sm.bcast[1];
-  __syncthreads();
-  return v;
-}
-
 // Stage rows [r0, r0+8) of the row-major c x c matrix M (times scale) into dst.
 __device__ void stage_rows(double (*dst)[kLMaxC + 1], const double* M, int c, int r0, double scale) {
   for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
@@ -259,27 +240,86 @@ __device__ void ritz_pair(LzSmem& sm, const double* alpha, const double* beta, i
   *res = fabs(beta[m - 1] * x[m - 1]);
 }
 
+// Vector entries owned by a CTA: the entries of the 8 x 8 tiles of H x that
+// the CTA computes (tiles t = bid, bid + G, ...), so that the projections of a
+// new w start without a grid barrier.  Local index q -> global index, or -1
+// for the padding of a partial tile.
+__device__ __forceinline__ long long own_index(int q, int bid, int G, int nt, int c) {
+  const int t = bid + (q >> 6) * G, e = q & 63;
+  const int row = (t / nt) * kLT + (e >> 3), col = (t % nt) * kLT + (e & 7);
+  return (row < c && col < c) ? (long long)row * c + col : -1;
+}
+
+// Per-CTA sum of a[i] * b[i] over the owned entries, reduced in a fixed order.
+__device__ double own_dot(LzSmem& sm, const double* a, const double* b, int nown, int bid, int G,
+                          int nt, int c) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nown; q += kLThreads) {
+    const long long i = own_index(q, bid, G, nt, c);
+    if (i >= 0) s = fma(__ldcg(a + i), __ldcg(b + i), s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm.red[0][threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLWarps; ++w) t += sm.red[0][w];
+    sm.bcast[1] = t;
+  }
+  __syncthreads();
+  const double v = sm.bcast[1];
+  __syncthreads();
+  return v;
+}
+
+// part[bid][i] = <basis_i, w> over the owned entries for i <= j (one warp per
+// vector), and part[bid][nslot] = |w|^2 when nslot >= 0.
+__device__ void own_projections(const LanczosArgs& a, double* part, int ldp, int j, int nslot,
+                                int nown, int bid, int G, int nt, int c, long long n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j + (nslot >= 0 ? 1 : 0); i += kLWarps) {
+    const bool norm = i > j;
+    const double* bi = norm ? a.w : a.basis + (long long)i * n;
+    double s = 0.0;
+    for (int q = lane; q < nown; q += 32) {
+      const long long e = own_index(q, bid, G, nt, c);
+      if (e >= 0) s = fma(__ldcg(bi + e), __ldcg(a.w + e), s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) __stcg(part + (long long)bid * ldp + (norm ? nslot : i), s);
+  }
+}
+
 __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a) {
   __shared__ LzSmem sm;
   const int c = a.c, K = a.K, m = a.m;
   const long long n = (long long)c * c;
   const int G = gridDim.x, bid = blockIdx.x;
-  const long long lo = n * bid / G, hi = n * (bid + 1) / G;
-  const int ldp = m + 2;                     // stride of the per-CTA partial sums
   const int nt = (c + kLT - 1) / kLT;
+  const int ntiles = nt * nt;
+  const int nown = (bid < ntiles ? (ntiles - bid + G - 1) / G : 0) * 64;
+  const int ldp = m + 2;                     // stride of the per-CTA partial sums
+  const int nslot = m + 1;                   // slot of |w|^2 in a CTA's partial sums
   double* part = a.part;
+  double* wn2 = a.coef + 2 * ldp - 1;        // |w|^2 of the current step
   unsigned target = 0;
 
   // start: Vprev = V, basis_0 = V / |V|
-  for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) __stcg(a.Vprev + e, __ldcg(a.V + e));
+  for (int q = threadIdx.x; q < nown; q += kLThreads) {
+    const long long e = own_index(q, bid, G, nt, c);
+    if (e >= 0) __stcg(a.Vprev + e, __ldcg(a.V + e));
+  }
   {
-    const double s = cta_dot(sm, a.V, a.V, lo, hi);
+    const double s = own_dot(sm, a.V, a.V, nown, bid, G, nt, c);
     if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
   }
   if (!lz_barrier(sm, a.bar, target, a.err)) return;
   double inv = 1.0 / sqrt(cta_ordered_sum(sm, part, G, ldp));
-  for (long long e = lo + threadIdx.x; e < hi; e += kLThreads)
-    __stcg(a.basis + e, __ldcg(a.V + e) * inv);
+  for (int q = threadIdx.x; q < nown; q += kLThreads) {
+    const long long e = own_index(q, bid, G, nt, c);
+    if (e >= 0) __stcg(a.basis + e, __ldcg(a.V + e) * inv);
+  }
   if (!lz_barrier(sm, a.bar, target, a.err)) return;
 
   int conv = 0;
@@ -289,8 +329,8 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
     for (int j = 0; j < m; ++j) {
       const double* x = a.basis + (long long)j * n;
       // phase A: Y_b = Op_b x for the 2K operators A_k0, B_k0 (stored after o_0)
-      for (int it = bid; it < 2 * K * nt * nt; it += G) {
-        const int b = it / (nt * nt), t = it % (nt * nt);
+      for (int it = bid; it < 2 * K * ntiles; it += G) {
+        const int b = it / ntiles, t = it % ntiles;
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
         stage_rows(sm.L, a.s0 + (long long)(1 + b) * n, c, i0, 1.0);
         stage_cols(sm.R, x, c, j0, 1.0);
@@ -300,8 +340,9 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
         tile_store(sm, a0, a1, a.Y + (long long)b * n, c, i0, j0);
       }
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
-      // phase B: w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T
-      for (int t = bid; t < nt * nt; t += G) {
+      // phase B: w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T on the
+      // owned tiles, then their projections on basis_0..j and |w|^2
+      for (int t = bid; t < ntiles; t += G) {
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
         double a0 = 0.0, a1 = 0.0;
         for (int term = 0; term < 2 + 2 * K; ++term) {
@@ -323,43 +364,63 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
         }
         tile_store(sm, a0, a1, a.w, c, i0, j0);
       }
+      own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
-      // two classical Gram-Schmidt passes against basis_0..j
-      double alpha_j = 0.0;
-      for (int pass = 0; pass < 2; ++pass) {
-        // partial dots of w with basis_0..j over this CTA's slice, one warp per vector
-        {
-          const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-          for (int i = warp; i <= j; i += kLWarps) {
-            const double* bi = a.basis + (long long)i * n;
-            double s = 0.0;
-            for (long long e = lo + lane; e < hi; e += 32) s = fma(__ldcg(bi + e), __ldcg(a.w + e), s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) __stcg(part + (long long)bid * ldp + i, s);
-          }
+      // coefficients of the first Gram-Schmidt pass and |w|^2 (one CTA each)
+      for (int i = bid; i <= j + 1; i += G) {
+        const double s = cta_ordered_sum(sm, part + (i > j ? nslot : i), G, ldp);
+        if (threadIdx.x == 0) __stcg(i > j ? wn2 : a.coef + i, s);
+      }
+      if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      // |w - sum c_i b_i|^2 = |w|^2 - sum c_i^2 for orthonormal b_i; when at
+      // least a quarter of |w|^2 remains, one pass is accurate to rounding
+      // (the second pass of "twice is enough" is needed only after heavy
+      // cancellation), and the norm needs no further reduction
+      const double w2 = __ldcg(wn2);
+      double c2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        const double ci = __ldcg(a.coef + i);
+        c2 = fma(ci, ci, c2);
+      }
+      const bool one_pass = w2 - c2 > 0.25 * w2;
+      double alpha_j = __ldcg(a.coef + j);
+      double beta_j;
+      if (one_pass) {
+        beta_j = sqrt(w2 - c2);
+      } else {
+        for (int q = threadIdx.x; q < nown; q += kLThreads) {
+          const long long e = own_index(q, bid, G, nt, c);
+          if (e < 0) continue;
+          double s = __ldcg(a.w + e);
+          for (int i = 0; i <= j; ++i)
+            s = fma(-__ldcg(a.coef + i), __ldcg(a.basis + (long long)i * n + e), s);
+          __stcg(a.w + e, s);
         }
+        __syncthreads();
+        own_projections(a, part, ldp, j, -1, nown, bid, G, nt, c, n);
         if (!lz_barrier(sm, a.bar, target, a.err)) return;
         for (int i = bid; i <= j; i += G) {
           const double s = cta_ordered_sum(sm, part + i, G, ldp);
-          if (threadIdx.x == 0) __stcg(a.coef + pass * ldp + i, s);
+          if (threadIdx.x == 0) __stcg(a.coef + ldp + i, s);
         }
         if (!lz_barrier(sm, a.bar, target, a.err)) return;
-        for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) {
+        for (int q = threadIdx.x; q < nown; q += kLThreads) {
+          const long long e = own_index(q, bid, G, nt, c);
+          if (e < 0) continue;
           double s = __ldcg(a.w + e);
           for (int i = 0; i <= j; ++i)
-            s = fma(-__ldcg(a.coef + pass * ldp + i), __ldcg(a.basis + (long long)i * n + e), s);
+            s = fma(-__ldcg(a.coef + ldp + i), __ldcg(a.basis + (long long)i * n + e), s);
           __stcg(a.w + e, s);
         }
-        // the next pass reads w with another thread-to-element map
         __syncthreads();
-        alpha_j += __ldcg(a.coef + pass * ldp + j);
+        alpha_j += __ldcg(a.coef + ldp + j);
+        {
+          const double s = own_dot(sm, a.w, a.w, nown, bid, G, nt, c);
+          if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
+        }
+        if (!lz_barrier(sm, a.bar, target, a.err)) return;
+        beta_j = sqrt(fmax(cta_ordered_sum(sm, part, G, ldp), 0.0));
       }
-      {
-        const double s = cta_dot(sm, a.w, a.w, lo, hi);
-        if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
-      }
-      if (!lz_barrier(sm, a.bar, target, a.err)) return;
-      const double beta_j = sqrt(fmax(cta_ordered_sum(sm, part, G, ldp), 0.0));
       tdim = j + 1;
       const bool breakdown = !(beta_j > 1e-12 * fmax(fabs(alpha_j) + beta_prev, 1e-300));
       if (bid == 0 && threadIdx.x == 0) {
@@ -368,10 +429,19 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
       }
       if (breakdown) break;
       beta_prev = beta_j;
-      // basis_{j+1} = w / beta_j
+      // basis_{j+1} = (w - sum c_i b_i) / beta_j (the projection is applied
+      // here on the one-pass path)
       inv = 1.0 / beta_j;
       double* nb = a.basis + (long long)(j + 1) * n;
-      for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) __stcg(nb + e, __ldcg(a.w + e) * inv);
+      for (int q = threadIdx.x; q < nown; q += kLThreads) {
+        const long long e = own_index(q, bid, G, nt, c);
+        if (e < 0) continue;
+        double s = __ldcg(a.w + e);
+        if (one_pass)
+          for (int i = 0; i <= j; ++i)
+            s = fma(-__ldcg(a.coef + i), __ldcg(a.basis + (long long)i * n + e), s);
+        __stcg(nb + e, s * inv);
+      }
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
     }
     // Ritz pair of the tridiagonal (CTA 0), then V = sum_i y_i basis_i
@@ -388,18 +458,23 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
     }
     if (!lz_barrier(sm, a.bar, target, a.err)) return;
     conv = __ldcg(a.flags);
-    for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) {
+    for (int q = threadIdx.x; q < nown; q += kLThreads) {
+      const long long e = own_index(q, bid, G, nt, c);
+      if (e < 0) continue;
       double s = 0.0;
       for (int i = 0; i < tdim; ++i) s = fma(__ldcg(a.y + i), __ldcg(a.basis + (long long)i * n + e), s);
       __stcg(a.V + e, s);
     }
+    __syncthreads();
     {
-      const double s = cta_dot(sm, a.V, a.V, lo, hi);
+      const double s = own_dot(sm, a.V, a.V, nown, bid, G, nt, c);
       if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
     }
     if (!lz_barrier(sm, a.bar, target, a.err)) return;
     inv = 1.0 / sqrt(cta_ordered_sum(sm, part, G, ldp));
-    for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) {
+    for (int q = threadIdx.x; q < nown; q += kLThreads) {
+      const long long e = own_index(q, bid, G, nt, c);
+      if (e < 0) continue;
       const double t = __ldcg(a.V + e) * inv;
       __stcg(a.V + e, t);
       __stcg(a.basis + e, t);
@@ -408,12 +483,15 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
   }
   // sign: <V, Vprev> >= 0
   {
-    const double s = cta_dot(sm, a.V, a.Vprev, lo, hi);
+    const double s = own_dot(sm, a.V, a.Vprev, nown, bid, G, nt, c);
     if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp + 1, s);
   }
   if (!lz_barrier(sm, a.bar, target, a.err)) return;
   if (cta_ordered_sum(sm, part + 1, G, ldp) < 0.0)
-    for (long long e = lo + threadIdx.x; e < hi; e += kLThreads) __stcg(a.V + e, -__ldcg(a.V + e));
+    for (int q = threadIdx.x; q < nown; q += kLThreads) {
+      const long long e = own_index(q, bid, G, nt, c);
+      if (e >= 0) __stcg(a.V + e, -__ldcg(a.V + e));
+    }
 }
 
 struct LzGrid {
