@@ -6,13 +6,16 @@
 // the way into shared memory, and the product is accumulated in FP32 tensor
 // memory as  A_l B_h + A_h B_l + A_h B_h  (3xTF32 / BF16x3) or A_h B_h alone.
 //
-// One CTA owns a 128 x BN output tile.  All 256 threads stage operand tiles
-// (any strides: the two-level K/batch index of GemmDesc), converting FP64 to
-// the MMA type and writing the K-major SWIZZLE_128B canonical layout; one
-// thread issues tcgen05.mma into a TMEM accumulator and commits to an
-// mbarrier per stage, so that staging of the next K tile overlaps the MMAs of
-// the current one (two stages).  The epilogue reads TMEM with tcgen05.ld and
-// writes FP64 (or a split-K partial).  Every mbarrier wait is bounded; on a
+// One CTA owns a 128 x BN output tile (BN <= 64).  All 256 threads stage
+// operand tiles (any strides: the two-level K/batch index of GemmDesc),
+// converting FP32 or FP64 to the MMA type and writing the K-major
+// SWIZZLE_128B canonical layout; one thread issues tcgen05.mma into a TMEM
+// accumulator and commits to an mbarrier per stage, so that staging of the
+// next K tile overlaps the MMAs of the current one (two stages).  Staging is
+// bound by the latency of its global loads, so the tiles are kept small enough
+// (<= 96 KB of shared memory, <= 128 registers) for two CTAs per SM, whose
+// loads overlap.  The epilogue reads TMEM with tcgen05.ld and writes FP32 or
+// FP64 (or a split-K partial).  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, waits (bounded) for its own MMAs,
 // frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -28,7 +31,7 @@ namespace {
 
 constexpr int kThreadsTC = 256;
 constexpr int kBM = 128;
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr long kWaitLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -426,7 +429,7 @@ void tc_configure() {
 }
 
 template <bool kBF16, bool kSplit, int BN>
-__global__ void __launch_bounds__(kThreadsTC, 1) gemm_tc_kernel(const GemmDesc d, TCParams tp) {
+__global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d, TCParams tp) {
   constexpr int BK = kBF16 ? 64 : 32;            // one 128-byte swizzle row
   constexpr int KSTEP = kBF16 ? 16 : 8;          // K of one tcgen05.mma
   constexpr int kA = kBM * 128;                  // bytes of one A tile (128 rows)
@@ -638,7 +641,7 @@ __global__ void splitk_reduce_tc(const GemmDesc d) {
   }
 }
 
-int tc_bn(int N) { return N >= 128 ? 128 : N >= 64 ? 64 : 32; }
+int tc_bn(int N) { return N >= 64 ? 64 : 32; }
 
 int tc_total_tiles(const GemmDesc& d, int BK) {
   int t = 0;

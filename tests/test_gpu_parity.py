@@ -85,6 +85,15 @@ def test_resync_tfim_l16_per_node():
     _resync_check(ti.tfim_chain(16, 1.0), 8, 0, per_node=True, warm=3, checks=3)
 
 
+def test_resync_per_node_tree_at_scale():
+    """One isometry per node on a 256-site chain (255 isometries, every layer's
+    nodes in one batched launch): the resynchronised sweep matches the oracle,
+    in FP64 and (to the tensor-core rounding) in 3xTF32."""
+    m = ti.tfim_chain(256, 1.0)
+    _resync_check(m, 16, 3, per_node=True, warm=4, checks=2)
+    _resync_check(m, 16, 3, per_node=True, warm=4, checks=1, tol=1e-5, prec="tf32x3")
+
+
 def test_resync_tfim_l1024_chi32():
     _resync_check(ti.tfim_chain(1024, 1.0), 32, 1, warm=5, checks=2)
 
