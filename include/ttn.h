@@ -99,6 +99,10 @@ typedef struct {
                                FP64 rounding), 2 = two long blocks (one Gram
                                matrix per ~1e5 of growth: half the FP64 work),
                                0 (default) = 1 in FP64 mode, 2 in mixed modes */
+  int polar_df;             /* mixed modes, 1 (default): the Gram and apply products
+                               of the first of several polar blocks in
+                               double-float arithmetic (FP32 pairs, ~48 bits) on
+                               the FP32 pipes; 0: FP64 */
 } ttn_options;
 
 /* Fill *opt with the defaults above. */
@@ -176,8 +180,10 @@ long long ttn_launch_count(ttn_t h);
  * events on the library's stream.  out[0..8] = FP64-engine milliseconds,
  * useful flops (2*M*N*K summed over groups and batches), launches; the same
  * three for the tensor-core engine; milliseconds and launches of all other
- * kernels (including event gaps); total milliseconds of the sweep.  The
- * sweep updates the tensors like ttn_sweep.  n_out >= 9. */
+ * kernels (including event gaps); total milliseconds of the sweep.  With
+ * n_out >= 12, out[9..11] = the same three for the double-float products
+ * (otherwise they count as "other").  The sweep updates the tensors like
+ * ttn_sweep.  n_out >= 9. */
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random

@@ -36,7 +36,7 @@ class Sweeper:
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
                  lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
-                 persistent=True, streams=8, polar_blocks=0):
+                 persistent=True, streams=8, polar_blocks=0, polar_df=True):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -66,6 +66,7 @@ class Sweeper:
         opt.persistent = 3 if persistent is True else (0 if persistent is False else int(persistent))
         opt.streams = int(streams)
         opt.polar_blocks = int(polar_blocks)
+        opt.polar_df = int(bool(polar_df))
         opt.top_mode = int(top_mode)
         if shift is not None:
             opt.shift = float(shift)
@@ -179,10 +180,10 @@ class Sweeper:
 
     def profile_sweep(self):
         """One eagerly launched sweep with every product timed by CUDA events."""
-        out = np.zeros(9)
-        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 9), "profile_sweep")
+        out = np.zeros(12)
+        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 12), "profile_sweep")
         keys = ["fp64_ms", "fp64_flops", "fp64_launches", "tc_ms", "tc_flops", "tc_launches",
-                "other_ms", "other_launches", "total_ms"]
+                "other_ms", "other_launches", "total_ms", "df_ms", "df_flops", "df_launches"]
         return dict(zip(keys, out.tolist()))
 
     @property

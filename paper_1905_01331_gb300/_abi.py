@@ -26,7 +26,8 @@ class Options(ctypes.Structure):
                 ("lanczos_restarts", ctypes.c_int), ("shift", ctypes.c_double),
                 ("polar_damping", ctypes.c_double), ("deterministic", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int),
+                ("polar_df", ctypes.c_int)]
 
 
 # Every symbol the header declares, with its signature.

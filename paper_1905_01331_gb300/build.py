@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttn.so")
 
-SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "misc.cu", "polar.cu", "lanczos.cu", "ttn.cu", "selftest.cu", "host_eig.cpp"]
+SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "misc.cu", "polar.cu", "lanczos.cu", "gemm_df.cu", "ttn.cu", "selftest.cu", "host_eig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr"]

@@ -181,6 +181,22 @@ int lanczos_grid(int c, int grid_share);
 // Returns the number of kernel launches (1), or -1 if the launch was refused.
 int lanczos_launch(const LanczosArgs& a, int grid, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Double-float products (gemm_df.cu): FP64 values held as FP32 pairs
+// (hi + lo), products accumulated in FP32 pairs on the FP32 pipes (~48
+// significant bits).  Used for the first polar block of the mixed modes.
+// ---------------------------------------------------------------------------
+// hi[i] = fl32(x[i]), lo[i] = fl32(x[i] - hi[i])
+int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s);
+// Split count of df_gram (its partial buffer holds splits * P * P doubles).
+int df_gram_splits(int P, int n2);
+// C (P x P, FP64) = X X^T for X (P x n2, row-major) given as (Xh, Xl).
+int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
+            cudaStream_t s);
+// C (P x n2, FP64) = F X for F (P x P) given as (Fh, Fl) and X as (Xh, Xl).
+int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
+             long long n2, double* C, cudaStream_t s);
+
 // dst[i] = (float) src[i]
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 

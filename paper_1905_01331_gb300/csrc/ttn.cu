@@ -626,6 +626,25 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
 }
 
 // w_t <- -polar(Gam - mu |Gam| w_t) by scaled Newton-Schulz blocks.
+// Profiling sweeps time the double-float products as engine 2: an event
+// before (df_begin) and after (df_end) each of them.
+void df_begin(ttn_ctx* h) {
+  if (!h->profiling) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, h->stream);
+  h->ev_pool.push_back(e);
+}
+void df_end(ttn_ctx* h, int launches, double flops) {
+  h->launches += launches;
+  if (!h->profiling) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, h->stream);
+  h->ev_pool.push_back(e);
+  h->ev_flops.push_back({2, flops});
+}
+
 // F = composed polynomial of one block from the Gram matrix in pA (one
 // cooperative launch; pA, pP, pT, pS are overwritten).
 void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ) {
@@ -681,12 +700,33 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   const bool short_blocks =
       h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && prec == 0);
   const std::vector<PolarBlock>& sched = short_blocks ? h->polar_f64 : h->polar_tc;
-  for (const PolarBlock& blk : sched) {
+  // Mixed modes: the first of several blocks in double-float arithmetic on the
+  // FP32 pipes (its rounding, ~1e-14, amplified by the block's growth stays
+  // far below the tensor-core rounding of the environment); the last block,
+  // which makes w an isometry, in FP64.  Operands in FP32 pairs: X in the
+  // one-leg scratch Y, F in Yt (both free during the polar step).
+  const bool df_ok = prec != 0 && h->opt.polar_df && NJ == 1 && P >= 32 && sched.size() > 1;
+  float* Xh = reinterpret_cast<float*>(h->Y);
+  float* Xl = Xh + PN;
+  float* Fh = reinterpret_cast<float*>(h->Yt);
+  float* Fl = Fh + PP;
+  if (df_ok && h->measuring)
+    h->partial_cap = std::max<size_t>(h->partial_cap, (size_t)df_gram_splits(P, (int)N) * PP);
+  for (size_t bi = 0; bi < sched.size(); ++bi) {
+    const PolarBlock& blk = sched[bi];
+    const bool df = df_ok && bi == 0 && !h->measuring;
+    if (df) {
+      h->launches += df_split(X, Xh, Xl, PN, h->stream);
+      df_begin(h);
+      df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
+             2.0 * ((P + 31) / 32) * ((P + 31) / 32 + 1) / 2 * 32 * 32 * (double)N);
+    } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
     add(g, grp(op(X, N, 1, 0, 0, PN), op(X, N, 1, 0, 0, PN), (int)N));
     g.sym = 1;
     run(h, g, 0);
+    }
     if ((h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size())) {
       if (!h->measuring) compose_block(h, blk, P, NJ);
     } else {
@@ -714,11 +754,17 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     }
     }
     // X2 = F X ; swap.  F amplifies the small singular directions by up to
-    // 1/damping, so this product is FP64 in every mode (a tensor-core product
-    // of it would lose those directions to cancellation).
+    // 1/damping, so this product is FP64 (or double-float) in every mode (a
+    // tensor-core product of it would lose those directions to cancellation).
+    if (df) {
+      h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
+      df_begin(h);
+      df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
+    } else {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
     run(h, f, 0);
+    }
     std::swap(X, X2);
   }
   if (!h->measuring) {
@@ -984,6 +1030,7 @@ void ttn_default_options(ttn_options* o) {
   o->persistent = 3;
   o->streams = 8;
   o->polar_blocks = 0;
+  o->polar_df = 1;
 }
 
 // Instances go to min(streams, instances) lanes, longest first onto the least
@@ -1458,7 +1505,7 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   h->profiling = false;
   int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
   if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
-  double ms[2] = {0, 0}, fl[2] = {0, 0}, cnt[2] = {0, 0};
+  double ms[3] = {0, 0, 0}, fl[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
   for (size_t i = 0; i < h->ev_flops.size(); ++i) {
     float e = 0.f;
     cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
@@ -1476,7 +1523,10 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   cudaEventDestroy(t1);
   out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
   out[3] = ms[1]; out[4] = fl[1]; out[5] = cnt[1];
-  out[6] = tot - ms[0] - ms[1]; out[7] = (double)h->launches - cnt[0] - cnt[1]; out[8] = tot;
+  out[6] = tot - ms[0] - ms[1] - ms[2];
+  out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2];
+  out[8] = tot;
+  if (n_out >= 12) { out[9] = ms[2]; out[10] = fl[2]; out[11] = cnt[2]; }
   h->sweeps_done += 1;
   return rc;
 }
