@@ -184,7 +184,7 @@ int lanczos_launch(const LanczosArgs& a, int grid, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // Double-float products (gemm_df.cu): FP64 values held as FP32 pairs
 // (hi + lo), products accumulated in FP32 pairs on the FP32 pipes (~48
-// significant bits).  Used for the first polar block of the mixed modes.
+// significant bits).  Used for the polar factor of the mixed modes.
 // ---------------------------------------------------------------------------
 // hi[i] = fl32(x[i]), lo[i] = fl32(x[i] - hi[i])
 int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s);

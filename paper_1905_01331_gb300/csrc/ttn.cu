@@ -700,11 +700,13 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   const bool short_blocks =
       h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && prec == 0);
   const std::vector<PolarBlock>& sched = short_blocks ? h->polar_f64 : h->polar_tc;
-  // Mixed modes: the first of several blocks in double-float arithmetic on the
-  // FP32 pipes (its rounding, ~1e-14, amplified by the block's growth stays
-  // far below the tensor-core rounding of the environment); the last block,
-  // which makes w an isometry, in FP64.  Operands in FP32 pairs: X in the
-  // one-leg scratch Y, F in Yt (both free during the polar step).
+  // Mixed modes: every block's Gram and apply products in double-float
+  // arithmetic on the FP32 pipes (~48 bits: the rounding amplified by a
+  // block's growth stays far below the tensor-core rounding of the
+  // environment), then one more Newton-Schulz step X <- (1.5 I - 0.5 X X^T) X
+  // that takes the isometry defect from ~1e-11 to ~1e-14.  Operands in FP32
+  // pairs: X in the one-leg scratch Y, F in Yt (both free during the polar
+  // step).
   const bool df_ok = prec != 0 && h->opt.polar_df && NJ == 1 && P >= 32 && sched.size() > 1;
   float* Xh = reinterpret_cast<float*>(h->Y);
   float* Xl = Xh + PN;
@@ -714,7 +716,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->partial_cap = std::max<size_t>(h->partial_cap, (size_t)df_gram_splits(P, (int)N) * PP);
   for (size_t bi = 0; bi < sched.size(); ++bi) {
     const PolarBlock& blk = sched[bi];
-    const bool df = df_ok && bi == 0 && !h->measuring;
+    const bool df = df_ok && !h->measuring;
     if (df) {
       h->launches += df_split(X, Xh, Xl, PN, h->stream);
       df_begin(h);
@@ -765,6 +767,17 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
     run(h, f, 0);
     }
+    std::swap(X, X2);
+  }
+  if (df_ok && !h->measuring) {
+    h->launches += df_split(X, Xh, Xl, PN, h->stream);
+    df_begin(h);
+    df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
+           2.0 * ((P + 31) / 32) * ((P + 31) / 32 + 1) / 2 * 32 * 32 * (double)N);
+    h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
+    h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
+    df_begin(h);
+    df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
     std::swap(X, X2);
   }
   if (!h->measuring) {
