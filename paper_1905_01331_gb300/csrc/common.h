@@ -142,7 +142,9 @@ bool compose_supported(int P, int nsteps);
 // FP64 flops the composition kernel executes (symmetric tiles only).
 double compose_flops(int P, int NJ, int nsteps);
 // Returns the number of kernel launches (1), or -1 if the launch was refused.
-int polar_compose(const ComposeArgs& a, cudaStream_t s);
+// df: the five buffers hold FP32 pairs (hi at p, lo at p + P*P floats; block b
+// at p + 2*b*P*P floats) and the products run in double-float arithmetic.
+int polar_compose(const ComposeArgs& a, cudaStream_t s, bool df = false);
 
 // ---------------------------------------------------------------------------
 // Top solve (lanczos.cu): restarted FP64 Lanczos for the lowest eigenvector of

@@ -177,27 +177,260 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_kernel(const ComposeA
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same composition in double-float arithmetic (mixed modes): every matrix
+// is a pair of FP32 arrays (hi at p, lo at p + P*P, block b of NJ at
+// p + 2*b*P*P floats), products accumulate in FP32 pairs on the FP32 pipes
+// (~48 significant bits; see gemm_df.cu), and Pm_j and the step coefficients
+// are applied in pair arithmetic while operands are staged.  A_j is used as
+// computed, without the symmetrisation of the FP64 kernel: the step formulas
+// keep every matrix of the block a polynomial in A_j whether or not rounding
+// keeps it symmetric, the block's error is set by the pairs' 48-bit rounding,
+// and the polar factor's final Newton-Schulz step restores the isometry.
+// Without the transposed reads the staging takes half as long.  F ends as
+// pairs, the operand format of the double-float apply.
+// ---------------------------------------------------------------------------
+
+struct ComposeDFSmem {
+  float Xh[kCT][kCMaxP + 1], Xl[kCT][kCMaxP + 1];
+  float Yh[kCT][kCMaxP + 1], Yl[kCT][kCMaxP + 1];
+  float rh[kCWarps][kCT * kCT], rl[kCWarps][kCT * kCT];
+  int ok;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (ah + al) + (bh + bl), renormalised
+__device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl, float& rh,
+                                         float& rl) {
+  float s, e;
+  two_sum_f(ah, bh, s, e);
+  e += al + bl;
+  rh = s + e;
+  rl = e - (rh - s);
+}
+
+// (ah + al) (ch + cl), renormalised
+__device__ __forceinline__ void pair_mul(float ah, float al, float ch, float cl, float& rh,
+                                         float& rl) {
+  const float p = ah * ch;
+  float pe = fmaf(ah, ch, -p);
+  pe = fmaf(ah, cl, fmaf(al, ch, pe));
+  rh = p + pe;
+  rl = pe - (rh - p);
+}
+
+__device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl, float& sh,
+                                         float& sl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);
+  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
+  float s, e;
+  two_sum_f(sh, p, s, e);
+  sl += e + c;
+  sh = s;
+}
+
+__device__ __forceinline__ void split_d(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+// Element (i, k) of dx I + sx S(M), S(M) = (M + M^T)/2 when sym, else M; M a
+// pair matrix (hi at M, lo at M + PP).  (dxh, dxl), (sxh, sxl): pairs.
+__device__ __forceinline__ void stage_elem(const float* M, long long PP, int P, int i, int k,
+                                           bool sym, float dxh, float dxl, float sxh, float sxl,
+                                           float& vh, float& vl) {
+  float mh = __ldcg(M + (long long)i * P + k), ml = __ldcg(M + PP + (long long)i * P + k);
+  if (sym) {
+    const float th = __ldcg(M + (long long)k * P + i), tl = __ldcg(M + PP + (long long)k * P + i);
+    pair_add(mh, ml, th, tl, mh, ml);
+    mh *= 0.5f;
+    ml *= 0.5f;
+  }
+  if (sxh != 1.f || sxl != 0.f) pair_mul(mh, ml, sxh, sxl, mh, ml);
+  if (i == k && (dxh != 0.f || dxl != 0.f)) pair_add(mh, ml, dxh, dxl, mh, ml);
+  vh = mh;
+  vl = ml;
+}
+
+// Tile (i0, j0) of X' Y' in pair arithmetic (see tile_product); element (r, c)
+// = (tid / 8, tid % 8) returned in (vh, vl) for tid < 64.
+__device__ void tile_product_df(ComposeDFSmem& sm, const float* X, float dxh, float dxl,
+                                float sxh, float sxl, bool symx, const float* Y, float dyh,
+                                float dyl, float syh, float syl, bool symy, int P, int i0, int j0,
+                                float& vh, float& vl) {
+  const long long PP = (long long)P * P;
+  for (int e = threadIdx.x; e < kCT * P; e += kCThreads) {
+    {
+      const int r = e / P, k = e - (e / P) * P;
+      const int gi = i0 + r;
+      float h = 0.f, l = 0.f;
+      if (gi < P) stage_elem(X, PP, P, gi, k, symx, dxh, dxl, sxh, sxl, h, l);
+      sm.Xh[r][k] = h;
+      sm.Xl[r][k] = l;
+    }
+    {
+      // column gj of Y = row gj of Y^T: element (k, gj)
+      const int k = e / kCT, c = e - (e / kCT) * kCT;
+      const int gj = j0 + c;
+      float h = 0.f, l = 0.f;
+      if (gj < P) stage_elem(Y, PP, P, k, gj, symy, dyh, dyl, syh, syl, h, l);
+      sm.Yh[c][k] = h;
+      sm.Yl[c][k] = l;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane >> 2, j = (lane & 3) * 2;
+  float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+  int n = 0;
+  for (int k = warp; k < P; k += kCWarps) {
+    const float xh = sm.Xh[i][k], xl = sm.Xl[i][k];
+    pair_mac(xh, xl, sm.Yh[j][k], sm.Yl[j][k], a0h, a0l);
+    pair_mac(xh, xl, sm.Yh[j + 1][k], sm.Yl[j + 1][k], a1h, a1l);
+    if (++n == 8) {
+      n = 0;
+      pair_add(a0h, a0l, 0.f, 0.f, a0h, a0l);
+      pair_add(a1h, a1l, 0.f, 0.f, a1h, a1l);
+    }
+  }
+  sm.rh[warp][i * kCT + j] = a0h;
+  sm.rl[warp][i * kCT + j] = a0l;
+  sm.rh[warp][i * kCT + j + 1] = a1h;
+  sm.rl[warp][i * kCT + j + 1] = a1l;
+  __syncthreads();
+  vh = 0.f;
+  vl = 0.f;
+  if (threadIdx.x < kCT * kCT)
+    for (int w = 0; w < kCWarps; ++w)
+      pair_add(vh, vl, sm.rh[w][threadIdx.x], sm.rl[w][threadIdx.x], vh, vl);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_tile_df(float* C, int P, int ti, int tj, float vh, float vl) {
+  if (threadIdx.x >= kCT * kCT) return;
+  const int gi = ti * kCT + threadIdx.x / kCT, gj = tj * kCT + threadIdx.x % kCT;
+  if (gi < P && gj < P) {
+    const long long PP = (long long)P * P;
+    __stcg(C + (long long)gi * P + gj, vh);
+    __stcg(C + PP + (long long)gi * P + gj, vl);
+  }
+}
+
+__device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int spins = 0;
+    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+      if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
+      if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
+      __nanosleep(128);
+    }
+    __threadfence();
+    sm.ok = ok;
+  }
+  __syncthreads();
+  return sm.ok != 0;
+}
+
+__global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const ComposeArgs a) {
+  __shared__ ComposeDFSmem sm;
+  const int P = a.P, ns = a.nsteps;
+  const int nt = (P + kCT - 1) / kCT, ntt = nt * nt;
+  const long long P2 = 2LL * P * P;               // floats per pair matrix
+  float* A0 = reinterpret_cast<float*>(a.A0);
+  float* A1 = reinterpret_cast<float*>(a.A1);
+  float* F = reinterpret_cast<float*>(a.F);
+  float* S = reinterpret_cast<float*>(a.S);
+  float* T = reinterpret_cast<float*>(a.T);
+  auto Fbuf = [&](int j) { return ((ns - j) & 1) ? S : F; };
+  unsigned target = 0;
+  for (int j = 0; j < ns; ++j) {
+    float alh, all, mbh, mbl;
+    split_d(a.alpha[j], alh, all);
+    split_d(-a.beta[j], mbh, mbl);
+    const bool last = j + 1 == ns;
+    const float* Aj = (j & 1) ? A1 : A0;
+    float* An = (j & 1) ? A0 : A1;
+    float* Fn = Fbuf(j + 1);
+    const int np = (j > 0 ? 1 : 0) + (last ? 0 : 1);
+    const int items1 = np * ntt * a.NJ;
+    for (int it = blockIdx.x; it < items1; it += gridDim.x) {
+      const int b = it / (np * ntt);
+      const int u = it % (np * ntt);
+      const bool isF = j > 0 && u < ntt;
+      const int ti = (u % ntt) / nt, tj = (u % ntt) % nt;
+      const float* Ab = Aj + b * P2;
+      float vh, vl;
+      if (isF)
+        tile_product_df(sm, Ab, alh, all, mbh, mbl, false, Fbuf(j) + b * P2, 0.f, 0.f, 1.f, 0.f,
+                        false, P, ti * kCT, tj * kCT, vh, vl);
+      else
+        tile_product_df(sm, Ab, 0.f, 0.f, 1.f, 0.f, false, Ab, alh, all, mbh, mbl, false, P,
+                        ti * kCT, tj * kCT, vh, vl);
+      store_tile_df((isF ? Fn : T) + b * P2, P, ti, tj, vh, vl);
+    }
+    if (j == 0) {
+      // F_1 = Pm_0, elementwise
+      const long long PP = (long long)P * P;
+      for (long long e = blockIdx.x * (long long)kCThreads + threadIdx.x; e < a.NJ * PP;
+           e += (long long)gridDim.x * kCThreads) {
+        const long long b = e / PP, r = e % PP;
+        float h, l;
+        stage_elem(Aj + b * P2, PP, P, (int)(r / P), (int)(r % P), false, alh, all, mbh, mbl, h, l);
+        __stcg(Fn + b * P2 + r, h);
+        __stcg(Fn + b * P2 + PP + r, l);
+      }
+    }
+    if (last) break;
+    target += gridDim.x;
+    if (!grid_barrier_df(sm, a.bar, target, a.err)) return;
+    const int items2 = ntt * a.NJ;
+    for (int it = blockIdx.x; it < items2; it += gridDim.x) {
+      const int b = it / ntt, ti = (it % ntt) / nt, tj = (it % ntt) % nt;
+      float vh, vl;
+      tile_product_df(sm, Aj + b * P2, alh, all, mbh, mbl, false, T + b * P2, 0.f, 0.f, 1.f, 0.f,
+                      false, P, ti * kCT, tj * kCT, vh, vl);
+      store_tile_df(An + b * P2, P, ti, tj, vh, vl);
+    }
+    target += gridDim.x;
+    if (!grid_barrier_df(sm, a.bar, target, a.err)) return;
+  }
+}
+
 struct DeviceGrid {
-  int sms = 0, per_sm = 0;
+  int sms = 0, per_sm = 0, per_sm_df = 0;
 };
 std::mutex g_grid_mutex;
 DeviceGrid g_grid[64];
 
-int compose_grid_cap() {
+int compose_grid_cap(bool df) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lock(g_grid_mutex);
   DeviceGrid& g = g_grid[dev];
   if (!g.sms) {
-    int sms = 0, occ = 0;
+    int sms = 0, occ = 0, occ_df = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, polar_compose_kernel, kCThreads, 0) !=
         cudaSuccess)
       return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_df, polar_compose_df_kernel, kCThreads,
+                                                      0) != cudaSuccess)
+      return 0;
     g.sms = sms;
     g.per_sm = std::min(occ, 2);
+    g.per_sm_df = std::min(occ_df, 2);
   }
-  return g.sms * g.per_sm;
+  return g.sms * (df ? g.per_sm_df : g.per_sm);
 }
 
 }  // namespace
@@ -217,9 +450,9 @@ double compose_flops(int P, int NJ, int nsteps) {
   return f;
 }
 
-int polar_compose(const ComposeArgs& a, cudaStream_t s) {
+int polar_compose(const ComposeArgs& a, cudaStream_t s, bool df) {
   if (!compose_supported(a.P, a.nsteps)) return -1;
-  int cap = compose_grid_cap();
+  int cap = compose_grid_cap(df);
   if (cap <= 0) return -1;
   if (a.grid_share > 1) cap = std::max(1, cap / a.grid_share);
   const int nt = (a.P + kCT - 1) / kCT;
@@ -235,8 +468,9 @@ int polar_compose(const ComposeArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, polar_compose_kernel, a) != cudaSuccess) return -1;
-  return 1;
+  const cudaError_t e = df ? cudaLaunchKernelEx(&cfg, polar_compose_df_kernel, a)
+                           : cudaLaunchKernelEx(&cfg, polar_compose_kernel, a);
+  return e == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace ttn

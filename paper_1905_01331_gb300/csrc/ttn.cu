@@ -647,9 +647,11 @@ void df_end(ttn_ctx* h, int launches, double flops) {
 
 // F = composed polynomial of one block from the Gram matrix in pA (one
 // cooperative launch; pA, pP, pT, pS are overwritten).
-void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ) {
+void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
   ComposeArgs a;
-  a.A0 = h->pA; a.A1 = h->pP; a.F = h->pF; a.T = h->pT; a.S = h->pS;
+  // double-float: A_0 arrives as pairs in pP (split from the FP64 Gram in pA)
+  a.A0 = df ? h->pP : h->pA; a.A1 = df ? h->pA : h->pP;
+  a.F = h->pF; a.T = h->pT; a.S = h->pS;
   a.P = P; a.NJ = NJ; a.nsteps = (int)blk.steps.size();
   for (int j = 0; j < a.nsteps; ++j) {
     a.alpha[j] = blk.steps[j].first;
@@ -664,7 +666,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ) {
     cudaEventCreate(&ev[1]);
     cudaEventRecord(ev[0], h->stream);
   }
-  const int n = polar_compose(a, h->stream);
+  const int n = polar_compose(a, h->stream, df);
   if (n < 0) {
     // the launch was refused: the flag turns the sweep into an error
     h->compose_refused = true;
@@ -675,7 +677,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ) {
     cudaEventRecord(ev[1], h->stream);
     h->ev_pool.push_back(ev[0]);
     h->ev_pool.push_back(ev[1]);
-    h->ev_flops.push_back({0, compose_flops(P, NJ, a.nsteps)});
+    h->ev_flops.push_back({df ? 2 : 0, compose_flops(P, NJ, a.nsteps)});
   }
 }
 
@@ -729,8 +731,11 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     g.sym = 1;
     run(h, g, 0);
     }
-    if ((h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size())) {
-      if (!h->measuring) compose_block(h, blk, P, NJ);
+    const bool kernel = (h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size());
+    if (kernel) {
+      if (df) h->launches += df_split(h->pA, reinterpret_cast<float*>(h->pP),
+                                      reinterpret_cast<float*>(h->pP) + PP, PP, h->stream);
+      if (!h->measuring) compose_block(h, blk, P, NJ, df);
     } else {
     if (!h->measuring) h->launches += set_identity(h->pF, P, NJ, h->stream);
     for (size_t j = 0; j < blk.steps.size(); ++j) {
@@ -759,9 +764,16 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     // 1/damping, so this product is FP64 (or double-float) in every mode (a
     // tensor-core product of it would lose those directions to cancellation).
     if (df) {
-      h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
+      // F as pairs: straight from the double-float composition, else split
+      const float* Fah = reinterpret_cast<const float*>(h->pF);
+      const float* Fal = Fah + PP;
+      if (!kernel) {
+        h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
+        Fah = Fh;
+        Fal = Fl;
+      }
       df_begin(h);
-      df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
+      df_end(h, df_apply(Fah, Fal, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
     } else {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
