@@ -99,11 +99,12 @@ typedef struct {
                                FP64 rounding), 2 = two long blocks (one Gram
                                matrix per ~1e5 of growth: half the FP64 work),
                                0 (default) = 1 in FP64 mode, 2 in mixed modes */
-  int polar_df;             /* mixed modes, 1 (default): the Gram and apply products
-                               of the polar factor in double-float arithmetic
-                               (FP32 pairs, ~48 bits) on the FP32 pipes, plus one
-                               final Newton-Schulz step (isometry to ~1e-14);
-                               0: FP64 */
+  int double_float;         /* mixed modes, 1 (default): the polar factor's products
+                               (Gram matrices, composition, apply, plus one final
+                               Newton-Schulz step: isometry to ~1e-14) and the
+                               Lanczos top solve's matrix-vector products in
+                               double-float arithmetic (FP32 pairs, ~48 bits) on
+                               the FP32 pipes; 0: FP64 */
 } ttn_options;
 
 /* Fill *opt with the defaults above. */

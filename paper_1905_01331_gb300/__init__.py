@@ -36,7 +36,7 @@ class Sweeper:
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
                  lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
-                 persistent=True, streams=8, polar_blocks=0, polar_df=True):
+                 persistent=True, streams=8, polar_blocks=0, double_float=True):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -66,7 +66,7 @@ class Sweeper:
         opt.persistent = 3 if persistent is True else (0 if persistent is False else int(persistent))
         opt.streams = int(streams)
         opt.polar_blocks = int(polar_blocks)
-        opt.polar_df = int(bool(polar_df))
+        opt.double_float = int(bool(double_float))
         opt.top_mode = int(top_mode)
         if shift is not None:
             opt.shift = float(shift)

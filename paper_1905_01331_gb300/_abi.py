@@ -27,7 +27,7 @@ class Options(ctypes.Structure):
                 ("polar_damping", ctypes.c_double), ("deterministic", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int),
-                ("polar_df", ctypes.c_int)]
+                ("double_float", ctypes.c_int)]
 
 
 # Every symbol the header declares, with its signature.

@@ -176,6 +176,15 @@ struct LanczosArgs {
   double tol;
   unsigned* bar;
   int* err;
+  // double-float matrix-vector products (mixed modes): df != 0 and pair
+  // buffers (each matrix or vector: n hi floats, then n lo floats) for the
+  // operators of both top sites ((1+2K) matrices each; s1p unused when s1 ==
+  // s0), the basis (m+1 vectors) and Y (2K matrices)
+  int df;
+  float* s0p;
+  float* s1p;
+  float* bp;
+  float* Yp;
 };
 bool lanczos_supported(int c, int m);
 // CTAs of the launch for top dimension c when grid_share streams share the GPU.

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "pair_arith.cuh"
 
 namespace ttn {
 
@@ -27,30 +28,8 @@ constexpr int kDBK = 16;
 // x -> (hi, lo) with hi = fl32(x), lo = fl32(x - hi)
 __global__ void split_f64_kernel(const double* x, float* hi, float* lo, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float h = __double2float_rn(v);
-    hi[i] = h;
-    lo[i] = __double2float_rn(v - (double)h);
-  }
-}
-
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh,
-                                       float& sl) {
-  const float p = ah * bh;
-  const float pe = fmaf(ah, bh, -p);
-  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
-  const float s = sh + p;
-  const float bb = s - sh;
-  const float e = (sh - (s - bb)) + (p - bb);
-  sl += e + c;
-  sh = s;
-}
-
-__device__ __forceinline__ void df_renorm(float& sh, float& sl) {
-  const float s = sh + sl;
-  sl = sl - (s - sh);
-  sh = s;
+       i += (long long)gridDim.x * blockDim.x)
+    split_d(x[i], hi[i], lo[i]);
 }
 
 // C (FP64) = A B for A: M x K rows (K contiguous), B either K-major (element
@@ -114,12 +93,12 @@ __global__ void __launch_bounds__(kDThreads) gemm_df_kernel(
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) df_mac(ah[i], al[i], bh[j], bl[j], sh[i][j], sl[i][j]);
+        for (int j = 0; j < TN; ++j) pair_mac(ah[i], al[i], bh[j], bl[j], sh[i][j], sl[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) df_renorm(sh[i][j], sl[i][j]);
+      for (int j = 0; j < TN; ++j) pair_renorm(sh[i][j], sl[i][j]);
     __syncthreads();
   }
 

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "pair_arith.cuh"
 
 namespace ttn {
 
@@ -240,6 +241,102 @@ __device__ void ritz_pair(LzSmem& sm, const double* alpha, const double* beta, i
   *res = fabs(beta[m - 1] * x[m - 1]);
 }
 
+// Double-float matrix-vector products (mixed modes): matrices and vectors as
+// FP32 pairs (hi block of n floats, then lo block), tiles staged into the
+// shared arrays L and R reinterpreted as hi/lo float rows.
+using FRow = float[kLMaxC + 1];
+
+__device__ __forceinline__ FRow* frows(double (*d)[kLMaxC + 1], int half) {
+  return reinterpret_cast<FRow*>(&d[0][0]) + half * kLT;
+}
+
+// rows [r0, r0+8) of the pair matrix M (hi at M, lo at M + n)
+__device__ void stage_rows_p(double (*dst)[kLMaxC + 1], const float* M, long long n, int c,
+                             int r0) {
+  FRow* h = frows(dst, 0);
+  FRow* l = frows(dst, 1);
+  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
+    const int r = e / c, k = e - r * c;
+    const bool ok = r0 + r < c;
+    const long long i = (long long)(r0 + r) * c + k;
+    h[r][k] = ok ? __ldcg(M + i) : 0.f;
+    l[r][k] = ok ? __ldcg(M + n + i) : 0.f;
+  }
+}
+// columns [c0, c0+8) of M as rows: dst[j][k] = M[k][c0 + j]
+__device__ void stage_cols_p(double (*dst)[kLMaxC + 1], const float* M, long long n, int c,
+                             int c0) {
+  FRow* h = frows(dst, 0);
+  FRow* l = frows(dst, 1);
+  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
+    const int k = e / kLT, j = e - k * kLT;
+    const bool ok = c0 + j < c;
+    const long long i = (long long)k * c + c0 + j;
+    h[j][k] = ok ? __ldcg(M + i) : 0.f;
+    l[j][k] = ok ? __ldcg(M + n + i) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void tile_fma_p(LzSmem& sm, int c, float& a0h, float& a0l, float& a1h,
+                                           float& a1l) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane >> 2, j = (lane & 3) * 2;
+  const FRow* Lh = frows(sm.L, 0);
+  const FRow* Ll = frows(sm.L, 1);
+  const FRow* Rh = frows(sm.R, 0);
+  const FRow* Rl = frows(sm.R, 1);
+  int cnt = 0;
+  for (int k = warp; k < c; k += kLWarps) {
+    const float xh = Lh[i][k], xl = Ll[i][k];
+    pair_mac(xh, xl, Rh[j][k], Rl[j][k], a0h, a0l);
+    pair_mac(xh, xl, Rh[j + 1][k], Rl[j + 1][k], a1h, a1l);
+    if (++cnt == 8) {
+      cnt = 0;
+      pair_renorm(a0h, a0l);
+      pair_renorm(a1h, a1l);
+    }
+  }
+  pair_renorm(a0h, a0l);
+  pair_renorm(a1h, a1l);
+}
+
+// Reduce the per-warp pair partial sums of a tile in warp order; store it as
+// pairs (Cp) or as FP64 (Cd).
+__device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float a1l, float* Cp,
+                             double* Cd, long long n, int c, int i0, int j0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane >> 2, j = (lane & 3) * 2;
+  float* rh = reinterpret_cast<float*>(&sm.red[0][0]);
+  float* rl = rh + kLWarps * kLT * kLT;
+  rh[warp * 64 + i * kLT + j] = a0h;
+  rl[warp * 64 + i * kLT + j] = a0l;
+  rh[warp * 64 + i * kLT + j + 1] = a1h;
+  rl[warp * 64 + i * kLT + j + 1] = a1l;
+  __syncthreads();
+  if (threadIdx.x < kLT * kLT) {
+    float vh = 0.f, vl = 0.f;
+    for (int w = 0; w < kLWarps; ++w) pair_add(vh, vl, rh[w * 64 + threadIdx.x], rl[w * 64 + threadIdx.x], vh, vl);
+    const int r = threadIdx.x / kLT, cc = threadIdx.x % kLT;
+    if (i0 + r < c && j0 + cc < c) {
+      const long long e = (long long)(i0 + r) * c + j0 + cc;
+      if (Cp) { __stcg(Cp + e, vh); __stcg(Cp + n + e, vl); }
+      if (Cd) __stcg(Cd + e, (double)vh + (double)vl);
+    }
+  }
+  __syncthreads();
+}
+
+// FP64 value and its pair at index e of a vector (pair vector: hi at P, lo at P + n)
+__device__ __forceinline__ void store_both(double* D, float* P, long long n, long long e, double v) {
+  __stcg(D + e, v);
+  if (P) {
+    float h, l;
+    split_d(v, h, l);
+    __stcg(P + e, h);
+    __stcg(P + n + e, l);
+  }
+}
+
 // Vector entries owned by a CTA: the entries of the 8 x 8 tiles of H x that
 // the CTA computes (tiles t = bid, bid + G, ...), so that the projections of a
 // new w start without a grid barrier.  Local index q -> global index, or -1
@@ -305,7 +402,24 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
   double* wn2 = a.coef + 2 * ldp - 1;        // |w|^2 of the current step
   unsigned target = 0;
 
-  // start: Vprev = V, basis_0 = V / |V|
+  const bool df = a.df != 0;
+  float* bp0 = df ? a.bp : nullptr;          // pairs of basis_0
+  // start: the operators as pairs (double-float mode), Vprev = V, basis_0 = V / |V|
+  if (df) {
+    const long long nops = (long long)(1 + 2 * K) * n;
+    const long long gt = (long long)blockIdx.x * kLThreads + threadIdx.x, gs = (long long)G * kLThreads;
+    for (int side = 0; side < (a.s1 == a.s0 ? 1 : 2); ++side) {
+      const double* src = side ? a.s1 : a.s0;
+      float* dst = side ? a.s1p : a.s0p;
+      for (long long e = gt; e < nops; e += gs) {
+        const long long q = e / n, r = e % n;
+        float h, l;
+        split_d(__ldcg(src + e), h, l);
+        __stcg(dst + 2 * q * n + r, h);
+        __stcg(dst + 2 * q * n + n + r, l);
+      }
+    }
+  }
   for (int q = threadIdx.x; q < nown; q += kLThreads) {
     const long long e = own_index(q, bid, G, nt, c);
     if (e >= 0) __stcg(a.Vprev + e, __ldcg(a.V + e));
@@ -318,9 +432,11 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
   double inv = 1.0 / sqrt(cta_ordered_sum(sm, part, G, ldp));
   for (int q = threadIdx.x; q < nown; q += kLThreads) {
     const long long e = own_index(q, bid, G, nt, c);
-    if (e >= 0) __stcg(a.basis + e, __ldcg(a.V + e) * inv);
+    if (e >= 0) store_both(a.basis, bp0, n, e, __ldcg(a.V + e) * inv);
   }
   if (!lz_barrier(sm, a.bar, target, a.err)) return;
+  const float* s0p = a.s0p;
+  const float* s1p = a.s1 == a.s0 ? a.s0p : a.s1p;
 
   int conv = 0;
   for (int cyc = 0; cyc < a.restarts && !conv; ++cyc) {
@@ -329,9 +445,19 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
     for (int j = 0; j < m; ++j) {
       const double* x = a.basis + (long long)j * n;
       // phase A: Y_b = Op_b x for the 2K operators A_k0, B_k0 (stored after o_0)
+      const float* xp = df ? a.bp + 2 * (long long)j * n : nullptr;
       for (int it = bid; it < 2 * K * ntiles; it += G) {
         const int b = it / ntiles, t = it % ntiles;
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
+        if (df) {
+          stage_rows_p(sm.L, s0p + 2 * (long long)(1 + b) * n, n, c, i0);
+          stage_cols_p(sm.R, xp, n, c, j0);
+          __syncthreads();
+          float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+          tile_fma_p(sm, c, a0h, a0l, a1h, a1l);
+          tile_store_p(sm, a0h, a0l, a1h, a1l, a.Yp + 2 * (long long)b * n, nullptr, n, c, i0, j0);
+          continue;
+        }
         stage_rows(sm.L, a.s0 + (long long)(1 + b) * n, c, i0, 1.0);
         stage_cols(sm.R, x, c, j0, 1.0);
         __syncthreads();
@@ -342,7 +468,29 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
       // phase B: w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T on the
       // owned tiles, then their projections on basis_0..j and |w|^2
-      for (int t = bid; t < ntiles; t += G) {
+      for (int t = bid; t < ntiles && df; t += G) {
+        const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
+        float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+        for (int term = 0; term < 2 + 2 * K; ++term) {
+          if (term == 0) {
+            stage_rows_p(sm.L, s0p, n, c, i0);
+            stage_cols_p(sm.R, xp, n, c, j0);
+          } else if (term == 1) {
+            stage_rows_p(sm.L, xp, n, c, i0);
+            stage_rows_p(sm.R, s1p, n, c, j0);
+          } else {
+            const int q = term - 2;            // Y_q with q < K: B_{q,1}; else A_{q-K,1}
+            const long long rop = q < K ? (long long)(1 + K + q) : (long long)(1 + q - K);
+            stage_rows_p(sm.L, a.Yp + 2 * (long long)q * n, n, c, i0);
+            stage_rows_p(sm.R, s1p + 2 * rop * n, n, c, j0);
+          }
+          __syncthreads();
+          tile_fma_p(sm, c, a0h, a0l, a1h, a1l);
+          __syncthreads();
+        }
+        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0);
+      }
+      for (int t = bid; t < ntiles && !df; t += G) {
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
         double a0 = 0.0, a1 = 0.0;
         for (int term = 0; term < 2 + 2 * K; ++term) {
@@ -440,7 +588,7 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
         if (one_pass)
           for (int i = 0; i <= j; ++i)
             s = fma(-__ldcg(a.coef + i), __ldcg(a.basis + (long long)i * n + e), s);
-        __stcg(nb + e, s * inv);
+        store_both(nb, df ? a.bp + 2 * (long long)(j + 1) * n : nullptr, n, e, s * inv);
       }
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
     }
@@ -477,7 +625,7 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
       if (e < 0) continue;
       const double t = __ldcg(a.V + e) * inv;
       __stcg(a.V + e, t);
-      __stcg(a.basis + e, t);
+      store_both(a.basis, bp0, n, e, t);
     }
     if (!lz_barrier(sm, a.bar, target, a.err)) return;
   }

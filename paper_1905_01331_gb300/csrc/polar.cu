@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "pair_arith.cuh"
 
 namespace ttn {
 
@@ -198,48 +199,6 @@ struct ComposeDFSmem {
   int ok;
 };
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (ah + al) + (bh + bl), renormalised
-__device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl, float& rh,
-                                         float& rl) {
-  float s, e;
-  two_sum_f(ah, bh, s, e);
-  e += al + bl;
-  rh = s + e;
-  rl = e - (rh - s);
-}
-
-// (ah + al) (ch + cl), renormalised
-__device__ __forceinline__ void pair_mul(float ah, float al, float ch, float cl, float& rh,
-                                         float& rl) {
-  const float p = ah * ch;
-  float pe = fmaf(ah, ch, -p);
-  pe = fmaf(ah, cl, fmaf(al, ch, pe));
-  rh = p + pe;
-  rl = pe - (rh - p);
-}
-
-__device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl, float& sh,
-                                         float& sl) {
-  const float p = ah * bh;
-  const float pe = fmaf(ah, bh, -p);
-  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
-  float s, e;
-  two_sum_f(sh, p, s, e);
-  sl += e + c;
-  sh = s;
-}
-
-__device__ __forceinline__ void split_d(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
-
 // Element (i, k) of dx I + sx S(M), S(M) = (M + M^T)/2 when sym, else M; M a
 // pair matrix (hi at M, lo at M + PP).  (dxh, dxl), (sxh, sxl): pairs.
 __device__ __forceinline__ void stage_elem(const float* M, long long PP, int P, int i, int k,
@@ -295,8 +254,8 @@ __device__ void tile_product_df(ComposeDFSmem& sm, const float* X, float dxh, fl
     pair_mac(xh, xl, sm.Yh[j + 1][k], sm.Yl[j + 1][k], a1h, a1l);
     if (++n == 8) {
       n = 0;
-      pair_add(a0h, a0l, 0.f, 0.f, a0h, a0l);
-      pair_add(a1h, a1l, 0.f, 0.f, a1h, a1l);
+      pair_renorm(a0h, a0l);
+      pair_renorm(a1h, a1l);
     }
   }
   sm.rh[warp][i * kCT + j] = a0h;

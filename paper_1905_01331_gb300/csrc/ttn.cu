@@ -106,6 +106,7 @@ struct Lane {
   double *lz_basis = nullptr, *lz_w = nullptr, *lz_c1 = nullptr, *lz_c2 = nullptr,
          *lz_alpha = nullptr, *lz_beta = nullptr, *lz_y = nullptr, *lz_tmp = nullptr,
          *top_stack0 = nullptr, *top_stack1 = nullptr, *lz_part = nullptr;
+  double *lz_opsp = nullptr, *lz_bp = nullptr, *lz_Yp = nullptr;
   int* iflags = nullptr;
 };
 
@@ -135,6 +136,8 @@ struct ttn_ctx {
          *lz_beta = nullptr, *lz_y = nullptr, *lz_tmp = nullptr, *top_stack0 = nullptr,
          *top_stack1 = nullptr;
   double* lz_part = nullptr;   // persistent Lanczos: per-CTA partial sums, then 2 (m + 2) coefficients
+  // double-float Lanczos: pairs of the top operators (both sites), basis, Y
+  double *lz_opsp = nullptr, *lz_bp = nullptr, *lz_Yp = nullptr;
   int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan [4]=wait expired
                                // [5]=grid-barrier counter of the polar composition
   int lz_m = 48;
@@ -156,7 +159,7 @@ namespace {
 #define TTN_LANE_FIELDS(X_) X_(stream) X_(Y) X_(Gam) X_(X) X_(X2) X_(Yt) X_(M1) X_(pA) X_(pF) \
   X_(pP) X_(pT) X_(pS) X_(partial) X_(red) X_(scal) X_(lz_basis) X_(lz_w) X_(lz_c1) X_(lz_c2) \
   X_(lz_alpha) X_(lz_beta) X_(lz_y) X_(lz_tmp) X_(top_stack0) X_(top_stack1) X_(lz_part) \
-  X_(iflags)
+  X_(lz_opsp) X_(lz_bp) X_(lz_Yp) X_(iflags)
 
 void load_lane(ttn_ctx* h, const Lane& l) {
 #define TTN_LOAD(f) h->f = l.f;
@@ -467,6 +470,11 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
       a.tol = h->opt.lanczos_tol;
       a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
       a.err = h->iflags + 4;
+      a.df = h->opt.prec != 0 && h->opt.double_float;
+      a.s0p = reinterpret_cast<float*>(h->lz_opsp);
+      a.s1p = a.s0p + 2 * (ll)(1 + 2 * I.K) * n;
+      a.bp = reinterpret_cast<float*>(h->lz_bp);
+      a.Yp = reinterpret_cast<float*>(h->lz_Yp);
       const int grid = lanczos_grid(c, h->profiling ? 1 : (int)h->lanes.size());
       const int nl = grid > 0 ? lanczos_launch(a, grid, h->stream) : -1;
       if (nl < 0) h->compose_refused = true;
@@ -709,7 +717,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // that takes the isometry defect from ~1e-11 to ~1e-14.  Operands in FP32
   // pairs: X in the one-leg scratch Y, F in Yt (both free during the polar
   // step).
-  const bool df_ok = prec != 0 && h->opt.polar_df && NJ == 1 && P >= 32 && sched.size() > 1;
+  const bool df_ok = prec != 0 && h->opt.double_float && NJ == 1 && P >= 32 && sched.size() > 1;
   float* Xh = reinterpret_cast<float*>(h->Y);
   float* Xl = Xh + PN;
   float* Fh = reinterpret_cast<float*>(h->Yt);
@@ -955,6 +963,11 @@ void layout(ttn_ctx* h, Arena& ar) {
     h->top_stack0 = ar.take((1 + 2 * K_max) * c2_max);
     h->top_stack1 = ar.take((1 + 2 * K_max) * c2_max);
     h->lz_part = ar.take((size_t)(kLMaxGrid + 2) * (h->lz_m + 2));
+    if (h->opt.prec != 0) {
+      h->lz_opsp = ar.take(2 * (1 + 2 * K_max) * c2_max);
+      h->lz_bp = ar.take((h->lz_m + 1) * c2_max);
+      h->lz_Yp = ar.take(2 * K_max * c2_max);
+    }
     h->iflags = ar.take_int(8);
     h->partial = ar.take(h->partial_cap);
     save_lane(h, h->lanes[k]);
@@ -1055,7 +1068,7 @@ void ttn_default_options(ttn_options* o) {
   o->persistent = 3;
   o->streams = 8;
   o->polar_blocks = 0;
-  o->polar_df = 1;
+  o->double_float = 1;
 }
 
 // Instances go to min(streams, instances) lanes, longest first onto the least

@@ -219,7 +219,7 @@ def test_double_float_polar_factor():
     ws, V = ti.initial_tensors(256, 2, 128, 7)
     E = {}
     for df in (True, False):
-        s = _sweeper(model, 128, prec="tf32x3", polar_df=df)
+        s = _sweeper(model, 128, prec="tf32x3", double_float=df)
         s.set_isometries(0, ws, V)
         E[df] = s.sweep(3)[:, 0]
         if df:
