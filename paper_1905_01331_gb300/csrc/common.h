@@ -201,6 +201,8 @@ int lanczos_launch(const LanczosArgs& a, int grid, cudaStream_t s);
 int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s);
 // Split count of df_gram (its partial buffer holds splits * P * P doubles).
 int df_gram_splits(int P, int n2);
+// Multiply-adds x 2 of the tiles df_gram computes (upper triangle only).
+double df_gram_flops(int P, long long n2);
 // C (P x P, FP64) = X X^T for X (P x n2, row-major) given as (Xh, Xl).
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
             cudaStream_t s);

@@ -22,7 +22,6 @@ namespace ttn {
 
 namespace {
 
-constexpr int kDThreads = 256;
 constexpr int kDBK = 16;
 
 // x -> (hi, lo) with hi = fl32(x), lo = fl32(x - hi)
@@ -32,18 +31,47 @@ __global__ void split_f64_kernel(const double* x, float* hi, float* lo, long lon
     split_d(x[i], hi[i], lo[i]);
 }
 
+// TM consecutive floats of shared memory into registers (vector loads; the
+// row pitch of every staged tile is a multiple of four floats).
+template <int TM>
+__device__ __forceinline__ void lds_frag(const float* p, float (&r)[TM]) {
+  if constexpr (TM % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < TM; i += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + i);
+      r[i] = v.x; r[i + 1] = v.y; r[i + 2] = v.z; r[i + 3] = v.w;
+    }
+  } else if constexpr (TM % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < TM; i += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p + i);
+      r[i] = v.x; r[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) r[i] = p[i];
+  }
+}
+
 // C (FP64) = A B for A: M x K rows (K contiguous), B either K-major (element
 // (k, n) at B[n * ldb + k], the Gram case B = A^T) or N-major (B[k * ldb + n]).
-// Output tile BM x BN per CTA, TM x TN per thread; blockIdx.z is the K split,
-// writing to part[z][M][N] when splits > 1.  sym: only tiles on or above the
-// diagonal, counted row by row in blockIdx.x.
-template <int BM, int BN, bool kBKmajor>
-__global__ void __launch_bounds__(kDThreads) gemm_df_kernel(
+// Output tile BM x BN per CTA of (BM / TM) x (BN / TN) threads, TM x TN per
+// thread; blockIdx.z is the K split, writing to part[z][M][N] when splits > 1.
+// sym: only tiles on or above the diagonal, counted row by row in blockIdx.x.
+// Two shared-memory stages: the next K tile is loaded into registers while the
+// current one is multiplied, one barrier per K tile.  MB: CTAs per SM the
+// register allocation must allow.
+template <int BM, int BN, int TM, int TN, bool kBKmajor, int MB>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     const float* __restrict__ Ah, const float* __restrict__ Al, long long lda,
     const float* __restrict__ Bh, const float* __restrict__ Bl, long long ldb, int M, int N, int K,
     double* C, long long ldc, double* part, int splits, int sym) {
-  constexpr int TM = BM / 16, TN = BN / 16;
-  __shared__ float sAh[kDBK][BM + 4], sAl[kDBK][BM + 4], sBh[kDBK][BN + 4], sBl[kDBK][BN + 4];
+  constexpr int TX = BN / TN, NT = (BM / TM) * TX;
+  constexpr int LA = BM * kDBK / NT, LB = BN * kDBK / NT;
+  static_assert(BM * kDBK % NT == 0 && BN * kDBK % NT == 0, "staging split");
+  static_assert((BM + 4) % 4 == 0 && (BN + 4) % 4 == 0, "row pitch");
+  __shared__ __align__(16) float sAh[2][kDBK][BM + 4], sAl[2][kDBK][BM + 4];
+  __shared__ __align__(16) float sBh[2][kDBK][BN + 4], sBl[2][kDBK][BN + 4];
   const int tiles_n = (N + BN - 1) / BN;
   int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
   if (sym) {
@@ -53,10 +81,50 @@ __global__ void __launch_bounds__(kDThreads) gemm_df_kernel(
     tn = tm + u;
   }
   const int m0 = tm * BM, n0 = tn * BN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int nkt = (K + kDBK - 1) / kDBK;
   const int kt_lo = (int)((long long)nkt * blockIdx.z / splits);
   const int kt_hi = (int)((long long)nkt * (blockIdx.z + 1) / splits);
+
+  float rAh[LA], rAl[LA], rBh[LB], rBl[LB];
+  auto load = [&](int kt) {
+    const int kb = kt * kDBK;
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int e = threadIdx.x + i * NT;
+      const int m = m0 + e / kDBK, k = kb + e % kDBK;
+      const bool ok = m < M && k < K;
+      rAh[i] = ok ? Ah[m * lda + k] : 0.f;
+      rAl[i] = ok ? Al[m * lda + k] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int e = threadIdx.x + i * NT;
+      int ni, ki;
+      if (kBKmajor) { ni = e / kDBK; ki = e % kDBK; } else { ki = e / BN; ni = e % BN; }
+      const int nn = n0 + ni, k = kb + ki;
+      const bool ok = nn < N && k < K;
+      const long long off = kBKmajor ? (long long)nn * ldb + k : (long long)k * ldb + nn;
+      rBh[i] = ok ? Bh[off] : 0.f;
+      rBl[i] = ok ? Bl[off] : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int e = threadIdx.x + i * NT;
+      sAh[buf][e % kDBK][e / kDBK] = rAh[i];
+      sAl[buf][e % kDBK][e / kDBK] = rAl[i];
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int e = threadIdx.x + i * NT;
+      int ni, ki;
+      if (kBKmajor) { ni = e / kDBK; ki = e % kDBK; } else { ki = e / BN; ni = e % BN; }
+      sBh[buf][ki][ni] = rBh[i];
+      sBl[buf][ki][ni] = rBl[i];
+    }
+  };
 
   float sh[TM][TN], sl[TM][TN];
 #pragma unroll
@@ -64,32 +132,22 @@ __global__ void __launch_bounds__(kDThreads) gemm_df_kernel(
 #pragma unroll
     for (int j = 0; j < TN; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
 
+  if (kt_lo < kt_hi) {
+    load(kt_lo);
+    store(0);
+  }
+  __syncthreads();
   for (int kt = kt_lo; kt < kt_hi; ++kt) {
-    const int kb = kt * kDBK;
-    for (int e = threadIdx.x; e < BM * kDBK; e += kDThreads) {
-      const int mi = e / kDBK, ki = e % kDBK;
-      const int m = m0 + mi, k = kb + ki;
-      const bool ok = m < M && k < K;
-      sAh[ki][mi] = ok ? Ah[m * lda + k] : 0.f;
-      sAl[ki][mi] = ok ? Al[m * lda + k] : 0.f;
-    }
-    for (int e = threadIdx.x; e < BN * kDBK; e += kDThreads) {
-      int ni, ki;
-      if (kBKmajor) { ni = e / kDBK; ki = e % kDBK; } else { ki = e / BN; ni = e % BN; }
-      const int nn = n0 + ni, k = kb + ki;
-      const bool ok = nn < N && k < K;
-      const long long off = kBKmajor ? (long long)nn * ldb + k : (long long)k * ldb + nn;
-      sBh[ki][ni] = ok ? Bh[off] : 0.f;
-      sBl[ki][ni] = ok ? Bl[off] : 0.f;
-    }
-    __syncthreads();
+    const int buf = (kt - kt_lo) & 1;
+    const bool more = kt + 1 < kt_hi;
+    if (more) load(kt + 1);
 #pragma unroll 4
     for (int kk = 0; kk < kDBK; ++kk) {
       float ah[TM], al[TM], bh[TN], bl[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) { ah[i] = sAh[kk][ty * TM + i]; al[i] = sAl[kk][ty * TM + i]; }
-#pragma unroll
-      for (int j = 0; j < TN; ++j) { bh[j] = sBh[kk][tx * TN + j]; bl[j] = sBl[kk][tx * TN + j]; }
+      lds_frag<TM>(&sAh[buf][kk][ty * TM], ah);
+      lds_frag<TM>(&sAl[buf][kk][ty * TM], al);
+      lds_frag<TN>(&sBh[buf][kk][tx * TN], bh);
+      lds_frag<TN>(&sBl[buf][kk][tx * TN], bl);
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -99,6 +157,7 @@ __global__ void __launch_bounds__(kDThreads) gemm_df_kernel(
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) pair_renorm(sh[i][j], sl[i][j]);
+    if (more) store(buf ^ 1);
     __syncthreads();
   }
 
@@ -135,6 +194,41 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
 
 int grid_n(long long n) { return (int)std::min<long long>((n + 255) / 256, 2048); }
 
+// Gram tiles of GB x GB (GT x GT per thread), the K range cut so that about
+// `target` CTAs run.
+int gram_splits(int P, int n2, int GB, int target) {
+  const int nt = (P + GB - 1) / GB, tiles = nt * (nt + 1) / 2;
+  const int kt = (n2 + kDBK - 1) / kDBK;
+  const int want = (target + tiles - 1) / tiles;
+  return std::max(1, std::min(std::min(want, kt / 2), 128));
+}
+
+template <int GB, int GT, int MB>
+int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
+                int splits, cudaStream_t s) {
+  const int nt = (P + GB - 1) / GB;
+  dim3 grid(nt * (nt + 1) / 2, 1, splits);
+  gemm_df_kernel<GB, GB, GT, GT, true, MB><<<grid, (GB / GT) * (GB / GT), 0, s>>>(
+      Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1);
+  int launches = 1;
+  if (splits > 1) {
+    df_reduce_kernel<<<grid_n((long long)P * P), 256, 0, s>>>(part, splits, P, P, GB, 1, C, P);
+    ++launches;
+  }
+  return launches;
+}
+
+template <int BM, int BN, int TM, int TN, int MB>
+int apply_launch(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
+                 long long n2, double* C, cudaStream_t s) {
+  const int tn = (int)((n2 + BN - 1) / BN), tm = (P + BM - 1) / BM;
+  gemm_df_kernel<BM, BN, TM, TN, false, MB><<<tm * tn, (BM / TM) * (BN / TN), 0, s>>>(
+      Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0);
+  return 1;
+}
+
+constexpr int kGramB = 32, kGramT = 2, kGramTarget = 296;
+
 }  // namespace
 
 int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s) {
@@ -142,35 +236,21 @@ int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s)
   return 1;
 }
 
-int df_gram_splits(int P, int n2) {
-  const int nt = (P + 31) / 32, tiles = nt * (nt + 1) / 2;
-  const int kt = (n2 + kDBK - 1) / kDBK;
-  const int want = (296 + tiles - 1) / tiles;
-  return std::max(1, std::min(std::min(want, kt / 2), 64));
+int df_gram_splits(int P, int n2) { return gram_splits(P, n2, kGramB, kGramTarget); }
+
+double df_gram_flops(int P, long long n2) {
+  const int nt = (P + kGramB - 1) / kGramB;
+  return 2.0 * nt * (nt + 1) / 2 * kGramB * kGramB * (double)n2;
 }
 
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
             cudaStream_t s) {
-  const int splits = df_gram_splits(P, (int)n2);
-  const int nt = (P + 31) / 32;
-  dim3 grid(nt * (nt + 1) / 2, 1, splits);
-  gemm_df_kernel<32, 32, true><<<grid, kDThreads, 0, s>>>(Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2,
-                                                         C, P, part, splits, 1);
-  int launches = 1;
-  if (splits > 1) {
-    df_reduce_kernel<<<grid_n((long long)P * P), 256, 0, s>>>(part, splits, P, P, 32, 1, C, P);
-    ++launches;
-  }
-  return launches;
+  return gram_launch<kGramB, kGramT, 2>(Xh, Xl, P, n2, C, part, df_gram_splits(P, (int)n2), s);
 }
 
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
              long long n2, double* C, cudaStream_t s) {
-  const int tn = (int)((n2 + 63) / 64), tm = (P + 63) / 64;
-  dim3 grid(tm * tn, 1, 1);
-  gemm_df_kernel<64, 64, false><<<grid, kDThreads, 0, s>>>(Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P,
-                                                          C, n2, nullptr, 1, 0);
-  return 1;
+  return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s);
 }
 
 }  // namespace ttn

@@ -265,9 +265,11 @@ __device__ __forceinline__ void stage_operand_t(const Operand& o, int k0_log2, l
     const T* tb = static_cast<const T*>(o.p) + base +
                   static_cast<long long>(kb >> k0_log2) * o.s_k1 +
                   static_cast<long long>(kb & (K0 - 1)) * o.s_k0;
-    // task: 4 consecutive rows x one chunk of CH consecutive K values
+    // task: 4 consecutive rows x one chunk of CH consecutive K values; the
+    // eight chunks of a row go to consecutive threads, so that a warp's
+    // swizzled 16-byte stores fill whole 128-byte rows (no bank conflicts)
     for (int task = threadIdx.x; task < (ROWS / 4) * NCH; task += kThreadsTC) {
-      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int rq = task / NCH, c = task % NCH;
       const int r = rq * 4;
       T v[CH][4];
       if (r < nrows_valid) {
@@ -353,7 +355,7 @@ __device__ __forceinline__ int load_f32(const Operand& o, int k0_log2, long long
 #pragma unroll
     for (int g = 0; g < TASKS; ++g) {
       const int task = threadIdx.x + g * kThreadsTC;
-      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int rq = task / NCH, c = task % NCH;
       const int r = rq * 4;
       if (task < (ROWS / 4) * NCH && r < nrows_valid) {
 #pragma unroll
@@ -394,7 +396,7 @@ __device__ __forceinline__ void store_f32(int path, const float* v, uint8_t* hi_
     for (int g = 0; g < TASKS; ++g) {
       const int task = threadIdx.x + g * kThreadsTC;
       if (task >= (ROWS / 4) * NCH) continue;
-      const int rq = task % (ROWS / 4), c = task / (ROWS / 4);
+      const int rq = task / NCH, c = task % NCH;
       const int r = rq * 4;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -405,6 +407,37 @@ __device__ __forceinline__ void store_f32(int path, const float* v, uint8_t* hi_
         if constexpr (kSplit) st_chunk<false>(lo_tile, r + i, c * CH, l);
       }
     }
+  }
+}
+
+// FP32 -> FP64 from the IEEE-754 fields (sign, exponent rebiased by
+// 1023 - 127 = 896, mantissa shifted up by 29 bits) with integer operations:
+// on this GPU the FP64 pipe (two operations per SM per clock) would bound
+// the epilogue of a tile.  Zeros keep their sign; subnormal, infinite and NaN
+// inputs take the converting instruction.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double(static_cast<int>(b & 0x80000000u), 0);
+    return static_cast<double>(x);
+  }
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
+}
+
+// C = alpha x + beta C for one FP32 accumulator x.  With beta = 0 the scaling
+// is an FP32 multiply (exact for alpha = +-1 or a power of two; otherwise one
+// FP32 rounding, below that of the FP32 accumulation itself); only beta != 0
+// with an FP64 C needs FP64 arithmetic.
+__device__ __forceinline__ void store_out(const GemmDesc& d, long long idx, float x, float af,
+                                          float bf) {
+  if (d.c_f32) {
+    float* c = static_cast<float*>(d.C) + idx;
+    *c = d.beta == 0.0 ? af * x : fmaf(af, x, bf * *c);
+  } else {
+    double* c = static_cast<double*>(d.C) + idx;
+    *c = d.beta == 0.0 ? f32_to_f64(af * x) : d.alpha * f32_to_f64(x) + d.beta * *c;
   }
 }
 
@@ -567,6 +600,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
     const int c_begin = (warp >> 2) * kHalf;
     const bool active = (BN >= 32) || (warp < 4);
     const long long MN = static_cast<long long>(d.M) * d.N;
+    const float af = static_cast<float>(d.alpha), bf = static_cast<float>(d.beta);
     for (int c0 = c_begin; active && c0 < c_begin + kHalf; c0 += 16) {
       uint32_t r[16];
       const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0;
@@ -588,25 +622,17 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
-            if (n < d.N) {
-              const double v = static_cast<double>(__uint_as_float(r[j]));
-              if (d.c_f32) {
-                float* c = static_cast<float*>(d.C) + cb + n * d.sc_n;
-                *c = d.beta == 0.0 ? static_cast<float>(d.alpha * v)
-                                   : static_cast<float>(d.alpha * v + d.beta * static_cast<double>(*c));
-              } else {
-                double* c = static_cast<double*>(d.C) + cb + n * d.sc_n;
-                *c = d.beta == 0.0 ? d.alpha * v : d.alpha * v + d.beta * *c;
-              }
-            }
+            if (n < d.N) store_out(d, cb + n * d.sc_n, __uint_as_float(r[j]), af, bf);
           }
         } else {
-          double* P = d.partial + (static_cast<long long>(split_id) * d.B0 * d.B1 + b) * MN +
-                      static_cast<long long>(m) * d.N;
+          // FP32 partials (the reduction adds them in FP32 pairs)
+          float* P = reinterpret_cast<float*>(d.partial) +
+                     (static_cast<long long>(split_id) * d.B0 * d.B1 + b) * MN +
+                     static_cast<long long>(m) * d.N;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
-            if (n < d.N) P[n] = static_cast<double>(__uint_as_float(r[j]));
+            if (n < d.N) P[n] = __uint_as_float(r[j]);
           }
         }
       }
@@ -618,26 +644,29 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
 }
 
+// C = alpha sum_s part[s] + beta C over the FP32 partials of the K splits,
+// summed in split order as an FP32 pair (error-free two-sum, low parts
+// accumulated), then rounded to FP32.
 __global__ void splitk_reduce_tc(const GemmDesc d) {
   if (d.skip && *d.skip) return;
   const long long MN = static_cast<long long>(d.M) * d.N;
   const long long total = MN * d.B0 * d.B1;
+  const float* part = reinterpret_cast<const float*>(d.partial);
+  const float af = static_cast<float>(d.alpha), bf = static_cast<float>(d.beta);
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long b = e / MN, r = e % MN;
     const int m = static_cast<int>(r / d.N), n = static_cast<int>(r % d.N);
-    double s = 0.0;
-    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + r];
+    float sh = 0.f, sl = 0.f;
+    for (int sp = 0; sp < d.splits; ++sp) {
+      const float x = part[(sp * d.B0 * d.B1 + b) * MN + r];
+      const float s = sh + x, bb = s - sh;
+      sl += (sh - (s - bb)) + (x - bb);
+      sh = s;
+    }
     const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
     const long long ce = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
-    if (d.c_f32) {
-      float* c = static_cast<float*>(d.C) + ce;
-      *c = d.beta == 0.0 ? static_cast<float>(d.alpha * s)
-                         : static_cast<float>(d.alpha * s + d.beta * static_cast<double>(*c));
-    } else {
-      double* c = static_cast<double*>(d.C) + ce;
-      *c = d.beta == 0.0 ? d.alpha * s : d.alpha * s + d.beta * *c;
-    }
+    store_out(d, ce, sh + sl, af, bf);
   }
 }
 

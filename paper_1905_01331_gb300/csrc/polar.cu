@@ -199,48 +199,58 @@ struct ComposeDFSmem {
   int ok;
 };
 
-// Element (i, k) of dx I + sx S(M), S(M) = (M + M^T)/2 when sym, else M; M a
-// pair matrix (hi at M, lo at M + PP).  (dxh, dxl), (sxh, sxl): pairs.
-__device__ __forceinline__ void stage_elem(const float* M, long long PP, int P, int i, int k,
-                                           bool sym, float dxh, float dxl, float sxh, float sxl,
-                                           float& vh, float& vl) {
-  float mh = __ldcg(M + (long long)i * P + k), ml = __ldcg(M + PP + (long long)i * P + k);
-  if (sym) {
-    const float th = __ldcg(M + (long long)k * P + i), tl = __ldcg(M + PP + (long long)k * P + i);
-    pair_add(mh, ml, th, tl, mh, ml);
-    mh *= 0.5f;
-    ml *= 0.5f;
-  }
+// dx I + sx M at element (i, k) for the pair (mh, ml) of M there.
+__device__ __forceinline__ void xform_elem(float& mh, float& ml, int i, int k, float dxh,
+                                           float dxl, float sxh, float sxl) {
   if (sxh != 1.f || sxl != 0.f) pair_mul(mh, ml, sxh, sxl, mh, ml);
   if (i == k && (dxh != 0.f || dxl != 0.f)) pair_add(mh, ml, dxh, dxl, mh, ml);
-  vh = mh;
-  vl = ml;
 }
 
-// Tile (i0, j0) of X' Y' in pair arithmetic (see tile_product); element (r, c)
-// = (tid / 8, tid % 8) returned in (vh, vl) for tid < 64.
+// Tile (i0, j0) of X' Y' in pair arithmetic (see tile_product, without the
+// symmetrisation); element (r, c) = (tid / 8, tid % 8) returned in (vh, vl)
+// for tid < 64.  The staging loads of up to four elements per operand are
+// issued before any of them is transformed and stored, so that one pass over
+// the rows and columns costs one load latency.
 __device__ void tile_product_df(ComposeDFSmem& sm, const float* X, float dxh, float dxl,
-                                float sxh, float sxl, bool symx, const float* Y, float dyh,
-                                float dyl, float syh, float syl, bool symy, int P, int i0, int j0,
-                                float& vh, float& vl) {
+                                float sxh, float sxl, const float* Y, float dyh, float dyl,
+                                float syh, float syl, int P, int i0, int j0, float& vh,
+                                float& vl) {
+  constexpr int kBatch = 4;
   const long long PP = (long long)P * P;
-  for (int e = threadIdx.x; e < kCT * P; e += kCThreads) {
-    {
-      const int r = e / P, k = e - (e / P) * P;
-      const int gi = i0 + r;
-      float h = 0.f, l = 0.f;
-      if (gi < P) stage_elem(X, PP, P, gi, k, symx, dxh, dxl, sxh, sxl, h, l);
-      sm.Xh[r][k] = h;
-      sm.Xl[r][k] = l;
+  const int total = kCT * P;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kCThreads) {
+    float xh[kBatch], xl[kBatch], yh[kBatch], yl[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kCThreads;
+      xh[u] = xl[u] = yh[u] = yl[u] = 0.f;
+      if (e < total) {
+        // rows of X: element (r, k); columns of Y: element (k, c)
+        const int r = e / P, k = e - r * P, gi = i0 + r;
+        if (gi < P) {
+          xh[u] = __ldcg(X + (long long)gi * P + k);
+          xl[u] = __ldcg(X + PP + (long long)gi * P + k);
+        }
+        const int k2 = e / kCT, c = e - k2 * kCT, gj = j0 + c;
+        if (gj < P) {
+          yh[u] = __ldcg(Y + (long long)k2 * P + gj);
+          yl[u] = __ldcg(Y + PP + (long long)k2 * P + gj);
+        }
+      }
     }
-    {
-      // column gj of Y = row gj of Y^T: element (k, gj)
-      const int k = e / kCT, c = e - (e / kCT) * kCT;
-      const int gj = j0 + c;
-      float h = 0.f, l = 0.f;
-      if (gj < P) stage_elem(Y, PP, P, k, gj, symy, dyh, dyl, syh, syl, h, l);
-      sm.Yh[c][k] = h;
-      sm.Yl[c][k] = l;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kCThreads;
+      if (e < total) {
+        const int r = e / P, k = e - r * P, gi = i0 + r;
+        if (gi < P) xform_elem(xh[u], xl[u], gi, k, dxh, dxl, sxh, sxl);
+        sm.Xh[r][k] = xh[u];
+        sm.Xl[r][k] = xl[u];
+        const int k2 = e / kCT, c = e - k2 * kCT, gj = j0 + c;
+        if (gj < P) xform_elem(yh[u], yl[u], k2, gj, dyh, dyl, syh, syl);
+        sm.Yh[c][k2] = yh[u];
+        sm.Yl[c][k2] = yl[u];
+      }
     }
   }
   __syncthreads();
@@ -330,11 +340,11 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
       const float* Ab = Aj + b * P2;
       float vh, vl;
       if (isF)
-        tile_product_df(sm, Ab, alh, all, mbh, mbl, false, Fbuf(j) + b * P2, 0.f, 0.f, 1.f, 0.f,
-                        false, P, ti * kCT, tj * kCT, vh, vl);
-      else
-        tile_product_df(sm, Ab, 0.f, 0.f, 1.f, 0.f, false, Ab, alh, all, mbh, mbl, false, P,
+        tile_product_df(sm, Ab, alh, all, mbh, mbl, Fbuf(j) + b * P2, 0.f, 0.f, 1.f, 0.f, P,
                         ti * kCT, tj * kCT, vh, vl);
+      else
+        tile_product_df(sm, Ab, 0.f, 0.f, 1.f, 0.f, Ab, alh, all, mbh, mbl, P, ti * kCT,
+                        tj * kCT, vh, vl);
       store_tile_df((isF ? Fn : T) + b * P2, P, ti, tj, vh, vl);
     }
     if (j == 0) {
@@ -343,8 +353,8 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
       for (long long e = blockIdx.x * (long long)kCThreads + threadIdx.x; e < a.NJ * PP;
            e += (long long)gridDim.x * kCThreads) {
         const long long b = e / PP, r = e % PP;
-        float h, l;
-        stage_elem(Aj + b * P2, PP, P, (int)(r / P), (int)(r % P), false, alh, all, mbh, mbl, h, l);
+        float h = __ldcg(Aj + b * P2 + r), l = __ldcg(Aj + b * P2 + PP + r);
+        xform_elem(h, l, (int)(r / P), (int)(r % P), alh, all, mbh, mbl);
         __stcg(Fn + b * P2 + r, h);
         __stcg(Fn + b * P2 + PP + r, l);
       }
@@ -356,8 +366,8 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
     for (int it = blockIdx.x; it < items2; it += gridDim.x) {
       const int b = it / ntt, ti = (it % ntt) / nt, tj = (it % ntt) % nt;
       float vh, vl;
-      tile_product_df(sm, Aj + b * P2, alh, all, mbh, mbl, false, T + b * P2, 0.f, 0.f, 1.f, 0.f,
-                      false, P, ti * kCT, tj * kCT, vh, vl);
+      tile_product_df(sm, Aj + b * P2, alh, all, mbh, mbl, T + b * P2, 0.f, 0.f, 1.f, 0.f, P,
+                      ti * kCT, tj * kCT, vh, vl);
       store_tile_df(An + b * P2, P, ti, tj, vh, vl);
     }
     target += gridDim.x;
@@ -387,7 +397,7 @@ int compose_grid_cap(bool df) {
       return 0;
     g.sms = sms;
     g.per_sm = std::min(occ, 2);
-    g.per_sm_df = std::min(occ_df, 2);
+    g.per_sm_df = std::min(occ_df, 4);
   }
   return g.sms * (df ? g.per_sm_df : g.per_sm);
 }

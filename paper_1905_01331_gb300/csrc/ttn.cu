@@ -731,7 +731,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       h->launches += df_split(X, Xh, Xl, PN, h->stream);
       df_begin(h);
       df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
-             2.0 * ((P + 31) / 32) * ((P + 31) / 32 + 1) / 2 * 32 * 32 * (double)N);
+             df_gram_flops(P, N));
     } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
@@ -793,7 +793,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += df_split(X, Xh, Xl, PN, h->stream);
     df_begin(h);
     df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
-           2.0 * ((P + 31) / 32) * ((P + 31) / 32 + 1) / 2 * 32 * 32 * (double)N);
+           df_gram_flops(P, N));
     h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
     h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
     df_begin(h);
