@@ -21,6 +21,7 @@
 
 #include "common.h"
 #include "pair_arith.cuh"
+#include "tridiag_df.cuh"
 
 namespace ttn {
 
@@ -30,7 +31,8 @@ constexpr int kLT = 8;                   // output tile edge of the matrix produ
 constexpr int kLThreads = 256;
 constexpr int kLWarps = kLThreads / 32;
 constexpr int kLMaxC = 256;
-constexpr int kLMaxSpin = 1 << 23;       // ~1 s of polling, then the error flag
+constexpr int kLMaxSpin = 1 << 21;       // ~1 s of polling, then the error flag
+constexpr int kLCheck = 8;               // steps between convergence checks within a cycle
 
 struct LzSmem {
   double L[kLT][kLMaxC + 1];             // left-operand rows of a tile
@@ -39,6 +41,7 @@ struct LzSmem {
   double tri[6][kLMaxM + 2];             // inverse iteration scratch (CTA 0)
   double da[kLMaxM + 2], db2[kLMaxM + 2];  // tridiagonal: diagonal, squared off-diagonal
   float fa[kLMaxM + 2], fb2[kLMaxM + 2];
+  double cf[kLMaxM + 2];                 // coefficients of the current combination
   double bcast[4];
   int ok;
 };
@@ -47,16 +50,19 @@ __device__ bool lz_barrier(LzSmem& sm, unsigned* bar, unsigned& target, int* err
   target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
+    // arrive with release semantics (this CTA's writes before it), poll with
+    // acquire semantics (the other CTAs' writes after it)
     int ok = 1;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int spins = 0;
-    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
       if (++spins > kLMaxSpin) { atomicOr(err, 4); ok = 0; break; }
-      __nanosleep(128);
+      __nanosleep(32);
     }
-    __threadfence();
     sm.ok = ok;
   }
   __syncthreads();
@@ -79,18 +85,37 @@ __device__ double cta_ordered_sum(LzSmem& sm, const double* x, int count, long l
   return v;
 }
 
+// Elements staged per thread: a tile edge of 8 rows or columns of length
+// c <= kLMaxC.  The staging functions issue all their loads before the first
+// shared-memory store, so that a staged tile costs one load latency.
+constexpr int kLStage = kLT * kLMaxC / kLThreads;
+
 // Stage rows [r0, r0+8) of the row-major c x c matrix M (times scale) into dst.
 __device__ void stage_rows(double (*dst)[kLMaxC + 1], const double* M, int c, int r0, double scale) {
-  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
-    const int r = e / c, k = e - r * c;
-    dst[r][k] = r0 + r < c ? scale * __ldcg(M + (long long)(r0 + r) * c + k) : 0.0;
+  double v[kLStage];
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, r = e / c, k = e - r * c;
+    v[u] = (e < kLT * c && r0 + r < c) ? __ldcg(M + (long long)(r0 + r) * c + k) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, r = e / c, k = e - r * c;
+    if (e < kLT * c) dst[r][k] = scale * v[u];
   }
 }
 // Stage columns [c0, c0+8) of M (times scale) as rows of dst: dst[j][k] = M[k][c0 + j].
 __device__ void stage_cols(double (*dst)[kLMaxC + 1], const double* M, int c, int c0, double scale) {
-  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
-    const int k = e / kLT, j = e - k * kLT;
-    dst[j][k] = c0 + j < c ? scale * __ldcg(M + (long long)k * c + c0 + j) : 0.0;
+  double v[kLStage];
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, k = e / kLT, j = e - k * kLT;
+    v[u] = (e < kLT * c && c0 + j < c) ? __ldcg(M + (long long)k * c + c0 + j) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, k = e / kLT, j = e - k * kLT;
+    if (e < kLT * c) dst[j][k] = scale * v[u];
   }
 }
 
@@ -106,8 +131,10 @@ __device__ __forceinline__ void tile_fma(const LzSmem& sm, int c, double& a0, do
   }
 }
 
-// Reduce the per-warp partial sums of a tile in warp order and store it.
-__device__ void tile_store(LzSmem& sm, double a0, double a1, double* C, int c, int i0, int j0) {
+// Reduce the per-warp partial sums of a tile in warp order and store it,
+// minus sigma X when sigma != 0 (the shifted operator H - sigma I).
+__device__ void tile_store(LzSmem& sm, double a0, double a1, double* C, int c, int i0, int j0,
+                           const double* X = nullptr, double sigma = 0.0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = lane >> 2, j = (lane & 3) * 2;
   sm.red[warp][i * kLT + j] = a0;
@@ -117,7 +144,11 @@ __device__ void tile_store(LzSmem& sm, double a0, double a1, double* C, int c, i
     double v = 0.0;
     for (int w = 0; w < kLWarps; ++w) v += sm.red[w][threadIdx.x];
     const int r = threadIdx.x / kLT, cc = threadIdx.x % kLT;
-    if (i0 + r < c && j0 + cc < c) __stcg(C + (long long)(i0 + r) * c + j0 + cc, v);
+    if (i0 + r < c && j0 + cc < c) {
+      const long long e = (long long)(i0 + r) * c + j0 + cc;
+      if (sigma != 0.0) v = fma(-sigma, __ldcg(X + e), v);
+      __stcg(C + e, v);
+    }
   }
   __syncthreads();
 }
@@ -137,6 +168,41 @@ __device__ int sturm_below(const T* a, const T* b2, int m, T x) {
   return cnt;
 }
 
+// The same count in FP64 without divisions (FP64 division is a long
+// instruction sequence on this GPU's two FP64 units per SM): the signs of the
+// leading principal minors d_i of T - x I, d_{i+1} = (a_i - x) d_i -
+// b2_{i-1} d_{i-1}, whose ratios are the pivots above (a zero pivot is
+// replaced by a tiny positive one, as above); the minors are rescaled by a
+// power of two (exactly) every eight steps.
+__device__ int sturm_below_f64(const double* a, const double* b2, int m, double x) {
+  int cnt = 0;
+  double dm = 1.0, d = a[0] - x;
+  if (d == 0.0) d = 1e-30;
+  if (d < 0.0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    double dn = fma(a[i] - x, d, -b2[i - 1] * dm);
+    if (dn == 0.0) dn = 1e-30 * d;
+    if ((dn < 0.0) != (d < 0.0)) ++cnt;
+    dm = d;
+    d = dn;
+    if ((i & 7) == 0) {
+      const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7FF) - 1023;
+      if (ex > -1000 && ex < 1000) {
+        const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+        d *= sc;
+        dm *= sc;
+      }
+    }
+  }
+  return cnt;
+}
+
+template <typename T>
+__device__ __forceinline__ int sturm_count(const T* a, const T* b2, int m, T x) {
+  if constexpr (sizeof(T) == 8) return sturm_below_f64(a, b2, m, x);
+  else return sturm_below<T>(a, b2, m, x);
+}
+
 // 32-way multisection of [lo, hi] for the lowest eigenvalue, by one warp,
 // until the interval is narrower than rel * max(|lo|, |hi|) or `its` rounds.
 template <typename T>
@@ -145,21 +211,21 @@ __device__ void multisect(const T* a, const T* b2, int m, T& lo, T& hi, T rel, i
   for (int it = 0; it < its; ++it) {
     const T mag = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
     if (!(hi - lo > rel * mag)) break;
-    const T pt = lo + (hi - lo) * (T)(lane + 1) / (T)33;
-    const unsigned below = __ballot_sync(0xffffffffu, sturm_below<T>(a, b2, m, pt) >= 1);
+    constexpr T r33 = (T)1 / (T)33;
+    const T pt = lo + (hi - lo) * ((T)(lane + 1) * r33);
+    const unsigned below = __ballot_sync(0xffffffffu, sturm_count<T>(a, b2, m, pt) >= 1);
     const int f = below ? __ffs(below) - 1 : 32;
-    const T nlo = f == 0 ? lo : lo + (hi - lo) * (T)f / (T)33;
-    const T nhi = f == 32 ? hi : lo + (hi - lo) * (T)(f + 1) / (T)33;
+    const T nlo = f == 0 ? lo : lo + (hi - lo) * ((T)f * r33);
+    const T nhi = f == 32 ? hi : lo + (hi - lo) * ((T)(f + 1) * r33);
     lo = nlo;
     hi = nhi;
   }
 }
 
-// Lowest eigenpair of the m x m tridiagonal (alpha, beta) by warp 0 of the
-// calling CTA: y (m entries, unit norm), theta, residual |beta_{m-1} y_{m-1}|.
-__device__ void ritz_pair(LzSmem& sm, const double* alpha, const double* beta, int m, double* y,
-                          double* theta, double* res) {
-  if (threadIdx.x >= 32) return;
+// Lowest eigenvalue of the m x m tridiagonal (alpha, beta) by warp 0 of the
+// calling CTA (threads >= 32 return at once): bracketed by FP32 multisection,
+// confirmed and refined in FP64; the tridiagonal is left in sm.da / sm.db2.
+__device__ double ritz_value(LzSmem& sm, const double* alpha, const double* beta, int m) {
   const int lane = threadIdx.x;
   double glo = alpha[0], ghi = alpha[0];
   for (int i = 0; i < m; ++i) {
@@ -180,12 +246,77 @@ __device__ void ritz_pair(LzSmem& sm, const double* alpha, const double* beta, i
   multisect<float>(sm.fa, sm.fb2, m, flo, fhi, 2e-6f, 8);
   const double tnorm = fmax(fabs(glo), fabs(ghi));
   double lo = (double)flo - 1e-5 * tnorm, hi = (double)fhi + 1e-5 * tnorm;
-  const int c_lo = sturm_below<double>(sm.da, sm.db2, m, lo);
-  const int c_hi = sturm_below<double>(sm.da, sm.db2, m, hi);
+  const int c_lo = sturm_below_f64(sm.da, sm.db2, m, lo);
+  const int c_hi = sturm_below_f64(sm.da, sm.db2, m, hi);
   if (!__all_sync(0xffffffffu, c_lo == 0 && c_hi >= 1)) { lo = glo; hi = ghi; }
   multisect<double>(sm.da, sm.db2, m, lo, hi, 4e-16, 16);
-  if (lane != 0) return;
-  const double th = 0.5 * (lo + hi);
+  return 0.5 * (lo + hi);
+}
+
+// Convergence test of the tridiagonal of the steps so far (alpha, beta: m
+// entries, shifted by -sigma) by warp 0 of the calling CTA, for the checks
+// within a cycle: the lowest eigenvalue bracketed in FP32 and refined by
+// 32-way multisection in pair arithmetic, then one round of inverse
+// iteration in pair arithmetic for the last component y_{m-1} of its
+// eigenvector; true when |beta_{m-1} y_{m-1}| <= tol |theta + sigma|.  (The
+// end of a cycle recomputes the pair in FP64; a wrong early answer costs a
+// restart, not accuracy.)  Uses sm.L as scratch.  The result is valid in
+// thread 0.
+__device__ bool ritz_check_df(LzSmem& sm, const double* alpha, const double* beta, int m,
+                              double sigma, double tol) {
+  using namespace tdf;
+  const int lane = threadIdx.x;
+  constexpr int S = kLMaxM + 2;
+  DF* A = reinterpret_cast<DF*>(&sm.L[0][0]);
+  DF* B = A + S;
+  DF* B2 = B + S;
+  double glo = alpha[0], ghi = alpha[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(beta[i]) : 0.0);
+    glo = fmin(glo, alpha[i] - r);
+    ghi = fmax(ghi, alpha[i] + r);
+  }
+  for (int i = lane; i < m; i += 32) {
+    const double b2 = i + 1 < m ? beta[i] * beta[i] : 0.0;
+    sm.fa[i] = (float)alpha[i];
+    sm.fb2[i] = (float)b2;
+    A[i] = make(alpha[i]);
+    B[i] = make(i + 1 < m ? beta[i] : 0.0);
+    B2[i] = make(b2);
+  }
+  __syncwarp();
+  float flo = (float)glo, fhi = (float)ghi;
+  multisect<float>(sm.fa, sm.fb2, m, flo, fhi, 2e-6f, 8);
+  const double tnorm = fmax(fabs(glo), fabs(ghi));
+  DF lo = make((double)flo - 1e-5 * tnorm), hi = make((double)fhi + 1e-5 * tnorm);
+  const int c_lo = sturm_below(A, B2, m, lo), c_hi = sturm_below(A, B2, m, hi);
+  if (!__all_sync(0xffffffffu, c_lo == 0 && c_hi >= 1)) { lo = make(glo); hi = make(ghi); }
+  constexpr float r33 = 1.f / 33.f;
+  for (int it = 0; it < 12; ++it) {
+    const float w = sub(hi, lo).h;
+    if (!(w > 1e-14f * fmaxf(fabsf(lo.h), fabsf(hi.h)))) break;
+    const DF pt = add(lo, {w * ((float)(lane + 1) * r33), 0.f});
+    const unsigned below = __ballot_sync(0xffffffffu, sturm_below(A, B2, m, pt) >= 1);
+    const int f = below ? __ffs(below) - 1 : 32;
+    const DF nlo = f == 0 ? lo : add(lo, {w * ((float)f * r33), 0.f});
+    const DF nhi = f == 32 ? hi : add(lo, {w * ((float)(f + 1) * r33), 0.f});
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane != 0) return false;
+  const DF th = add(lo, {0.5f * sub(hi, lo).h, 0.f});
+  DF* w = B2 + S;
+  const double ylast = last_component(A, B, m, th, w, w + S, w + 2 * S, w + 3 * S, w + 4 * S);
+  return fabs(beta[m - 1]) * ylast <= tol * fmax(fabs(to_double(th) + sigma), 1e-300);
+}
+
+// Lowest eigenpair of the m x m tridiagonal (alpha, beta) by warp 0 of the
+// calling CTA: y (m entries, unit norm), theta, residual |beta_{m-1} y_{m-1}|.
+__device__ void ritz_pair(LzSmem& sm, const double* alpha, const double* beta, int m, double* y,
+                          double* theta, double* res) {
+  if (threadIdx.x >= 32) return;
+  const double th = ritz_value(sm, alpha, beta, m);
+  if (threadIdx.x != 0) return;
   // inverse iteration on (T - th I) x = x_prev: LU with partial pivoting of
   // the tridiagonal, two rounds
   double* x = sm.tri[0];
@@ -255,12 +386,19 @@ __device__ void stage_rows_p(double (*dst)[kLMaxC + 1], const float* M, long lon
                              int r0) {
   FRow* h = frows(dst, 0);
   FRow* l = frows(dst, 1);
-  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
-    const int r = e / c, k = e - r * c;
-    const bool ok = r0 + r < c;
+  float vh[kLStage], vl[kLStage];
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, r = e / c, k = e - r * c;
+    const bool ok = e < kLT * c && r0 + r < c;
     const long long i = (long long)(r0 + r) * c + k;
-    h[r][k] = ok ? __ldcg(M + i) : 0.f;
-    l[r][k] = ok ? __ldcg(M + n + i) : 0.f;
+    vh[u] = ok ? __ldcg(M + i) : 0.f;
+    vl[u] = ok ? __ldcg(M + n + i) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, r = e / c, k = e - r * c;
+    if (e < kLT * c) { h[r][k] = vh[u]; l[r][k] = vl[u]; }
   }
 }
 // columns [c0, c0+8) of M as rows: dst[j][k] = M[k][c0 + j]
@@ -268,12 +406,19 @@ __device__ void stage_cols_p(double (*dst)[kLMaxC + 1], const float* M, long lon
                              int c0) {
   FRow* h = frows(dst, 0);
   FRow* l = frows(dst, 1);
-  for (int e = threadIdx.x; e < kLT * c; e += kLThreads) {
-    const int k = e / kLT, j = e - k * kLT;
-    const bool ok = c0 + j < c;
+  float vh[kLStage], vl[kLStage];
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, k = e / kLT, j = e - k * kLT;
+    const bool ok = e < kLT * c && c0 + j < c;
     const long long i = (long long)k * c + c0 + j;
-    h[j][k] = ok ? __ldcg(M + i) : 0.f;
-    l[j][k] = ok ? __ldcg(M + n + i) : 0.f;
+    vh[u] = ok ? __ldcg(M + i) : 0.f;
+    vl[u] = ok ? __ldcg(M + n + i) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kLStage; ++u) {
+    const int e = threadIdx.x + u * kLThreads, k = e / kLT, j = e - k * kLT;
+    if (e < kLT * c) { h[j][k] = vh[u]; l[j][k] = vl[u]; }
   }
 }
 
@@ -301,9 +446,10 @@ __device__ __forceinline__ void tile_fma_p(LzSmem& sm, int c, float& a0h, float&
 }
 
 // Reduce the per-warp pair partial sums of a tile in warp order; store it as
-// pairs (Cp) or as FP64 (Cd).
+// pairs (Cp) or as FP64 (Cd, minus sigma X when sigma != 0).
 __device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float a1l, float* Cp,
-                             double* Cd, long long n, int c, int i0, int j0) {
+                             double* Cd, long long n, int c, int i0, int j0,
+                             const double* X = nullptr, double sigma = 0.0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = lane >> 2, j = (lane & 3) * 2;
   float* rh = reinterpret_cast<float*>(&sm.red[0][0]);
@@ -320,7 +466,11 @@ __device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float 
     if (i0 + r < c && j0 + cc < c) {
       const long long e = (long long)(i0 + r) * c + j0 + cc;
       if (Cp) { __stcg(Cp + e, vh); __stcg(Cp + n + e, vl); }
-      if (Cd) __stcg(Cd + e, (double)vh + (double)vl);
+      if (Cd) {
+        double v = (double)vh + (double)vl;
+        if (sigma != 0.0) v = fma(-sigma, __ldcg(X + e), v);
+        __stcg(Cd + e, v);
+      }
     }
   }
   __syncthreads();
@@ -370,25 +520,80 @@ __device__ double own_dot(LzSmem& sm, const double* a, const double* b, int nown
   return v;
 }
 
-// part[bid][i] = <basis_i, w> over the owned entries for i <= j (one warp per
-// vector), and part[bid][nslot] = |w|^2 when nslot >= 0.
+// part[bid][i] = <basis_i, w> over the owned entries for i <= j, and
+// part[bid][nslot] = |w|^2 when nslot >= 0.  Warp w takes the vectors
+// 4w .. 4w+3, 4w+32 .. (their loads issued together); each sum runs over the
+// owned entries lane by lane, then a fixed butterfly.
 __device__ void own_projections(const LanczosArgs& a, double* part, int ldp, int j, int nslot,
                                 int nown, int bid, int G, int nt, int c, long long n) {
+  constexpr int U = 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i <= j + (nslot >= 0 ? 1 : 0); i += kLWarps) {
-    const bool norm = i > j;
-    const double* bi = norm ? a.w : a.basis + (long long)i * n;
-    double s = 0.0;
+  const int nv = j + 1 + (nslot >= 0 ? 1 : 0);
+  for (int i0 = warp * U; i0 < nv; i0 += kLWarps * U) {
+    double s[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) s[u] = 0.0;
     for (int q = lane; q < nown; q += 32) {
       const long long e = own_index(q, bid, G, nt, c);
-      if (e >= 0) s = fma(__ldcg(bi + e), __ldcg(a.w + e), s);
+      if (e < 0) continue;
+      double bv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u;
+        bv[u] = i < nv ? __ldcg((i > j ? a.w : a.basis + (long long)i * n) + e) : 0.0;
+      }
+      const double wv = __ldcg(a.w + e);
+#pragma unroll
+      for (int u = 0; u < U; ++u) s[u] = fma(bv[u], wv, s[u]);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) __stcg(part + (long long)bid * ldp + (norm ? nslot : i), s);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+      const int i = i0 + u;
+      if (lane == 0 && i < nv) __stcg(part + (long long)bid * ldp + (i > j ? nslot : i), s[u]);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a) {
+// Copy cnt coefficients to shared memory (sm.cf).
+__device__ __forceinline__ void load_coefs(LzSmem& sm, const double* cf, int cnt) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += kLThreads) sm.cf[i] = __ldcg(cf + i);
+  __syncthreads();
+}
+
+// For every owned entry e: f(e, base[e] + sgn * sum_{i < cnt} sm.cf[i] basis_i[e])
+// (base may be null: 0).  S = 1, 2 or 4 threads share an entry, each summing
+// the terms i = sub, sub + S, ... with eight loads in flight; the S partial
+// sums are added in a fixed order.
+template <typename Fn>
+__device__ void owned_combine(const LanczosArgs& a, const LzSmem& sm, int cnt, const double* base,
+                              double sgn, int nown, int bid, int G, int nt, int c, long long n,
+                              Fn f) {
+  const int S = nown >= kLThreads ? 1 : (nown > kLThreads / 4 ? 2 : 4);
+  const int per = kLThreads / S, sub = threadIdx.x % S;
+  for (int q0 = 0; q0 < nown; q0 += per) {
+    const int q = q0 + threadIdx.x / S;
+    const long long e = q < nown ? own_index(q, bid, G, nt, c) : -1;
+    double s = 0.0;
+    if (e >= 0) {
+      int i = sub;
+      for (; i + 7 * S < cnt; i += 8 * S) {
+        double b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = __ldcg(a.basis + (long long)(i + u * S) * n + e);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = fma(sm.cf[i + u * S], b[u], s);
+      }
+      for (; i < cnt; i += S) s = fma(sm.cf[i], __ldcg(a.basis + (long long)i * n + e), s);
+    }
+    if (S >= 2) s += __shfl_down_sync(0xffffffffu, s, 1);
+    if (S >= 4) s += __shfl_down_sync(0xffffffffu, s, 2);
+    if (sub == 0 && e >= 0) f(e, (base ? __ldcg(base + e) : 0.0) + sgn * s);
+  }
+}
+
+__global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs a) {
   __shared__ LzSmem sm;
   const int c = a.c, K = a.K, m = a.m;
   const long long n = (long long)c * c;
@@ -442,6 +647,12 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
   for (int cyc = 0; cyc < a.restarts && !conv; ++cyc) {
     int tdim = 0;
     double beta_prev = 0.0;
+    // Steps j >= 1 run on H - sigma I with sigma = alpha_0, the Rayleigh
+    // quotient of the start vector (the same Krylov space; the tridiagonal is
+    // shifted by -sigma, its first entry 0).  Without the shift |w|^2 ~ E^2
+    // would dwarf beta_j^2 and every step would need the second
+    // Gram-Schmidt pass.
+    double sigma = 0.0;
     for (int j = 0; j < m; ++j) {
       const double* x = a.basis + (long long)j * n;
       // phase A: Y_b = Op_b x for the 2K operators A_k0, B_k0 (stored after o_0)
@@ -488,7 +699,7 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
           tile_fma_p(sm, c, a0h, a0l, a1h, a1l);
           __syncthreads();
         }
-        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0);
+        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0, x, sigma);
       }
       for (int t = bid; t < ntiles && !df; t += G) {
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
@@ -510,7 +721,7 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
           tile_fma(sm, c, a0, a1);
           __syncthreads();
         }
-        tile_store(sm, a0, a1, a.w, c, i0, j0);
+        tile_store(sm, a0, a1, a.w, c, i0, j0, x, sigma);
       }
       own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
@@ -525,72 +736,80 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
       // (the second pass of "twice is enough" is needed only after heavy
       // cancellation), and the norm needs no further reduction
       const double w2 = __ldcg(wn2);
-      double c2 = 0.0;
-      for (int i = 0; i <= j; ++i) {
-        const double ci = __ldcg(a.coef + i);
-        c2 = fma(ci, ci, c2);
+      load_coefs(sm, a.coef, j + 1);
+      // sum of c_i^2 in a fixed order (lane-strided, then a butterfly): the
+      // same value, and the same one-pass decision, in every CTA
+      if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i <= j; i += 32) t = fma(sm.cf[i], sm.cf[i], t);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) sm.bcast[2] = t;
       }
+      __syncthreads();
+      const double c2 = sm.bcast[2];
       const bool one_pass = w2 - c2 > 0.25 * w2;
-      double alpha_j = __ldcg(a.coef + j);
+      double alpha_j = sm.cf[j];
       double beta_j;
       if (one_pass) {
         beta_j = sqrt(w2 - c2);
       } else {
-        for (int q = threadIdx.x; q < nown; q += kLThreads) {
-          const long long e = own_index(q, bid, G, nt, c);
-          if (e < 0) continue;
-          double s = __ldcg(a.w + e);
-          for (int i = 0; i <= j; ++i)
-            s = fma(-__ldcg(a.coef + i), __ldcg(a.basis + (long long)i * n + e), s);
-          __stcg(a.w + e, s);
-        }
+        // second pass: w1 = w - sum c_i b_i, then d_i = <b_i, w1> and |w1|^2 in
+        // one reduction; |w1 - sum d_i b_i|^2 = |w1|^2 - sum d_i^2 (the d_i are
+        // rounding-sized), and basis_{j+1} below subtracts sum d_i b_i
+        owned_combine(a, sm, j + 1, a.w, -1.0, nown, bid, G, nt, c, n,
+                      [&](long long e, double v) { __stcg(a.w + e, v); });
         __syncthreads();
-        own_projections(a, part, ldp, j, -1, nown, bid, G, nt, c, n);
+        own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
         if (!lz_barrier(sm, a.bar, target, a.err)) return;
-        for (int i = bid; i <= j; i += G) {
-          const double s = cta_ordered_sum(sm, part + i, G, ldp);
+        for (int i = bid; i <= j + 1; i += G) {
+          const double s = cta_ordered_sum(sm, part + (i > j ? nslot : i), G, ldp);
           if (threadIdx.x == 0) __stcg(a.coef + ldp + i, s);
         }
         if (!lz_barrier(sm, a.bar, target, a.err)) return;
-        for (int q = threadIdx.x; q < nown; q += kLThreads) {
-          const long long e = own_index(q, bid, G, nt, c);
-          if (e < 0) continue;
-          double s = __ldcg(a.w + e);
-          for (int i = 0; i <= j; ++i)
-            s = fma(-__ldcg(a.coef + ldp + i), __ldcg(a.basis + (long long)i * n + e), s);
-          __stcg(a.w + e, s);
+        load_coefs(sm, a.coef + ldp, j + 2);
+        if (threadIdx.x < 32) {
+          double t = 0.0;
+          for (int i = threadIdx.x; i <= j; i += 32) t = fma(sm.cf[i], sm.cf[i], t);
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (threadIdx.x == 0) sm.bcast[2] = t;
         }
         __syncthreads();
-        alpha_j += __ldcg(a.coef + ldp + j);
-        {
-          const double s = own_dot(sm, a.w, a.w, nown, bid, G, nt, c);
-          if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
-        }
-        if (!lz_barrier(sm, a.bar, target, a.err)) return;
-        beta_j = sqrt(fmax(cta_ordered_sum(sm, part, G, ldp), 0.0));
+        alpha_j += sm.cf[j];
+        beta_j = sqrt(fmax(sm.cf[j + 1] - sm.bcast[2], 0.0));
+      }
+      if (j == 0) {
+        sigma = alpha_j;
+        alpha_j = 0.0;
       }
       tdim = j + 1;
-      const bool breakdown = !(beta_j > 1e-12 * fmax(fabs(alpha_j) + beta_prev, 1e-300));
+      const bool breakdown = !(beta_j > 1e-12 * fmax(fabs(alpha_j + sigma) + beta_prev, 1e-300));
       if (bid == 0 && threadIdx.x == 0) {
         a.alpha[j] = alpha_j;
         a.beta[j] = breakdown ? 0.0 : beta_j;
       }
       if (breakdown) break;
       beta_prev = beta_j;
-      // basis_{j+1} = (w - sum c_i b_i) / beta_j (the projection is applied
-      // here on the one-pass path)
+      // basis_{j+1} = (w - sum c_i b_i) / beta_j, or (w1 - sum d_i b_i) / beta_j
       inv = 1.0 / beta_j;
       double* nb = a.basis + (long long)(j + 1) * n;
-      for (int q = threadIdx.x; q < nown; q += kLThreads) {
-        const long long e = own_index(q, bid, G, nt, c);
-        if (e < 0) continue;
-        double s = __ldcg(a.w + e);
-        if (one_pass)
-          for (int i = 0; i <= j; ++i)
-            s = fma(-__ldcg(a.coef + i), __ldcg(a.basis + (long long)i * n + e), s);
-        store_both(nb, df ? a.bp + 2 * (long long)(j + 1) * n : nullptr, n, e, s * inv);
+      float* nbp = df ? a.bp + 2 * (long long)(j + 1) * n : nullptr;
+      // (sm.cf holds the c_i of the one-pass path or the d_i of the second pass)
+      owned_combine(a, sm, j + 1, a.w, -1.0, nown, bid, G, nt, c, n,
+                    [&](long long e, double v) { store_both(nb, nbp, n, e, v * inv); });
+      // every kLCheck steps CTA 0 tests the tridiagonal so far (pair
+      // arithmetic); the cycle ends early once its Ritz pair passes the
+      // convergence test
+      const bool check = (j + 1) % kLCheck == 0 && j + 1 < m;
+      if (check && bid == 0) {
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          const bool ok = ritz_check_df(sm, a.alpha, a.beta, j + 1, sigma, a.tol);
+          if (threadIdx.x == 0) __stcg(a.scal + 3, ok ? 1.0 : 0.0);
+        }
+        __syncthreads();
       }
       if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      if (check && __ldcg(a.scal + 3) != 0.0) break;
     }
     // Ritz pair of the tridiagonal (CTA 0), then V = sum_i y_i basis_i
     if (!lz_barrier(sm, a.bar, target, a.err)) return;
@@ -598,21 +817,19 @@ __global__ void __launch_bounds__(kLThreads) lanczos_kernel(const LanczosArgs a)
       ritz_pair(sm, a.alpha, a.beta, tdim, a.y, a.scal + 1, a.scal + 2);
       __syncthreads();
       if (threadIdx.x == 0) {
+        // Ritz value of H: the tridiagonal's plus the shift
+        const double theta = *(volatile double*)(a.scal + 1) + sigma;
+        a.scal[1] = theta;
         a.flags[1] = tdim;
-        a.flags[0] = *(volatile double*)(a.scal + 2) <=
-                     a.tol * fmax(fabs(*(volatile double*)(a.scal + 1)), 1e-300);
+        a.flags[0] = *(volatile double*)(a.scal + 2) <= a.tol * fmax(fabs(theta), 1e-300);
         __threadfence();
       }
     }
     if (!lz_barrier(sm, a.bar, target, a.err)) return;
     conv = __ldcg(a.flags);
-    for (int q = threadIdx.x; q < nown; q += kLThreads) {
-      const long long e = own_index(q, bid, G, nt, c);
-      if (e < 0) continue;
-      double s = 0.0;
-      for (int i = 0; i < tdim; ++i) s = fma(__ldcg(a.y + i), __ldcg(a.basis + (long long)i * n + e), s);
-      __stcg(a.V + e, s);
-    }
+    load_coefs(sm, a.y, tdim);
+    owned_combine(a, sm, tdim, nullptr, 1.0, nown, bid, G, nt, c, n,
+                  [&](long long e, double v) { __stcg(a.V + e, v); });
     __syncthreads();
     {
       const double s = own_dot(sm, a.V, a.V, nown, bid, G, nt, c);

@@ -33,7 +33,7 @@ constexpr int kCT = 8;                       // output tile edge
 constexpr int kCThreads = 256;               // 8 warps, one K-slice each
 constexpr int kCWarps = kCThreads / 32;
 constexpr int kCMaxP = 256;
-constexpr int kCMaxSpin = 1 << 23;           // ~1 s of polling, then the error flag
+constexpr int kCMaxSpin = 1 << 21;           // ~1 s of polling, then the error flag
 
 struct ComposeSmem {
   double X[kCT][kCMaxP + 1];                 // rows i0.. of the left factor
@@ -102,16 +102,18 @@ __device__ double tile_product(ComposeSmem& sm, const double* X, double dx, doub
 __device__ bool grid_barrier(ComposeSmem& sm, unsigned* bar, unsigned target, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    // arrive with release semantics, poll with acquire semantics
     int ok = 1;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int spins = 0;
-    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
       if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
-      __nanosleep(128);
+      __nanosleep(32);
     }
-    __threadfence();
     sm.ok = ok;
   }
   __syncthreads();
@@ -294,16 +296,18 @@ __device__ __forceinline__ void store_tile_df(float* C, int P, int ti, int tj, f
 __device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    // arrive with release semantics, poll with acquire semantics
     int ok = 1;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int spins = 0;
-    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
       if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
-      __nanosleep(128);
+      __nanosleep(32);
     }
-    __threadfence();
     sm.ok = ok;
   }
   __syncthreads();
@@ -397,7 +401,7 @@ int compose_grid_cap(bool df) {
       return 0;
     g.sms = sms;
     g.per_sm = std::min(occ, 2);
-    g.per_sm_df = std::min(occ_df, 4);
+    g.per_sm_df = std::min(occ_df, 2);
   }
   return g.sms * (df ? g.per_sm_df : g.per_sm);
 }
