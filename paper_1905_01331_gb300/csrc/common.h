@@ -69,7 +69,7 @@ void gemm_tc_init();
 
 // out[b] = sum_i x[b*stride + i] * y[b*stride + i] for b < nb, i < n.
 // scratch: at least nb * kDotBlocks doubles.
-constexpr int kDotBlocks = 64;
+constexpr int kDotBlocks = 256;
 int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
                 double* out, double* scratch, cudaStream_t s);
 

@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "common.h"
+#include "f64_bits.cuh"
 
 namespace ttn {
 
@@ -31,11 +32,16 @@ __global__ void dot_partial_kernel(const double* x, const double* y, long long n
   const int b = blockIdx.y, blk = blockIdx.x;
   const double* xb = x + b * stride;
   const double* yb = y + b * stride;
-  double s = 0.0;
-  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    s = fma(xb[i], yb[i], s);
-  s = block_sum(s);
+  // two interleaved accumulators (FP64 latency on this GPU), added at the end
+  double s0 = 0.0, s1 = 0.0;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  long long i = blk * (long long)blockDim.x + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    s0 = fma(xb[i], yb[i], s0);
+    s1 = fma(xb[i + step], yb[i + step], s1);
+  }
+  if (i < n) s0 = fma(xb[i], yb[i], s0);
+  const double s = block_sum(s0 + s1);
   if (threadIdx.x == 0) partial[b * kDotBlocks + blk] = s;
 }
 
@@ -360,7 +366,7 @@ __global__ void top_energy_kernel(const double* dot, const double* vv, const dou
 __global__ void to_f32_kernel(const double* src, float* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    dst[i] = static_cast<float>(src[i]);
+    dst[i] = f64b::to_f32(src[i]);
 }
 
 int grid_for(long long n, int per = 256, int cap = 1184) {

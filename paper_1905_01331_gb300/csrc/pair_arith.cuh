@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "f64_bits.cuh"
+
 namespace ttn {
 
 // s + e = a + b exactly
@@ -53,10 +55,8 @@ __device__ __forceinline__ void pair_renorm(float& sh, float& sl) {
   sh = s;
 }
 
-// x -> (hi, lo): hi = fl32(x), lo = fl32(x - hi)
-__device__ __forceinline__ void split_d(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
+// x -> (hi, lo): hi = fl32(x), lo = fl32(x - hi) (integer operations on the
+// IEEE fields, f64_bits.cuh)
+__device__ __forceinline__ void split_d(double x, float& h, float& l) { f64b::split(x, h, l); }
 
 }  // namespace ttn
