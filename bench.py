@@ -34,6 +34,12 @@ WORKLOAD = {"workload": "tfim_chain_L1024_h1_chi128", "L": 1024, "h": 1.0, "chi"
             "seed": 1, "model": "transverse-field Ising chain, periodic",
             "tree": "binary TTN, one isometry per layer"}
 METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
+# DRAM bytes (read + write) per launch of a kernel family, averaged over one
+# sweep's launches of it (third sweep from the seeded start), from the ncu
+# captures summarised in profiles/gemm_df_kernel_tfim_L1024_chi128.md and
+# profiles/gemm_tc_kernel_tfim_L1024_chi128_tf32x3.md (None for a family
+# without one)
+TRAFFIC = {"df": 14.52e6}
 
 
 def parse():
@@ -293,12 +299,21 @@ def run_gpu(args):
                  "peak_source": "measured cuBLAS DGEMM 8192^3 on this pool's GB300 (1.10 TFLOP/s)"},
         # double-float products: FP32 flops executed, 15 per multiply-add
         # (1 MUL + 3 FMA + 8 ADD), against the FP32 FMA peak from unit counts
-        "df": {"bound": "alu", "kernel": "gemm_df_kernel (double-float products, FP32 pipes)",
+        "df": {"bound": "alu", "kernel": "gemm_df_kernel (double-float Gram and apply products, "
+                                         "FP32 pipes; with df_reduce_kernel)",
                "ms": prof.get("df_ms", 0.0), "achieved_units": prof.get("df_flops", 0.0) / 2 * 15,
                "launches": prof.get("df_launches", 0.0),
                "peak": sm_count * 128 * 2 * sm_ghz / 1e3,
                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock (FP32 FMA peak); "
                               "the kernel's mix (8 of 12 instructions are adds) caps it at 0.625"},
+        # the double-float polar composition (P x P products between grid barriers)
+        "dfc": {"bound": "alu", "kernel": "polar_compose_df_kernel (double-float composition, "
+                                          "persistent, grid barriers)",
+                "ms": prof.get("dfc_ms", 0.0), "achieved_units": prof.get("dfc_flops", 0.0) / 2 * 15,
+                "launches": prof.get("dfc_launches", 0.0),
+                "peak": sm_count * 128 * 2 * sm_ghz / 1e3,
+                "peak_source": "FP32 FMA peak as for df; latency-bound (two grid barriers per "
+                               "Newton-Schulz step)"},
     }
     fam = {}
     for k, f in families.items():
@@ -308,7 +323,7 @@ def run_gpu(args):
                   "launches_per_sweep": f["launches"], "ms_per_sweep": f["ms"],
                   "share_of_sweep": f["ms"] / prof["total_ms"]}
     dom = max(fam, key=lambda k: fam[k]["ms_per_sweep"])
-    roofline = dict(fam[dom], traffic=None)
+    roofline = dict(fam[dom], traffic=TRAFFIC.get(dom))
 
     out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

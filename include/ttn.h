@@ -183,9 +183,10 @@ long long ttn_launch_count(ttn_t h);
  * useful flops (2*M*N*K summed over groups and batches), launches; the same
  * three for the tensor-core engine; milliseconds and launches of all other
  * kernels (including event gaps); total milliseconds of the sweep.  With
- * n_out >= 12, out[9..11] = the same three for the double-float products
- * (otherwise they count as "other").  The sweep updates the tensors like
- * ttn_sweep.  n_out >= 9. */
+ * n_out >= 15, out[9..11] = the same three for the double-float Gram and
+ * apply products and out[12..14] for the double-float polar composition;
+ * with 12 <= n_out < 15, out[9..11] = both together; with fewer they count as
+ * "other".  The sweep updates the tensors like ttn_sweep.  n_out >= 9. */
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random

@@ -180,10 +180,11 @@ class Sweeper:
 
     def profile_sweep(self):
         """One eagerly launched sweep with every product timed by CUDA events."""
-        out = np.zeros(12)
-        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 12), "profile_sweep")
+        out = np.zeros(15)
+        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 15), "profile_sweep")
         keys = ["fp64_ms", "fp64_flops", "fp64_launches", "tc_ms", "tc_flops", "tc_launches",
-                "other_ms", "other_launches", "total_ms", "df_ms", "df_flops", "df_launches"]
+                "other_ms", "other_launches", "total_ms", "df_ms", "df_flops", "df_launches",
+                "dfc_ms", "dfc_flops", "dfc_launches"]
         return dict(zip(keys, out.tolist()))
 
     @property

@@ -45,13 +45,16 @@ __global__ void dot_partial_kernel(const double* x, const double* y, long long n
   if (threadIdx.x == 0) partial[b * kDotBlocks + blk] = s;
 }
 
+// out[b] = sum of the kDotBlocks partial sums of batch b: one warp per batch,
+// lane-strided sums, then a fixed butterfly.
 __global__ void dot_final_kernel(const double* partial, int nb, double* out, const int* skip) {
   if (skip && *skip) return;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (b >= nb) return;
   double s = 0.0;
-  for (int i = 0; i < kDotBlocks; ++i) s += partial[b * kDotBlocks + i];
-  out[b] = s;
+  for (int i = lane; i < kDotBlocks; i += 32) s += partial[b * kDotBlocks + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[b] = s;
 }
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
@@ -381,7 +384,7 @@ int grid_for(long long n, int per = 256, int cap = 1184) {
 int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
                 double* out, double* scratch, cudaStream_t s) {
   dot_partial_kernel<<<dim3(kDotBlocks, nb), 256, 0, s>>>(x, y, n, stride, scratch, nullptr);
-  dot_final_kernel<<<(nb + 127) / 128, 128, 0, s>>>(scratch, nb, out, nullptr);
+  dot_final_kernel<<<(nb + 3) / 4, 128, 0, s>>>(scratch, nb, out, nullptr);
   return 2;
 }
 

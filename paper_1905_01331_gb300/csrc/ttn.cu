@@ -685,7 +685,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
     cudaEventRecord(ev[1], h->stream);
     h->ev_pool.push_back(ev[0]);
     h->ev_pool.push_back(ev[1]);
-    h->ev_flops.push_back({df ? 2 : 0, compose_flops(P, NJ, a.nsteps)});
+    h->ev_flops.push_back({df ? 3 : 0, compose_flops(P, NJ, a.nsteps)});
   }
 }
 
@@ -1543,7 +1543,7 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   h->profiling = false;
   int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
   if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
-  double ms[3] = {0, 0, 0}, fl[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
+  double ms[4] = {0, 0, 0, 0}, fl[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0};
   for (size_t i = 0; i < h->ev_flops.size(); ++i) {
     float e = 0.f;
     cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
@@ -1561,10 +1561,18 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   cudaEventDestroy(t1);
   out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
   out[3] = ms[1]; out[4] = fl[1]; out[5] = cnt[1];
-  out[6] = tot - ms[0] - ms[1] - ms[2];
-  out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2];
+  out[6] = tot - ms[0] - ms[1] - ms[2] - ms[3];
+  out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2] - cnt[3];
   out[8] = tot;
-  if (n_out >= 12) { out[9] = ms[2]; out[10] = fl[2]; out[11] = cnt[2]; }
+  if (n_out >= 15) {
+    out[9] = ms[2]; out[10] = fl[2]; out[11] = cnt[2];
+    out[12] = ms[3]; out[13] = fl[3]; out[14] = cnt[3];
+  } else if (n_out >= 12) {
+    out[9] = ms[2] + ms[3]; out[10] = fl[2] + fl[3]; out[11] = cnt[2] + cnt[3];
+  } else {
+    out[6] += ms[2] + ms[3];
+    out[7] += cnt[2] + cnt[3];
+  }
   h->sweeps_done += 1;
   return rc;
 }
