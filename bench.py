@@ -39,7 +39,7 @@ METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
 # captures summarised in profiles/gemm_df_kernel_tfim_L1024_chi128.md and
 # profiles/gemm_tc_kernel_tfim_L1024_chi128_tf32x3.md (None for a family
 # without one)
-TRAFFIC = {"df": 14.52e6}
+TRAFFIC = {"df": 14.52e6, "tc": 15.74e6}
 
 
 def parse():
