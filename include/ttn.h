@@ -79,7 +79,8 @@ typedef struct {
                                1: v <- -H_top v / |H_top v| (minus the polar
                                factor of v's environment, the literal reading
                                of "updated similarly", Sec. III.B) */
-  double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E| (default 1e-13) */
+  double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E|; 0 (default): 1e-13 in
+                               FP64 mode, 1e-10 in the mixed modes */
   int lanczos_max;          /* Krylov dimension per restart (default 48) */
   int lanczos_restarts;     /* restarts per sweep (default 3) */
   double shift;             /* bond shift c; NaN = lambda_max of the bond term */

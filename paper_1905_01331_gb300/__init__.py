@@ -34,7 +34,7 @@ class Sweeper:
     """
 
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
-                 lanczos_tol=1e-13, lanczos_max=48, lanczos_restarts=3,
+                 lanczos_tol=0.0, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
                  persistent=True, streams=8, polar_blocks=0, double_float=True):
         import torch

@@ -437,6 +437,15 @@ void top_matvec(ttn_ctx* h, Instance& I, const double* x, double* w, const int* 
   run(h, d, 0);
 }
 
+// Residual tolerance of the top solve: the option, or by default 1e-13 in
+// FP64 mode and 1e-10 in the mixed modes, whose top operators carry the
+// tensor-core rounding of the ascended layers (1e-6 to 3e-5 relative): a
+// tighter solve of that operator would not move the state further.
+double lanczos_tolerance(const ttn_ctx* h) {
+  if (h->opt.lanczos_tol > 0.0) return h->opt.lanczos_tol;
+  return h->opt.prec == 0 ? 1e-13 : 1e-10;
+}
+
 void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
   const int T = I.T, c = I.chis[T];
   const ll n = (ll)c * c;
@@ -467,7 +476,7 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
       a.alpha = h->lz_alpha; a.beta = h->lz_beta; a.y = h->lz_y; a.scal = h->scal;
       a.flags = h->iflags + 6;
       a.c = c; a.K = I.K; a.m = m; a.restarts = h->opt.lanczos_restarts;
-      a.tol = h->opt.lanczos_tol;
+      a.tol = lanczos_tolerance(h);
       a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
       a.err = h->iflags + 4;
       a.df = h->opt.prec != 0 && h->opt.double_float;
@@ -507,7 +516,7 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
     }
     if (h->measuring) continue;
     h->launches += lz_ritz(h->lz_alpha, h->lz_beta, tdim, h->lz_m, h->lz_y, theta, res, conv,
-                           h->opt.lanczos_tol, h->stream);
+                           lanczos_tolerance(h), h->stream);
     h->launches += lz_combine(h->lz_basis, n, tdim, h->lz_y, I.V, h->red, nrm2, tdim, skip, conv,
                               h->stream);
   }
@@ -1058,7 +1067,7 @@ void ttn_default_options(ttn_options* o) {
   if (!o) return;
   o->prec = TTN_FP64;
   o->top_mode = 0;
-  o->lanczos_tol = 1e-13;
+  o->lanczos_tol = 0.0;
   o->lanczos_max = 48;
   o->lanczos_restarts = 3;
   o->shift = NAN;
