@@ -518,6 +518,18 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
     const long long abase = b0 * G.a.s_b0 + static_cast<long long>(b1) * G.a.s_b1;
     const long long bbase = b0 * G.b.s_b0 + static_cast<long long>(b1) * G.b.s_b1;
     const int first = max(0, t_lo - t_global), last = min(nt, t_hi - t_global);
+    // TF32 modes with FP32 operands: the global loads of K tile t + 1 are
+    // issued as soon as tile t is in shared memory, so that they are in
+    // flight during the barrier, the MMA issue and the wait for a free stage
+    float va[16], vb[16];
+    int pa = 0, pb = 0;
+    const bool f32ops = G.a.f32 && G.b.f32;
+    if constexpr (!kBF16) {
+      if (f32ops && first < last) {
+        pa = load_f32<kBM>(G.a, G.k0_log2, abase, m0, mvalid, first * BK, G.K, va);
+        pb = load_f32<BN>(G.b, G.k0_log2, bbase, n0, nvalid, first * BK, G.K, vb);
+      }
+    }
     for (int t = first; t < last; ++t) {
       const int stage = issued % kStages;
       // the MMAs that read this stage (tile issued - kStages) must be done;
@@ -532,10 +544,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
       uint8_t* b_lo = st + 2 * kA + kB;
       const int kb = t * BK;
       if constexpr (!kBF16) {
-        if (G.a.f32 && G.b.f32) {
-          float va[16], vb[16];
-          const int pa = load_f32<kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, va);
-          const int pb = load_f32<BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K, vb);
+        if (f32ops) {
           store_f32<kSplit, kBM>(pa, va, a_hi, a_lo);
           store_f32<kSplit, BN>(pb, vb, b_hi, b_lo);
           if (!pa)
@@ -544,6 +553,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
           if (!pb)
             stage_operand<kBF16, kSplit, BK, BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb, G.K,
                                                  b_hi, b_lo);
+          if (t + 1 < last) {
+            pa = load_f32<kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb + BK, G.K, va);
+            pb = load_f32<BN>(G.b, G.k0_log2, bbase, n0, nvalid, kb + BK, G.K, vb);
+          }
         } else {
           stage_operand<kBF16, kSplit, BK, kBM>(G.a, G.k0_log2, abase, m0, mvalid, kb, G.K, a_hi,
                                                 a_lo);
