@@ -10,9 +10,10 @@
 //     p = a_hi b_hi exactly (p + fma(a_hi, b_hi, -p)),  cross terms a_hi b_lo +
 //     a_lo b_hi rounded to FP32, a_lo b_lo dropped, error-free two-sum of the
 //     running high part, renormalisation once per K tile,
-// about 12 FP32 instructions per multiply-add: ~48 significant bits, five
-// times the FP64 rate.  A final Newton-Schulz step in the same arithmetic
-// brings the isometry defect to ~1e-14.
+// about 12 FP32 instructions per multiply-add: ~48 significant bits at about
+// four times the FP64 rate here (2.1 against 0.55 T multiply-adds/s).  A final
+// Newton-Schulz step in the same arithmetic brings the isometry defect to
+// ~1e-14.
 #include <algorithm>
 
 #include "common.h"

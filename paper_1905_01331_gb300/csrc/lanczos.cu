@@ -1,7 +1,9 @@
 // Top-tensor update (Sec. III.B: the top tensor is "updated similarly"; read
 // as the lowest eigenvector of the top Hamiltonian) as one persistent
-// cooperative launch: restarted Lanczos in FP64 with full reorthogonalisation
-// (two classical Gram-Schmidt passes), warm-started from the previous V.
+// cooperative launch: restarted Lanczos with full reorthogonalisation,
+// warm-started from the previous V.  Vectors, projections and the
+// tridiagonal are FP64; in the mixed modes the matrix-vector products run in
+// double-float pair arithmetic on pair copies of the operators and the basis.
 //
 // H_top acts on the c x c top tensor V as
 //     H V = o_0 V + V o_1^T + sum_k (A_k0 V B_k1^T + B_k0 V A_k1^T),
@@ -9,13 +11,19 @@
 // two bonds of the periodic ring at the top).  One Lanczos step is
 //     phase A   Y_k = A_k0 x, Y_{K+k} = B_k0 x               (2K products)
 //     phase B   w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T
-//     dots/reduce/subtract twice, then |w| and alpha_j, beta_j
+//               (minus sigma x after the first step: the recurrence runs on
+//               H - sigma I, sigma the Rayleigh quotient of the start vector)
+//     projections on the basis and |w|^2, one classical Gram-Schmidt pass,
+//     a second one ("twice is enough") when the first removed more than 3/4
+//     of |w|^2, then alpha_j, beta_j and the next basis vector
 // with every phase shared by all CTAs and a grid barrier between phases
-// (bounded spin, error flag).  Vector phases split the n = c^2 entries into
-// one contiguous slice per CTA; every reduction adds its per-CTA partial
-// sums in a fixed order, so the result does not depend on timing.  The
-// eigenpair of the tridiagonal matrix is found by CTA 0 (bisection by Sturm
-// counts, first in FP32 to bracket, then in FP64, and inverse iteration).
+// (bounded spin, error flag).  Each CTA owns the vector entries of the 8 x 8
+// output tiles it computes; every reduction adds its per-CTA partial sums in
+// a fixed order, so the result does not depend on timing.  Every kLCheck
+// steps CTA 0 tests the tridiagonal so far for convergence in pair
+// arithmetic (tridiag_df.cuh) and a passed test ends the cycle; at the end of
+// a cycle CTA 0 finds the eigenpair of the tridiagonal (Sturm bisection, in
+// FP32 to bracket, then in FP64, and inverse iteration).
 #include <algorithm>
 #include <mutex>
 
