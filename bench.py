@@ -246,16 +246,20 @@ def run_gpu(args):
     prof = s.profile_sweep()
 
     # e2e through the C ABI with host buffers: upload the state, one sweep,
-    # read the energy back, every step
+    # read the energy back, every step.  The state uploaded is the one the
+    # timed sweeps reached (read back once into pinned host memory), so that
+    # every e2e step does the same work as a timed sweep plus the copies.
     n_w = sum(int(np.prod(w.shape)) for w in ws)
-    flat_host = torch.from_numpy(np.concatenate([w.ravel() for w in ws])).pin_memory()
-    v_host = torch.from_numpy(np.ascontiguousarray(V)).pin_memory()
+    flat_host = torch.empty(n_w, dtype=torch.float64).pin_memory()
+    v_host = torch.empty(V.size, dtype=torch.float64).pin_memory()
     E_host = np.zeros(1)
     import ctypes
     dp = ctypes.POINTER(ctypes.c_double)
     fp = ctypes.cast(flat_host.data_ptr(), dp)
     vp = ctypes.cast(v_host.data_ptr(), dp)
     ep = E_host.ctypes.data_as(dp)
+    if s.lib.ttn_get_isometries(s.h, 0, fp, vp):
+        raise RuntimeError("reading the state back failed")
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
         s.lib.ttn_set_isometries(s.h, 0, fp, vp)
