@@ -31,6 +31,8 @@ class Sweeper:
 
     ``models``: objects with ``Lx, Ly, o (d0 x d0), A, B (K x d0 x d0)`` (for
     example ``ttn_inputs.Model``); ``chis``: bond-dimension caps (int or list).
+    The other arguments set the fields of ``ttn_options`` (include/ttn.h);
+    ``lanczos_tol=0`` selects the precision's default top-solve tolerance.
     """
 
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
