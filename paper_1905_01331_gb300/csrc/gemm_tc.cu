@@ -169,15 +169,6 @@ __device__ __forceinline__ void st_chunk(uint8_t* tile, int r, int kk, const uin
   *reinterpret_cast<uint4*>(tile + swz_off<kBF16>(r, kk)) = q;
 }
 
-__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
-  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-    const double2 t = *reinterpret_cast<const double2*>(p);
-    a = t.x; b = t.y;
-  } else {
-    a = p[0]; b = p[1];
-  }
-}
-
 // N consecutive values (N = 4 or 8) with 16-byte loads when aligned.
 template <typename T, int N>
 __device__ __forceinline__ void ldv(const T* p, T* out) {
@@ -202,15 +193,6 @@ __device__ __forceinline__ void ldv(const T* p, T* out) {
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) out[i] = p[i];
-}
-
-__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
-  if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    a = t.x; b = t.y;
-  } else {
-    a = p[0]; b = p[1];
-  }
 }
 
 // Stage rows [r0, r0 + ROWS) x K tile [kb, kb + BK) of one operand.  Fast
