@@ -105,3 +105,17 @@ def test_every_product_stays_inside_its_buffer(lib, prec):
     ps = [_problem(ti.tfim_chain(L, 1.0), chi) for L, chi in ((64, 32), (512, 128), (128, 64))]
     arr = (_abi.Problem * 3)(*[p for p, _ in ps])
     assert lib.ttn_workspace_bytes(arr, 3, ctypes.byref(opt)) > 0
+
+
+def test_default_options_match_the_header(lib):
+    """ttn_default_options fills the defaults include/ttn.h documents (host
+    only): automatic top-solve tolerance (0: 1e-13 in FP64 mode, 1e-10 in the
+    mixed modes), Krylov dimension 48 with 3 restarts, both persistent kernels,
+    8 streams, automatic polar blocks, double-float polar factor."""
+    from paper_1905_01331_gb300 import _abi
+    opt = _abi.Options()
+    lib.ttn_default_options(ctypes.byref(opt))
+    assert opt.lanczos_tol == 0.0
+    assert (opt.lanczos_max, opt.lanczos_restarts) == (48, 3)
+    assert (opt.persistent, opt.streams, opt.polar_blocks, opt.double_float) == (3, 8, 0, 1)
+    assert opt.polar_damping == 1e-7
