@@ -297,3 +297,71 @@ def test_top_polar_step_is_a_power_step_and_monotone():
     assert v1 @ H @ v1 <= v0 @ H @ v0 + 1e-12
     Es = [ttn.sweep(st, top_mode=1) for _ in range(6)]
     assert all(b <= a + 1e-11 * abs(a) for a, b in zip(Es, Es[1:]))
+
+
+# --- pins added for the leftmost density matrix, the damping sign, entropy ----
+
+@pytest.mark.parametrize("per_node", [False, True])
+@pytest.mark.parametrize("which", ["tfim", "heis"])
+def test_leftmost_density_matrix_matches_brute_force(which, per_node):
+    """rdm(which=1) is the one-site density matrix of the leftmost site of
+    each site layer, traced out of the contracted state vector.  The right
+    spine (the other child at every level) gives another site's matrix and
+    must fail the same comparison on some layer."""
+    m = ti.tfim_chain(16, 0.8) if which == "tfim" else ti.heisenberg_xxx(16)
+    st = _state(m, 3, 31, per_node)
+    for _ in range(2):
+        ttn.sweep(st)
+    T = len(st.ws)
+    right_spine_differs = False
+    for t in range(T + 1):
+        psi = ed.state_vector(st.ws, st.V, per_node=per_node, stop_layer=t)
+        N, d = st.L >> t, (st.V.shape[0] if t == T else st.ws[t].shape[-1])
+        brute = ed.site_density_matrix(psi, N, d, 0)
+        rho = ttn.rdm(st, t, which=1)
+        assert np.abs(rho - brute).max() < 1e-13
+        # planted mistake: walk down through the right child instead
+        wrong = st.V @ st.V.T
+        for u in range(T - 1, t - 1, -1):
+            w = st.ws[u][0] if per_node else st.ws[u]
+            wrong = ttn.d_right(w, ttn.left_product(wrong, w))
+        if np.abs(wrong - brute).max() > 1e-6:
+            right_spine_differs = True
+    assert right_spine_differs
+
+
+def test_damping_keeps_old_isometry_on_null_directions():
+    """Rank-deficient environment gamma = -S Q (S positive semidefinite of rank
+    2 < P, Q isometric) with w_old = Q: on the null directions of S only the
+    proximal term -mu |gamma| w_old is left, so the update must return w_old
+    there, i.e. exactly Q.  With the opposite sign of the damping term the null
+    directions flip and the result differs from Q by O(1)."""
+    rng = np.random.default_rng(5)
+    P, n = 5, 3
+    Q = np.linalg.qr(rng.standard_normal((n * n, P)))[0].T
+    U = np.linalg.qr(rng.standard_normal((P, P)))[0]
+    S = U @ np.diag([3.0, 1.5, 0.0, 0.0, 0.0]) @ U.T
+    gamma = (-S @ Q).reshape(P, n, n)
+    w = ttn.polar_update(gamma, Q.reshape(P, n, n), damping=1e-7)
+    assert np.abs(w.reshape(P, -1) - Q).max() < 1e-9
+    g = gamma.reshape(P, -1) + 1e-7 * np.linalg.norm(gamma) * Q   # wrong sign
+    Uw, _, Vt = np.linalg.svd(g, full_matrices=False)
+    assert np.abs(-(Uw @ Vt) - Q).max() > 0.5
+
+
+def test_entanglement_of_hand_computed_spectra():
+    """Sec. IV.B: lambda = -log2 p, S = -sum p log2 p.  A density matrix with
+    eigenvalues (1/2, 1/4, 1/4) in a random basis: lambda = (1, 2, 2) and
+    S = 1.5 bits; the maximally mixed state of dimension 8: S = 3; a pure
+    state: S = 0."""
+    rng = np.random.default_rng(2)
+    O = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+    lam, S = ttn.entanglement(O @ np.diag([0.25, 0.5, 0.25]) @ O.T)
+    assert np.abs(np.sort(lam) - np.array([1.0, 2.0, 2.0])).max() < 1e-12
+    assert abs(S - 1.5) < 1e-12
+    lam, S = ttn.entanglement(np.eye(8) / 8)
+    assert np.abs(lam - 3.0).max() < 1e-12 and abs(S - 3.0) < 1e-12
+    v = rng.standard_normal(6)
+    v /= np.linalg.norm(v)
+    lam, S = ttn.entanglement(np.outer(v, v))
+    assert abs(S) < 1e-12 and abs(lam[0]) < 1e-12
