@@ -20,8 +20,12 @@
  *    allocates device memory itself.  The workspace must stay allocated and
  *    unused by the caller until ttn_destroy.
  *  - Stream: `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Work is enqueued on it; calls that return host values
- *    synchronise that stream only.
+ *    stream).  The library enqueues its kernels on non-blocking streams of its
+ *    own, created by ttn_create (one per concurrent instance lane), and fences
+ *    them to `stream` with events: a call's work starts after everything
+ *    enqueued on `stream` before the call, and `stream` waits for that work,
+ *    so it behaves as if enqueued on `stream`.  Calls that return host values
+ *    synchronise the library's streams only.
  *  - Layouts are row-major C order.  An isometry of layer t is w[p][l][r]
  *    with parent p < chi_{t+1} and children l, r < chi_t (Eq. (constraint)
  *    reads sum_{l,r} w[p][l][r] w[p'][l][r] = delta_{p p'}); the top tensor is
@@ -106,6 +110,19 @@ typedef struct {
                                Lanczos top solve's matrix-vector products in
                                double-float arithmetic (FP32 pairs, ~48 bits) on
                                the FP32 pipes; 0: FP64 */
+  int tc_engine;            /* tensor-core products: 0 (default) the TMA-fed,
+                               warp-specialised kernel wherever the operand
+                               layouts allow it (FP32, K or MN index contiguous;
+                               TF32 modes), else the thread-staged kernel;
+                               1: the thread-staged kernel for every product */
+  int wait_polls;           /* polls of a grid-barrier wait in the persistent
+                               kernels before it expires and the sweep reports
+                               TTN_ETIMEOUT (0, the default: 2^21 polls, about
+                               one second) */
+  const void* tiles;        /* autotuner blob from ttn_autotune (NULL: the
+                               launchers' default tile widths and split counts);
+                               copied by ttn_create */
+  size_t tiles_bytes;
 } ttn_options;
 
 /* Fill *opt with the defaults above. */
@@ -142,8 +159,45 @@ int ttn_get_isometries(ttn_t h, int inst, double* host_w_all, double* host_v);
  * environment of w_t, replace w_t by minus its polar factor and descend the
  * density matrices through the new w_t.  host_energy (may be NULL) receives
  * n_sweeps * n_problems doubles, sweep-major: the energy found by each top
- * solve, shift restored. */
+ * solve, shift restored.
+ * The call returns after the sweeps have run: it reads the device status
+ * words of the context (and clears them once reported).  Status, most severe
+ * first: TTN_ECUDA; TTN_ETIMEOUT (a bounded wait in a kernel expired: the
+ * tensors are then unspecified, restore them with ttn_set_isometries or
+ * ttn_set_state); TTN_ENAN (a non-finite energy); TTN_ENOCONV (in the last
+ * sweep of some instance the top solve missed its residual tolerance within
+ * lanczos_max * lanczos_restarts steps -- the tensors are a valid, updated
+ * state, usual in the first sweeps from a random start -- or, in the mixed
+ * modes, a polar factor was left more than 1e-5 from an isometry by its
+ * Newton-Schulz blocks); TTN_OK. */
 int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy);
+
+/* Sweep until the energy per spin of every instance changes by less than
+ * `tol` from one sweep to the next (the convergence criterion of Sec. IV,
+ * |delta e| < 1e-10), or until max_sweeps sweeps.  The change is computed on
+ * the device after every sweep; the host reads the instances' flags after
+ * every chunk of up to 8 sweeps, so up to 7 sweeps may follow the first one
+ * that met the criterion (they can only lower the energy).  The first sweep
+ * of a call is compared with nothing and never counts.  *n_done (may be NULL)
+ * receives the sweeps run; host_energy (may be NULL) receives max_sweeps *
+ * n_problems doubles as in ttn_sweep (the first *n_done rows written).
+ * Returns TTN_OK when the criterion was met, TTN_ENOCONV when max_sweeps ran
+ * out first, or an error status of ttn_sweep. */
+int ttn_sweep_until(ttn_t h, double tol, int max_sweeps, int* n_done, double* host_energy);
+
+/* Diagnostics of one instance's current tensors, computed on the device in
+ * FP64 (Eqs. (constraint), (normalization); Sec. IV): out[0] = max over layers
+ * and nodes of max |W W^T - I| (isometry defect); out[1] = max over site
+ * layers t of |Tr R_t - N_t| / N_t (R_t: the density matrices of the N_t sites
+ * of layer t, summed; each has trace one); out[2] = max over site layers of
+ * max |R_t - R_t^T| / N_t; out[3] = |<v, v> - 1|; out[4] = the change of the
+ * energy per spin in the last sweep (NaN before two sweeps); out[5] = 1 if
+ * the last sweep's top solve met its tolerance, else 0; out[6] = the Krylov
+ * dimension of its last cycle; with n_out >= 8, out[7] = 1 if a polar factor
+ * of the last sweep (mixed modes) was left more than 1e-5 from an isometry by
+ * its Newton-Schulz blocks, else 0.  n_out >= 7.  Overwrites the context's
+ * density matrices (a sweep recomputes them). */
+int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out);
 
 /* Operators of site layer `site_layer` ascended through the current
  * isometries (Fig. 3 pushed upward: o' = W[o(x)I + I(x)o + sum_k A_k(x)B_k]W^T,
@@ -191,12 +245,24 @@ long long ttn_launch_count(ttn_t h);
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
- * operands over eleven cases (K-major / M-major, two-level K and batch, ragged
- * edges, split K, alpha/beta, FP32 sources).  d_ws: caller device memory of at least
- * ttn_selftest_bytes(); prec: 1..4 (ttn_precision); out_rel[i] receives
- * max|C_tc - C_fp64| / max|C_fp64| of case i (n_out >= 11). */
+ * operands over sixteen cases: FP64 sources (K-major / M-major, two-level K
+ * and batch, ragged edges, split K, alpha/beta), then FP32 sources (cases
+ * 10-16, the layouts of the TMA-fed kernel in the TF32 modes: ragged tiles,
+ * two-level K with a broadcast batch, batched transposed products, mixed K- /
+ * MN-major groups, a split-K close with FP64 output).  d_ws: caller device
+ * memory of at least ttn_selftest_bytes(); prec: 1..4 (ttn_precision);
+ * out_rel[i] receives max|C_tc - C_fp64| / max|C_fp64| of case i for
+ * i < min(n_out, 16) (n_out >= 11). */
 size_t ttn_selftest_bytes(void);
 int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out, void* stream);
+
+/* Diagnostic: the double-float (FP32 pair) Gram and apply products that the
+ * mixed modes use for the polar factor, against the FP64 engine on seeded
+ * operands: Gram X X^T for (P, n2) = (128, 16384) and (96, 1000), apply F X
+ * for (128, 16384) and (40, 1000).  d_ws: caller device memory of at least
+ * ttn_selftest_bytes(); out_rel[i] = max |C_df - C_fp64| / max |C_fp64|
+ * (n_out >= 4). */
+int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_out, void* stream);
 
 /* Allocation-free close product, for callers that cannot allocate device
  * memory (plug-ins inside an application that owns the CUDA allocator, or code
@@ -214,6 +280,22 @@ int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n
  * as void*); the call allocates nothing. */
 int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, int Q, long long n2,
                       double* d_C, void* stream);
+
+/* Autotuner of the grouped products (tile shapes and split counts): with
+ * reps > 0, one sweep of every instance runs eagerly on one stream and, at
+ * the first occurrence of each product shape (its sizes, groups and operand
+ * layouts; not its addresses), every candidate configuration is timed with
+ * CUDA events over `reps` launches after one warm-up launch: for tensor-core
+ * products the engine (TMA-fed where eligible, thread-staged), its tile width
+ * BN and the split count of K; for FP64 products the tile (16, 32, 64) and
+ * the split count; the split counts are limited to the context's split-K
+ * buffer.  The fastest becomes the product's configuration (the next
+ * ttn_sweep captures its graph again).  The sweep updates the tensors like
+ * ttn_sweep.  With blob_bytes != NULL the table is exported: blob == NULL
+ * returns the size in *blob_bytes, else the table is written to blob (at
+ * least *blob_bytes bytes) for ttn_options.tiles of a later ttn_create.
+ * reps == 0 only exports. */
+int ttn_autotune(ttn_t h, int reps, void* blob, size_t* blob_bytes);
 
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);

@@ -38,7 +38,8 @@ class Sweeper:
     def __init__(self, models, chis, per_node=False, prec="fp64", stream=None,
                  lanczos_tol=0.0, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
-                 persistent=True, streams=8, polar_blocks=0, double_float=True):
+                 persistent=True, streams=8, polar_blocks=0, double_float=True, wait_polls=0,
+                 tc_engine=0, tiles=None):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -54,7 +55,9 @@ class Sweeper:
             A = np.ascontiguousarray(m.A, dtype=np.float64)
             B = np.ascontiguousarray(m.B, dtype=np.float64)
             self._keep += [o, A, B]
-            d = 2
+            d = int(round(o.shape[0] ** (1.0 / m.Ly)))
+            if d ** m.Ly != o.shape[0]:
+                raise TTNError(f"one-site term of dimension {o.shape[0]} is not d^Ly for Ly={m.Ly}")
             probs[i] = _abi.Problem(m.Lx, m.Ly, d, int(chi), A.shape[0], int(bool(per_node)),
                                     _ptr(o), _ptr(A), _ptr(B))
         opt = _abi.Options()
@@ -70,6 +73,12 @@ class Sweeper:
         opt.polar_blocks = int(polar_blocks)
         opt.double_float = int(bool(double_float))
         opt.top_mode = int(top_mode)
+        opt.wait_polls = int(wait_polls)
+        opt.tc_engine = int(tc_engine)
+        if tiles:
+            self._tiles = ctypes.create_string_buffer(bytes(tiles), len(tiles))
+            opt.tiles = ctypes.cast(self._tiles, ctypes.c_void_p)
+            opt.tiles_bytes = len(tiles)
         if shift is not None:
             opt.shift = float(shift)
         self.opt = opt
@@ -128,15 +137,55 @@ class Sweeper:
             off += k
         return ws, V
 
-    def sweep(self, n_sweeps=1):
-        """Run sweeps; returns energies of shape (n_sweeps, n_instances)."""
+    def _sweep_status(self, rc, strict):
+        # TTN_ENOCONV from ttn_sweep: the last top solve missed its tolerance;
+        # the tensors are a valid updated state (usual in the first sweeps)
+        self.top_converged = rc != _abi.TTN_ENOCONV_CODE
+        if rc == _abi.TTN_ENOCONV_CODE and not strict:
+            return
+        self._check(rc, "sweep")
+
+    def sweep(self, n_sweeps=1, strict=False):
+        """Run sweeps; returns energies of shape (n_sweeps, n_instances).
+        ``self.top_converged`` tells whether the last top solves met their
+        tolerance (with ``strict`` a miss raises)."""
         E = np.empty((n_sweeps, self.n))
-        self._check(self.lib.ttn_sweep(self.h, n_sweeps, _ptr(E)), "sweep")
+        self._sweep_status(self.lib.ttn_sweep(self.h, n_sweeps, _ptr(E)), strict)
         return E
 
-    def sweep_async(self, n_sweeps=1):
-        """Enqueue sweeps on the stream without reading energies back."""
-        self._check(self.lib.ttn_sweep(self.h, n_sweeps, None), "sweep")
+    def sweep_async(self, n_sweeps=1, strict=False):
+        """Run sweeps without reading the energies back."""
+        self._sweep_status(self.lib.ttn_sweep(self.h, n_sweeps, None), strict)
+
+    def sweep_until(self, tol=1e-10, max_sweeps=1000):
+        """Sweep until the energy per spin of every instance changes by less
+        than ``tol`` between sweeps (Sec. IV), at most ``max_sweeps``.
+        Returns (converged, energies of shape (sweeps run, n_instances))."""
+        E = np.empty((max_sweeps, self.n))
+        done = ctypes.c_int()
+        rc = self.lib.ttn_sweep_until(self.h, float(tol), int(max_sweeps), ctypes.byref(done), _ptr(E))
+        if rc not in (0, _abi.TTN_ENOCONV_CODE):
+            self._check(rc, "sweep_until")
+        return rc == 0, E[:done.value].copy()
+
+    def autotune(self, reps=3):
+        """Time the candidate tile widths, engines and split counts of every
+        product shape during one sweep and keep the fastest; returns the
+        table as bytes (for ``tiles=`` of another Sweeper)."""
+        n = ctypes.c_size_t()
+        self._check(self.lib.ttn_autotune(self.h, int(reps), None, ctypes.byref(n)), "autotune")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self.lib.ttn_autotune(self.h, 0, buf, ctypes.byref(n)), "autotune export")
+        return bytes(buf.raw[:n.value])
+
+    def diagnostics(self, inst=0):
+        """Isometry defect, density-matrix traces and symmetry, norm of v,
+        last energy change per spin, top-solve convergence (FP64, device)."""
+        out = np.zeros(8)
+        self._check(self.lib.ttn_diagnostics(self.h, inst, _ptr(out), 8), "diagnostics")
+        keys = ["isometry_defect", "trace_error", "asymmetry", "norm_error", "delta_e",
+                "top_converged", "krylov_dim", "polar_unconverged"]
+        return dict(zip(keys, out.tolist()))
 
     def energy(self, inst=0):
         E = ctypes.c_double()

@@ -8,6 +8,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libttn.so")
 
 TTN_FP64, TTN_TF32, TTN_TF32X3, TTN_BF16, TTN_BF16X3 = range(5)
+TTN_ENOCONV_CODE = -4
+TTN_ETIMEOUT_CODE = -5
 STATUS = {0: "TTN_OK", -1: "TTN_EINVAL", -2: "TTN_ENOMEM", -3: "TTN_ECUDA",
           -4: "TTN_ENOCONV", -5: "TTN_ETIMEOUT", -6: "TTN_ENAN"}
 
@@ -27,7 +29,9 @@ class Options(ctypes.Structure):
                 ("polar_damping", ctypes.c_double), ("deterministic", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int),
-                ("double_float", ctypes.c_int)]
+                ("double_float", ctypes.c_int), ("tc_engine", ctypes.c_int),
+                ("wait_polls", ctypes.c_int), ("tiles", ctypes.c_void_p),
+                ("tiles_bytes", ctypes.c_size_t)]
 
 
 # Every symbol the header declares, with its signature.
@@ -42,6 +46,9 @@ SIGNATURES = {
     "ttn_set_isometries": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
     "ttn_get_isometries": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
     "ttn_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "ttn_sweep_until": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), _dp]),
+    "ttn_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int]),
     "ttn_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
     "ttn_ascend": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "ttn_rdm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
@@ -53,8 +60,12 @@ SIGNATURES = {
     "ttn_selftest_bytes": (ctypes.c_size_t, []),
     "ttn_selftest_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, _dp,
                                          ctypes.c_int, ctypes.c_void_p]),
+    "ttn_selftest_df": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, _dp, ctypes.c_int,
+                                       ctypes.c_void_p]),
     "ttn_close_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
+    "ttn_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_size_t)]),
     "ttn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ttn_destroy": (None, [ctypes.c_void_p]),
 }

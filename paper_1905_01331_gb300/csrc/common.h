@@ -45,6 +45,11 @@ struct GemmDesc {
   int sym;           // C = A A^T (symmetric, M == N): only tiles on or above the
                      // diagonal are computed and mirrored (FP64 engine)
   int sym_tile;      // tile size the launcher used (set by the launcher)
+  int tc_engine;     // tensor-core engine: 0 the TMA-fed kernel where the operand
+                     // layouts allow it, 1 always the thread-staged kernel
+  int tile;          // tile width chosen by the autotuner (0: the launcher's
+                     // default): BN of a tensor-core kernel, the square tile of
+                     // the FP64 engine
 };
 // passed by value as a kernel parameter (limit 32764 bytes)
 static_assert(sizeof(GemmDesc) + 64 < 32764, "GemmDesc too large for a kernel parameter");
@@ -53,6 +58,9 @@ static_assert(sizeof(GemmDesc) + 64 < 32764, "GemmDesc too large for a kernel pa
 // kernel by desc.prec).  Returns the number of kernel launches.
 int gemm_launch(const GemmDesc& d, cudaStream_t stream);
 
+// SM count of the current device (cached per device; 152 without a device).
+int device_sm_count();
+
 // Split count / partial-buffer size the launcher will use for a descriptor.
 int gemm_pick_splits(const GemmDesc& d);
 size_t gemm_partial_elems(const GemmDesc& d, int splits);
@@ -60,6 +68,9 @@ size_t gemm_partial_elems(const GemmDesc& d, int splits);
 // Tensor-core path (gemm_tc.cu).
 int gemm_tc_launch(const GemmDesc& d, cudaStream_t stream);
 bool gemm_tc_supported(const GemmDesc& d);
+// The TMA-fed kernel can run this product (TF32 modes, FP32 operands with a
+// contiguous K or MN index, aligned strides).
+bool gemm_tma_eligible(const GemmDesc& d);
 int tc_pick_splits(const GemmDesc& d);
 void gemm_tc_init();
 
@@ -137,6 +148,7 @@ struct ComposeArgs {
   unsigned* bar;
   int* err;
   int grid_share;   // concurrent streams sharing the GPU: the grid takes 1/grid_share of it
+  int max_spin;     // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
 };
 bool compose_supported(int P, int nsteps);
 // FP64 flops the composition kernel executes (symmetric tiles only).
@@ -176,6 +188,7 @@ struct LanczosArgs {
   double tol;
   unsigned* bar;
   int* err;
+  int max_spin;       // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
   // double-float matrix-vector products (mixed modes): df != 0 and pair
   // buffers (each matrix or vector: n hi floats, then n lo floats) for the
   // operators of both top sites ((1+2K) matrices each; s1p unused when s1 ==
@@ -212,6 +225,19 @@ int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl,
 
 // dst[i] = (float) src[i]
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s);
+
+// Energy change per spin after a sweep (Sec. IV convergence test): dstat =
+// [previous energy, change per spin, tolerance], istat[2] = converged,
+// istat[3] = sweeps seen (the first is compared with nothing).
+int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cudaStream_t s);
+// flag[0] |= 1 when max |A - I| (P x P) exceeds thr or is not a number.
+int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s);
+// dst[i] = src ? src[i] : value for i < n.
+int store_ints(int* dst, const int* src, int n, int value, cudaStream_t s);
+// One CTA: out = [sum of traces, max |M - I| (or |M|), max |M - M^T|] over nb
+// n x n blocks at M + b * stride.
+int mat_stats(const double* M, int n, int nb, long long stride, int sub_identity, double* out,
+              cudaStream_t s);
 
 // NaN/Inf scan: flag[0] |= 1 if any element is not finite.
 int finite_check(const double* x, long long n, int* flag, cudaStream_t s);

@@ -179,10 +179,34 @@ int launch_tile(const GemmDesc& d, cudaStream_t s) {
 
 }  // namespace
 
+// SM count of the current device, read once per device (152 on GB300, also
+// the value when no device is visible, e.g. when only sizes are planned).
+int device_sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    cache[dev] = sms;
+  }
+  return cache[dev];
+}
+
 // 64 x 64 tiles when they alone give two waves, else 32 x 32 or 16 x 16.
 int f64_tile(const GemmDesc& d) {
+  if (d.tile == 16 || d.tile == 32 || d.tile == 64) return d.tile;
   const long long b = (long long)d.B0 * d.B1;
-  if (d.M >= 64 && d.N >= 64 && ((long long)((d.M + 63) / 64) * ((d.N + 63) / 64) * b >= 296 ||
+  const long long wave2 = 2LL * device_sm_count();
+  if (d.M >= 64 && d.N >= 64 && ((long long)((d.M + 63) / 64) * ((d.N + 63) / 64) * b >= wave2 ||
                                  total_k_tiles(d) < 8))
     return 64;
   if (d.M >= 32 && d.N >= 32) return 32;
@@ -198,8 +222,9 @@ int gemm_pick_splits(const GemmDesc& d) {
   const long long tiles = (d.sym && d.M == d.N) ? tm * (tm + 1) / 2 : tm * tn;
   const long long base = tiles * d.B0 * d.B1;
   const int kt = total_k_tiles(d);
-  if (base >= 296 || kt < 4) return 1;
-  int s = (int)std::min<long long>((296 + base - 1) / base, kt / 2);
+  const long long wave2 = 2LL * device_sm_count();   // two CTAs per SM
+  if (base >= wave2 || kt < 4) return 1;
+  int s = (int)std::min<long long>((wave2 + base - 1) / base, kt / 2);
   s = std::max(1, std::min(s, 64));
   return s;
 }
@@ -295,6 +320,10 @@ extern "C" int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, in
   splits = static_cast<int>(std::min<long long>(splits, kNoAllocScratchDoubles / per_split));
   d.splits = std::max(1, splits);
   d.partial = scratch;
-  gemm_launch(d, reinterpret_cast<cudaStream_t>(stream));
+  // an error left pending by earlier work of the caller is reported, not
+  // cleared, and nothing is launched; an error of this call's own launches
+  // is reported and cleared
+  if (cudaPeekAtLastError() != cudaSuccess) return TTN_ECUDA;
+  if (gemm_launch(d, reinterpret_cast<cudaStream_t>(stream)) < 1) return TTN_ECUDA;
   return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ECUDA;
 }

@@ -18,10 +18,13 @@
 // FP64 (or a split-K partial).  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, waits (bounded) for its own MMAs,
 // frees its TMEM and returns.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 
 #include "common.h"
 
@@ -665,6 +668,515 @@ __global__ void splitk_reduce_tc(const GemmDesc d) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-fed, warp-specialised variant for the TF32 modes with FP32 operands
+// whose K index or MN index is contiguous (every full-layer product of the
+// sweep).  Per CTA one 128 x BN output tile and a ring of S stages; a stage
+// holds the raw FP32 tiles of A (128 x 32) and B (BN x 32), loaded by TMA
+// (SWIZZLE_128B: the K-major canonical layout of the MMA; an MN-contiguous
+// operand arrives as 32 x 32 boxes and is transposed), converted in place to
+// TF32 heads by four converter warps, which also write the tails of the
+// split form; one thread issues the tcgen05.mma of the stage and commits its
+// completion to the stage's "empty" barrier, which frees it for the next TMA.
+//   warp 0: TMA producer (one thread)       warp 1: TMEM owner, MMA issuer
+//   warps 2-5: converters, then the epilogue (TMEM lanes 32 (w % 4) ..)
+// Every wait is bounded; an expired wait raises the error flag and the CTA's
+// abort flag, every role then stops, the producer waits (bounded) for the
+// copies it issued, the MMA thread commits so that the epilogue can wait for
+// its MMAs, and TMEM is freed.
+// ---------------------------------------------------------------------------
+
+int tc_total_tiles(const GemmDesc& d, int BK);
+
+constexpr int kTThreads = 192;
+constexpr int kTConv = 128;
+constexpr int kTSmem = 196608;           // bytes of the stage ring
+
+struct TmaParams {
+  CUtensorMap a[kMaxGroups];
+  CUtensorMap b[kMaxGroups];
+  int a_mn[kMaxGroups], b_mn[kMaxGroups];     // 1: MN index contiguous (transposed boxes)
+  int a_use[kMaxGroups], b_use[kMaxGroups];   // bit i: map dim i is a real index (else coordinate 0)
+  int total_tiles;
+  int* err;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity,
+                                             const volatile int* abort_flag) {
+  const uint32_t a = smem_u32(bar);
+  for (long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                          int c2, int c3, int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// Named barrier of the four converter warps (id 1), with an AND vote.
+__device__ __forceinline__ bool conv_vote(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v))
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// TF32 head and tail of four FP32 values (head rounded to nearest).
+template <bool kSplit>
+__device__ __forceinline__ void split4(const float* x, uint4& h, uint4& l) {
+  uint32_t hh[4], ll[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hh[q] = tf32_bits(x[q]);
+    ll[q] = kSplit ? tf32_bits(x[q] - __uint_as_float(hh[q])) : 0u;
+  }
+  h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+  l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+}
+
+// A K-major raw tile of ROWS rows is already in the MMA layout: heads in
+// place, tails at the same offsets of the tail tile.
+template <bool kSplit, int ROWS>
+__device__ __forceinline__ void convert_kmajor(uint8_t* hi, uint8_t* lo, int ct) {
+  constexpr int kChunks = ROWS * 128 / 16;
+#pragma unroll 4
+  for (int i = ct; i < kChunks; i += kTConv) {
+    const float4 v = *reinterpret_cast<const float4*>(hi + 16 * i);
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    uint4 h, l;
+    split4<kSplit>(x, h, l);
+    *reinterpret_cast<uint4*>(hi + 16 * i) = h;
+    if constexpr (kSplit) *reinterpret_cast<uint4*>(lo + 16 * i) = l;
+  }
+}
+
+// An MN-contiguous operand arrives as ROWS / 32 boxes of 32 K rows x 32 MN
+// values (box j at hi + 4096 j, row k at 128 k, 16-byte chunk c stored at
+// c ^ (k & 7)).  Converter thread ct owns MN row ct: it reads its 32 values,
+// all converter threads meet, and it writes the row in the K-major layout.
+template <bool kSplit, int ROWS>
+__device__ __forceinline__ void convert_mnmajor(uint8_t* hi, uint8_t* lo, int ct) {
+  float v[32];
+  const bool active = ct < ROWS;
+  if (active) {
+    const int j = ct >> 5, c = (ct & 31) >> 2, e = ct & 3;
+    const uint8_t* box = hi + 4096 * j;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      v[k] = *reinterpret_cast<const float*>(box + 128 * k + ((c ^ (k & 7)) << 4) + 4 * e);
+  }
+  conv_sync();
+  if (active) {
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+      uint4 h, l;
+      split4<kSplit>(v + 4 * kc, h, l);
+      const int off = 128 * ct + ((kc ^ (ct & 7)) << 4);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      if constexpr (kSplit) *reinterpret_cast<uint4*>(lo + off) = l;
+    }
+  }
+}
+
+// 16 accumulators of row m, columns n..n+15, to C (or the split-K partials),
+// with vector stores where the row is contiguous and aligned.
+__device__ __forceinline__ void store_row16(const GemmDesc& d, int b, int b0, int b1, int split_id,
+                                            int m, int n, const uint32_t* r, float af, float bf) {
+  const bool full = n + 16 <= d.N;
+  if (d.splits > 1) {
+    float* P = reinterpret_cast<float*>(d.partial) +
+               (static_cast<long long>(split_id) * d.B0 * d.B1 + b) * static_cast<long long>(d.M) * d.N +
+               static_cast<long long>(m) * d.N + n;
+    if (full && (reinterpret_cast<uintptr_t>(P) & 15) == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(P + j) =
+            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                        __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+    } else {
+      for (int j = 0; j < 16 && n + j < d.N; ++j) P[j] = __uint_as_float(r[j]);
+    }
+    return;
+  }
+  const long long cb = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m;
+  if (full && d.sc_n == 1 && d.beta == 0.0) {
+    if (d.c_f32) {
+      float* C = static_cast<float*>(d.C) + cb + n;
+      if ((reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(C + j) =
+              make_float4(af * __uint_as_float(r[j]), af * __uint_as_float(r[j + 1]),
+                          af * __uint_as_float(r[j + 2]), af * __uint_as_float(r[j + 3]));
+        return;
+      }
+    } else {
+      double* C = static_cast<double*>(d.C) + cb + n;
+      if ((reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2)
+          *reinterpret_cast<double2*>(C + j) =
+              make_double2(f32_to_f64(af * __uint_as_float(r[j])),
+                           f32_to_f64(af * __uint_as_float(r[j + 1])));
+        return;
+      }
+    }
+  }
+  for (int j = 0; j < 16; ++j)
+    if (n + j < d.N) store_out(d, cb + static_cast<long long>(n + j) * d.sc_n, __uint_as_float(r[j]), af, bf);
+}
+
+template <bool kSplit, int BN>
+__global__ void __launch_bounds__(kTThreads, 1)
+    gemm_tma_kernel(const GemmDesc d, const __grid_constant__ TmaParams tp) {
+  constexpr int kA = kBM * 128;                     // raw A tile: 128 rows x 32 FP32
+  constexpr int kB = BN * 128;
+  constexpr int kHi = kA + kB;                      // raw tiles, TF32 heads after conversion
+  constexpr int kStageBytes = (kSplit ? 2 : 1) * kHi;
+  constexpr int S = kTSmem / kStageBytes < 8 ? kTSmem / kStageBytes : 8;
+  constexpr uint32_t kIdesc = instr_desc(2u, kBM, BN);
+  static_assert(S >= 2, "stage ring");
+  static_assert(BN == 64 || BN == 128, "tile width");
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full_bar[S], conv_bar[S], empty_bar[S], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  if (d.skip && *d.skip) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (d.N + BN - 1) / BN;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+  const int b = blockIdx.y;
+  const int b0 = b % d.B0, b1 = b / d.B0;
+  const int split_id = blockIdx.z;
+  const int m0 = tm * kBM, n0 = tn * BN;
+  const int t_lo = static_cast<int>(static_cast<long long>(tp.total_tiles) * split_id / d.splits);
+  const int t_hi =
+      static_cast<int>(static_cast<long long>(tp.total_tiles) * (split_id + 1) / d.splits);
+  const int nk = t_hi - t_lo;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&conv_bar[s])),
+                   "r"(kTConv));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)));
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0 && nk > 0) {
+      // ---- TMA producer ----
+      int kt = 0, t_global = 0;
+      bool ok = true;
+      for (int g = 0; g < d.ngroups && t_global < t_hi && ok; ++g) {
+        const Group& G = d.g[g];
+        const int nt = G.K / 32;
+        if (t_global + nt <= t_lo) { t_global += nt; continue; }
+        const int first = max(0, t_lo - t_global), last = min(nt, t_hi - t_global);
+        const int k0m = (1 << G.k0_log2) - 1;
+        const int ua = tp.a_use[g], ub = tp.b_use[g];
+        for (int t = first; t < last; ++t) {
+          const int s = kt % S, u = kt / S;
+          if (u > 0 && !mbar_wait_ab(&empty_bar[s], (u - 1) & 1, abort_v)) { ok = false; break; }
+          const uint32_t st = smem_u32(smem + s * kStageBytes);
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          mbar_expect_tx(&full_bar[s], kHi);
+          const int kb = t * 32;
+          const int k0 = kb & k0m, k1 = kb >> G.k0_log2;
+          const int a2 = (ua & 4) ? k1 : 0, a3 = (ua & 8) ? b0 : 0, a4 = (ua & 16) ? b1 : 0;
+          const int c2 = (ub & 4) ? k1 : 0, c3 = (ub & 8) ? b0 : 0, c4 = (ub & 16) ? b1 : 0;
+          if (!tp.a_mn[g]) {
+            tma_load5(st, &tp.a[g], k0, m0, a2, a3, a4, fb);
+          } else {
+#pragma unroll
+            for (int j = 0; j < kBM / 32; ++j) tma_load5(st + 4096 * j, &tp.a[g], m0 + 32 * j, k0, a2, a3, a4, fb);
+          }
+          if (!tp.b_mn[g]) {
+            tma_load5(st + kA, &tp.b[g], k0, n0, c2, c3, c4, fb);
+          } else {
+#pragma unroll
+            for (int j = 0; j < BN / 32; ++j) tma_load5(st + kA + 4096 * j, &tp.b[g], n0 + 32 * j, k0, c2, c3, c4, fb);
+          }
+          ++kt;
+        }
+        t_global += nt;
+      }
+      if (!ok) {
+        *abort_v = 1;
+        if (tp.err) atomicOr(tp.err, 1);
+      }
+      // the copies of the last use of every stage must land before the CTA exits
+      for (int q = max(0, kt - S); q < kt; ++q) mbar_wait(&full_bar[q % S], (q / S) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      bool ok = true;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % S, u = kt / S;
+        if (!mbar_wait_ab(&conv_bar[s], u & 1, abort_v)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi = smem_u32(smem + s * kStageBytes);
+        const uint32_t b_hi = a_hi + kA;
+        const uint32_t a_lo = a_hi + kHi, b_lo = a_lo + kA;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t off = j * 32;   // 8 TF32 values of K per instruction
+          const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+          if constexpr (kSplit) {
+            mma<false>(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), kIdesc, acc);
+            mma<false>(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), kIdesc, 1u);
+            mma<false>(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), kIdesc, 1u);
+          } else {
+            mma<false>(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), kIdesc, acc);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+      }
+      if (!ok) {
+        *abort_v = 1;
+        if (tp.err) atomicOr(tp.err, 1);
+      }
+      mma_commit(&done_bar);   // arrives once every MMA issued above is complete
+    }
+  } else {
+    // ---- converters ----
+    const int ct = threadIdx.x - 64;
+    bool ok = true;
+    int kt = 0, t_global = 0;
+    for (int g = 0; g < d.ngroups && t_global < t_hi && ok; ++g) {
+      const Group& G = d.g[g];
+      const int nt = G.K / 32;
+      if (t_global + nt <= t_lo) { t_global += nt; continue; }
+      const int first = max(0, t_lo - t_global), last = min(nt, t_hi - t_global);
+      const bool amn = tp.a_mn[g] != 0, bmn = tp.b_mn[g] != 0;
+      for (int t = first; t < last; ++t) {
+        const int s = kt % S, u = kt / S;
+        // all converter threads take the same decision (their named barriers follow)
+        if (!conv_vote(mbar_wait_ab(&full_bar[s], u & 1, abort_v))) { ok = false; break; }
+        uint8_t* st = smem + s * kStageBytes;
+        if (amn) convert_mnmajor<kSplit, kBM>(st, st + kHi, ct);
+        else convert_kmajor<kSplit, kBM>(st, st + kHi, ct);
+        if (bmn) convert_mnmajor<kSplit, BN>(st + kA, st + kHi + kA, ct);
+        else convert_kmajor<kSplit, BN>(st + kA, st + kHi + kA, ct);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv_bar[s]);
+        ++kt;
+      }
+      t_global += nt;
+    }
+    if (!ok) {
+      *abort_v = 1;
+      if (tp.err && ct == 0) atomicOr(tp.err, 1);
+    }
+    // ---- epilogue: wait for the MMAs (also after an abort), then TMEM -> C ----
+    const bool done = mbar_wait(&done_bar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // one decision per warp: tcgen05.ld is a warp-collective instruction
+    if (__all_sync(0xffffffffu, done && !*abort_v)) {
+      const int quarter = warp & 3;
+      const int row = quarter * 32 + lane;
+      const int m = m0 + row;
+      const float af = static_cast<float>(d.alpha), bf = static_cast<float>(d.beta);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        if (nk == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = 0u;
+        } else {
+          const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        if (m < d.M && n0 + c0 < d.N) store_row16(d, b, b0, b1, split_id, m, n0 + c0, r, af, bf);
+      }
+    } else if (!done && tp.err && ct == 0) {
+      atomicOr(tp.err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+template <bool kSplit, int BN>
+void tma_configure() {
+  cudaFuncSetAttribute(gemm_tma_kernel<kSplit, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kTSmem + 1024);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Layout of one operand for the TMA kernel: FP32, K0 a multiple of 32 (a K
+// tile never straddles two K1 slices), K or MN index contiguous, every other
+// stride a multiple of 16 bytes, 16-byte aligned base.  Arithmetic only, so
+// that the split count of a product is the same when it is planned and run.
+bool tma_operand_ok(const Operand& o, int k0_log2) {
+  if (!o.f32 || k0_log2 < 5) return false;
+  if ((reinterpret_cast<uintptr_t>(o.p) & 15) != 0) return false;
+  const bool kmaj = o.s_k0 == 1, mnmaj = o.s_mn == 1;
+  if (!kmaj && !mnmaj) return false;
+  const long long other = kmaj ? o.s_mn : o.s_k0;
+  if (other <= 0 || (other & 3)) return false;
+  const long long rest[3] = {o.s_k1, o.s_b0, o.s_b1};
+  for (long long r : rest)
+    if (r < 0 || (r & 3)) return false;
+  return true;
+}
+
+bool tma_eligible(const GemmDesc& d) {
+  if (d.prec != 1 && d.prec != 2) return false;
+  for (int g = 0; g < d.ngroups; ++g)
+    if (!tma_operand_ok(d.g[g].a, d.g[g].k0_log2) || !tma_operand_ok(d.g[g].b, d.g[g].k0_log2))
+      return false;
+  return d.ngroups > 0 && d.ngroups <= kMaxGroups;
+}
+
+int tma_bn(int N) { return N >= 128 ? 128 : 64; }
+
+// Tensor map of one operand: dims (contiguous index, the other of K0 / MN,
+// K1, B0, B1); an index of extent 1 or stride 0 (a broadcast) becomes a dummy
+// dimension of extent 1 whose coordinate is 0 (bit clear in *use).
+bool encode_operand(const Operand& o, int k0_log2, int K, int rows, int B0, int B1, int box_rows,
+                    CUtensorMap* map, int* mn_major, int* use) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const long long K0 = 1LL << k0_log2, K1 = K >> k0_log2;
+  const bool kmaj = o.s_k0 == 1;
+  long long ext[5] = {kmaj ? K0 : rows, kmaj ? rows : K0, K1, B0, B1};
+  long long str[5] = {1, kmaj ? o.s_mn : o.s_k0, o.s_k1, o.s_b0, o.s_b1};
+  *use = 0;
+  cuuint64_t gdim[5], gstride[4];
+  long long prev_bytes = 4, prev_ext = ext[0];
+  gdim[0] = static_cast<cuuint64_t>(ext[0]);
+  for (int i = 1; i < 5; ++i) {
+    long long bytes;
+    if (ext[i] > 1 && str[i] > 0) {
+      *use |= 1 << i;
+      bytes = str[i] * 4;
+    } else {
+      ext[i] = 1;
+      bytes = prev_bytes * prev_ext;   // dummy: nested after the previous dimension
+    }
+    if (bytes % 16 != 0 || bytes >= (1LL << 40)) return false;
+    gdim[i] = static_cast<cuuint64_t>(ext[i]);
+    gstride[i - 1] = static_cast<cuuint64_t>(bytes);
+    prev_bytes = bytes;
+    prev_ext = ext[i];
+  }
+  const cuuint32_t box[5] = {32u, kmaj ? static_cast<cuuint32_t>(box_rows) : 32u, 1u, 1u, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  *mn_major = kmaj ? 0 : 1;
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(o.p), gdim, gstride, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Returns 1 (launched) or 0 (a tensor map could not be encoded: the caller
+// runs the thread-staged kernel instead).
+template <bool kSplit, int BN>
+int launch_tma(const GemmDesc& d, cudaStream_t s) {
+  static TmaParams tp;   // host staging of the kernel parameter (launch copies it)
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  memset(&tp, 0, sizeof(tp));
+  for (int g = 0; g < d.ngroups; ++g) {
+    const Group& G = d.g[g];
+    if (!encode_operand(G.a, G.k0_log2, G.K, d.M, d.B0, d.B1, kBM, &tp.a[g], &tp.a_mn[g], &tp.a_use[g]))
+      return 0;
+    if (!encode_operand(G.b, G.k0_log2, G.K, d.N, d.B0, d.B1, BN, &tp.b[g], &tp.b_mn[g], &tp.b_use[g]))
+      return 0;
+  }
+  tp.total_tiles = tc_total_tiles(d, 32);
+  tp.err = d.err;
+  const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
+  dim3 grid(tiles, d.B0 * d.B1, d.splits);
+  gemm_tma_kernel<kSplit, BN><<<grid, kTThreads, kTSmem + 1024, s>>>(d, tp);
+  return 1;
+}
+
+int launch_tma_bn(const GemmDesc& d, cudaStream_t s) {
+  const bool split = d.prec == 2;
+  const int bn = (d.tile == 64 || d.tile == 128) ? d.tile : tma_bn(d.N);
+  if (bn == 128) return split ? launch_tma<true, 128>(d, s) : launch_tma<false, 128>(d, s);
+  return split ? launch_tma<true, 64>(d, s) : launch_tma<false, 64>(d, s);
+}
+
 int tc_bn(int N) { return N >= 64 ? 64 : 32; }
 
 int tc_total_tiles(const GemmDesc& d, int BK) {
@@ -686,7 +1198,7 @@ int launch_tc(const GemmDesc& d, cudaStream_t s, int* err) {
 
 template <bool kBF16, bool kSplit>
 int launch_tc_bn(const GemmDesc& d, cudaStream_t s, int* err) {
-  switch (tc_bn(d.N)) {
+  switch ((d.tile == 32 || d.tile == 64 || d.tile == 128) ? d.tile : tc_bn(d.N)) {
     case 128: return launch_tc<kBF16, kSplit, 128>(d, s, err);
     case 64: return launch_tc<kBF16, kSplit, 64>(d, s, err);
     default: return launch_tc<kBF16, kSplit, 32>(d, s, err);
@@ -696,11 +1208,15 @@ int launch_tc_bn(const GemmDesc& d, cudaStream_t s, int* err) {
 }  // namespace
 
 void gemm_tc_init() {
+  tma_configure<false, 64>(); tma_configure<false, 128>();
+  tma_configure<true, 64>(); tma_configure<true, 128>();
   tc_configure<false, false, 32>(); tc_configure<false, false, 64>(); tc_configure<false, false, 128>();
   tc_configure<false, true, 32>(); tc_configure<false, true, 64>(); tc_configure<false, true, 128>();
   tc_configure<true, false, 32>(); tc_configure<true, false, 64>(); tc_configure<true, false, 128>();
   tc_configure<true, true, 32>(); tc_configure<true, true, 64>(); tc_configure<true, true, 128>();
 }
+
+bool gemm_tma_eligible(const GemmDesc& d) { return tma_eligible(d); }
 
 bool gemm_tc_supported(const GemmDesc& d) {
   if (d.prec == 0) return false;
@@ -712,16 +1228,20 @@ bool gemm_tc_supported(const GemmDesc& d) {
 
 int tc_pick_splits(const GemmDesc& d) {
   const int BK = (d.prec == 3 || d.prec == 4) ? 64 : 32;
+  const int bn = (d.tc_engine != 1 && tma_eligible(d)) ? tma_bn(d.N) : tc_bn(d.N);
   const long long base = static_cast<long long>((d.M + kBM - 1) / kBM) *
-                         ((d.N + tc_bn(d.N) - 1) / tc_bn(d.N)) * d.B0 * d.B1;
+                         ((d.N + bn - 1) / bn) * d.B0 * d.B1;
   const int kt = tc_total_tiles(d, BK);
-  if (base >= 148 || kt < 8) return 1;
-  int s = static_cast<int>(std::min<long long>((148 + base - 1) / base, kt / 4));
+  const long long sms = device_sm_count();
+  if (base >= sms || kt < 8) return 1;
+  int s = static_cast<int>(std::min<long long>((sms + base - 1) / base, kt / 4));
   return std::max(1, std::min(s, 64));
 }
 
 int gemm_tc_launch(const GemmDesc& d, cudaStream_t s) {
   int n = 0;
+  if (d.tc_engine != 1 && tma_eligible(d)) n = launch_tma_bn(d, s);
+  if (n == 0)
   switch (d.prec) {
     case 1: n = launch_tc_bn<false, false>(d, s, d.err); break;
     case 2: n = launch_tc_bn<false, true>(d, s, d.err); break;

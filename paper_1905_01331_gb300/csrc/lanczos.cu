@@ -54,7 +54,7 @@ struct LzSmem {
   int ok;
 };
 
-__device__ bool lz_barrier(LzSmem& sm, unsigned* bar, unsigned& target, int* err) {
+__device__ bool lz_barrier(LzSmem& sm, unsigned* bar, unsigned& target, int* err, int max_spin) {
   target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -68,7 +68,7 @@ __device__ bool lz_barrier(LzSmem& sm, unsigned* bar, unsigned& target, int* err
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
-      if (++spins > kLMaxSpin) { atomicOr(err, 4); ok = 0; break; }
+      if (++spins > max_spin) { atomicOr(err, 4); ok = 0; break; }
       __nanosleep(32);
     }
     sm.ok = ok;
@@ -641,13 +641,13 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
     const double s = own_dot(sm, a.V, a.V, nown, bid, G, nt, c);
     if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
   }
-  if (!lz_barrier(sm, a.bar, target, a.err)) return;
+  if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
   double inv = 1.0 / sqrt(cta_ordered_sum(sm, part, G, ldp));
   for (int q = threadIdx.x; q < nown; q += kLThreads) {
     const long long e = own_index(q, bid, G, nt, c);
     if (e >= 0) store_both(a.basis, bp0, n, e, __ldcg(a.V + e) * inv);
   }
-  if (!lz_barrier(sm, a.bar, target, a.err)) return;
+  if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
   const float* s0p = a.s0p;
   const float* s1p = a.s1 == a.s0 ? a.s0p : a.s1p;
 
@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
         tile_fma(sm, c, a0, a1);
         tile_store(sm, a0, a1, a.Y + (long long)b * n, c, i0, j0);
       }
-      if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
       // phase B: w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T on the
       // owned tiles, then their projections on basis_0..j and |w|^2
       for (int t = bid; t < ntiles && df; t += G) {
@@ -732,13 +732,13 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
         tile_store(sm, a0, a1, a.w, c, i0, j0, x, sigma);
       }
       own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
-      if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
       // coefficients of the first Gram-Schmidt pass and |w|^2 (one CTA each)
       for (int i = bid; i <= j + 1; i += G) {
         const double s = cta_ordered_sum(sm, part + (i > j ? nslot : i), G, ldp);
         if (threadIdx.x == 0) __stcg(i > j ? wn2 : a.coef + i, s);
       }
-      if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
       // |w - sum c_i b_i|^2 = |w|^2 - sum c_i^2 for orthonormal b_i; when at
       // least a quarter of |w|^2 remains, one pass is accurate to rounding
       // (the second pass of "twice is enough" is needed only after heavy
@@ -768,12 +768,12 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
                       [&](long long e, double v) { __stcg(a.w + e, v); });
         __syncthreads();
         own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
-        if (!lz_barrier(sm, a.bar, target, a.err)) return;
+        if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
         for (int i = bid; i <= j + 1; i += G) {
           const double s = cta_ordered_sum(sm, part + (i > j ? nslot : i), G, ldp);
           if (threadIdx.x == 0) __stcg(a.coef + ldp + i, s);
         }
-        if (!lz_barrier(sm, a.bar, target, a.err)) return;
+        if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
         load_coefs(sm, a.coef + ldp, j + 2);
         if (threadIdx.x < 32) {
           double t = 0.0;
@@ -816,11 +816,11 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
         }
         __syncthreads();
       }
-      if (!lz_barrier(sm, a.bar, target, a.err)) return;
+      if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
       if (check && __ldcg(a.scal + 3) != 0.0) break;
     }
     // Ritz pair of the tridiagonal (CTA 0), then V = sum_i y_i basis_i
-    if (!lz_barrier(sm, a.bar, target, a.err)) return;
+    if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
     if (bid == 0) {
       ritz_pair(sm, a.alpha, a.beta, tdim, a.y, a.scal + 1, a.scal + 2);
       __syncthreads();
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
         __threadfence();
       }
     }
-    if (!lz_barrier(sm, a.bar, target, a.err)) return;
+    if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
     conv = __ldcg(a.flags);
     load_coefs(sm, a.y, tdim);
     owned_combine(a, sm, tdim, nullptr, 1.0, nown, bid, G, nt, c, n,
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
       const double s = own_dot(sm, a.V, a.V, nown, bid, G, nt, c);
       if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp, s);
     }
-    if (!lz_barrier(sm, a.bar, target, a.err)) return;
+    if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
     inv = 1.0 / sqrt(cta_ordered_sum(sm, part, G, ldp));
     for (int q = threadIdx.x; q < nown; q += kLThreads) {
       const long long e = own_index(q, bid, G, nt, c);
@@ -852,14 +852,14 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
       __stcg(a.V + e, t);
       store_both(a.basis, bp0, n, e, t);
     }
-    if (!lz_barrier(sm, a.bar, target, a.err)) return;
+    if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
   }
   // sign: <V, Vprev> >= 0
   {
     const double s = own_dot(sm, a.V, a.Vprev, nown, bid, G, nt, c);
     if (threadIdx.x == 0) __stcg(part + (long long)bid * ldp + 1, s);
   }
-  if (!lz_barrier(sm, a.bar, target, a.err)) return;
+  if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
   if (cta_ordered_sum(sm, part + 1, G, ldp) < 0.0)
     for (int q = threadIdx.x; q < nown; q += kLThreads) {
       const long long e = own_index(q, bid, G, nt, c);

@@ -372,6 +372,74 @@ __global__ void to_f32_kernel(const double* src, float* dst, long long n) {
     dst[i] = f64b::to_f32(src[i]);
 }
 
+// Energy change per spin of the last sweep (the convergence test of Sec. IV):
+// dstat[0] = energy of the previous sweep, dstat[1] = change per spin,
+// dstat[2] = tolerance; istat[2] = 1 when |change| < tolerance and a previous
+// energy exists, istat[3] = sweeps seen since the last reset.
+__global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, double inv_spins) {
+  const double e = *E;
+  const int seen = istat[3];
+  const double d = (e - dstat[0]) * inv_spins;
+  dstat[1] = seen > 0 ? d : __longlong_as_double(0x7FF8000000000000LL);
+  istat[2] = (seen > 0 && fabs(d) < dstat[2]) ? 1 : 0;
+  dstat[0] = e;
+  istat[3] = seen + 1;
+}
+
+// flag[0] |= 1 when max |A - I| of the P x P matrix A exceeds thr (one CTA).
+__global__ void far_from_identity_kernel(const double* A, int P, double thr, int* flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const long long n = (long long)P * P;
+  int mine = 0;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const int i = (int)(e / P), j = (int)(e % P);
+    const double d = A[e] - (i == j ? 1.0 : 0.0);
+    if (!(fabs(d) <= thr)) mine = 1;   // NaN counts as far
+  }
+  if (mine) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && any) atomicOr(flag, 1);
+}
+
+__global__ void store_ints_kernel(int* dst, const int* src, int n, int value) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src ? src[i] : value;
+}
+
+// Statistics of nb n x n blocks (block b at M + b*stride), one CTA, fixed
+// order: out[0] = sum of the traces, out[1] = max |M - I| (sub_identity) or
+// max |M| , out[2] = max |M_ij - M_ji|.
+__global__ void mat_stats_kernel(const double* M, int n, int nb, long long stride,
+                                 int sub_identity, double* out) {
+  __shared__ double st[256], sd[256], sa[256];
+  double tr = 0.0, dev = 0.0, asym = 0.0;
+  const long long nn = (long long)n * n;
+  for (int b = 0; b < nb; ++b) {
+    const double* Mb = M + b * stride;
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      const double x = Mb[e];
+      if (i == j) tr += x;
+      dev = fmax(dev, fabs(x - ((sub_identity && i == j) ? 1.0 : 0.0)));
+      asym = fmax(asym, fabs(x - Mb[(long long)j * n + i]));
+    }
+  }
+  st[threadIdx.x] = tr;
+  sd[threadIdx.x] = dev;
+  sa[threadIdx.x] = asym;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      st[threadIdx.x] += st[threadIdx.x + k];
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + k]);
+      sa[threadIdx.x] = fmax(sa[threadIdx.x], sa[threadIdx.x + k]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = st[0]; out[1] = sd[0]; out[2] = sa[0]; }
+}
+
 int grid_for(long long n, int per = 256, int cap = 1184) {
   long long g = (n + per - 1) / per;
   if (g < 1) g = 1;
@@ -521,6 +589,27 @@ int top_energy_sum(const double* dot, const double* vv, const double* e, int per
 
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
   to_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  return 1;
+}
+
+int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cudaStream_t s) {
+  sweep_delta_kernel<<<1, 1, 0, s>>>(E, dstat, istat, inv_spins);
+  return 1;
+}
+
+int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s) {
+  far_from_identity_kernel<<<1, 256, 0, s>>>(A, P, thr, flag);
+  return 1;
+}
+
+int store_ints(int* dst, const int* src, int n, int value, cudaStream_t s) {
+  store_ints_kernel<<<1, 32, 0, s>>>(dst, src, n, value);
+  return 1;
+}
+
+int mat_stats(const double* M, int n, int nb, long long stride, int sub_identity, double* out,
+              cudaStream_t s) {
+  mat_stats_kernel<<<1, 256, 0, s>>>(M, n, nb, stride, sub_identity, out);
   return 1;
 }
 

@@ -97,9 +97,10 @@ __device__ double tile_product(ComposeSmem& sm, const double* X, double dx, doub
 }
 
 // Grid-wide barrier of a co-resident grid: arrive on a counter zeroed before
-// the launch and poll it, at most kCMaxSpin times.  Returns false (and raises
+// the launch and poll it, at most max_spin times.  Returns false (and raises
 // *err) when the wait expires or another CTA has raised *err.
-__device__ bool grid_barrier(ComposeSmem& sm, unsigned* bar, unsigned target, int* err) {
+__device__ bool grid_barrier(ComposeSmem& sm, unsigned* bar, unsigned target, int* err,
+                             int max_spin) {
   __syncthreads();
   if (threadIdx.x == 0) {
     // arrive with release semantics, poll with acquire semantics
@@ -111,7 +112,7 @@ __device__ bool grid_barrier(ComposeSmem& sm, unsigned* bar, unsigned target, in
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
-      if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
+      if (++spins > max_spin) { atomicOr(err, 2); ok = 0; break; }
       __nanosleep(32);
     }
     sm.ok = ok;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_kernel(const ComposeA
     }
     if (last) break;
     target += gridDim.x;
-    if (!grid_barrier(sm, a.bar, target, a.err)) return;
+    if (!grid_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
     // phase 2: A_{j+1} = Pm_j T
     const int items2 = ntt * a.NJ;
     for (int it = blockIdx.x; it < items2; it += gridDim.x) {
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_kernel(const ComposeA
       store_tile(An + b * PP, P, ti, tj, v);
     }
     target += gridDim.x;
-    if (!grid_barrier(sm, a.bar, target, a.err)) return;
+    if (!grid_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
   }
 }
 
@@ -293,7 +294,8 @@ __device__ __forceinline__ void store_tile_df(float* C, int P, int ti, int tj, f
   }
 }
 
-__device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err) {
+__device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err,
+                                int max_spin) {
   __syncthreads();
   if (threadIdx.x == 0) {
     // arrive with release semantics, poll with acquire semantics
@@ -305,7 +307,7 @@ __device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned targe
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if (v >= target) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
-      if (++spins > kCMaxSpin) { atomicOr(err, 2); ok = 0; break; }
+      if (++spins > max_spin) { atomicOr(err, 2); ok = 0; break; }
       __nanosleep(32);
     }
     sm.ok = ok;
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
     }
     if (last) break;
     target += gridDim.x;
-    if (!grid_barrier_df(sm, a.bar, target, a.err)) return;
+    if (!grid_barrier_df(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
     const int items2 = ntt * a.NJ;
     for (int it = blockIdx.x; it < items2; it += gridDim.x) {
       const int b = it / ntt, ti = (it % ntt) / nt, tj = (it % ntt) % nt;
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
       store_tile_df(An + b * P2, P, ti, tj, vh, vl);
     }
     target += gridDim.x;
-    if (!grid_barrier_df(sm, a.bar, target, a.err)) return;
+    if (!grid_barrier_df(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
   }
 }
 

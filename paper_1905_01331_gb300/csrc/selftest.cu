@@ -59,7 +59,7 @@ using namespace ttn;
 
 extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n_out,
                                  void* stream) {
-  if (!d_ws || !out_rel || n_out < 11 || prec < 1 || prec > 4) return TTN_EINVAL;
+  if (!d_ws || !out_rel || n_out < 11 || prec < 1 || prec > 4) return TTN_EINVAL;   // 16 cases
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   gemm_tc_init();
   double* base = reinterpret_cast<double*>(d_ws);
@@ -173,6 +173,39 @@ extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out
     d.g[d.ngroups++] = group(mkf(A32, 1, 128, 0, 0, 0), mkf(B32, 8192, 1, 0, 0, 0), 8192, 1);
     cases.push_back({d, 128 * 128});
   }
+  // layouts of the TMA-fed engine (FP32 sources, TF32 modes): ragged tiles,
+  // two-level K with a broadcast batch, batched transposed products, the
+  // environment's mixed K-/MN-major groups, a split-K close with FP64 output
+  {  // 12: ragged M = 200, N = 96 (a partial second tile of 64), both K-major, K = 64
+    GemmDesc d = base_desc(200, 96, 1, 1, 96, 1, 0, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 64, 1, 0, 0, 0), mkf(B32, 64, 1, 0, 0, 0), 64, 1);
+    cases.push_back({d, 200 * 96});
+  }
+  {  // 13: K0 = 32, K1 = 4; batch B0 = 3 over A, B broadcast over the batch, B MN-major
+    GemmDesc d = base_desc(128, 64, 3, 1, 64, 1, 128 * 64, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 32, 1, 32 * 128, 4 * 32 * 128, 0),
+                             mkf(B32, 1, 64, 32 * 64, 0, 0), 32, 4);
+    cases.push_back({d, 3 * 128 * 64});
+  }
+  {  // 14: 16 left products: A MN-major shared, B MN-major batched (stride 128^2)
+    GemmDesc d = base_desc(128, 128, 16, 1, 128, 1, 128 * 128, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 1, 128, 0, 0, 0), mkf(B32, 1, 128, 0, 128 * 128, 0), 128, 1);
+    cases.push_back({d, 16 * 128 * 128});
+  }
+  {  // 15: environment shape, M = 128, N = 4096, K = 128: G K-major and G^T MN-major,
+     // the one-leg products MN-major
+    GemmDesc d = base_desc(128, 4096, 1, 1, 4096, 1, 0, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 128, 1, 0, 0, 0), mkf(B32, 1, 4096, 0, 0, 0), 128, 1);
+    d.g[d.ngroups++] = group(mkf(A32 + 16384, 1, 128, 0, 0, 0), mkf(B32 + 524288, 1, 4096, 0, 0, 0),
+                             128, 1);
+    cases.push_back({d, 128 * 4096});
+  }
+  {  // 16: close product, K = 16384 (split K), batch of 2 over A, FP64 output
+    GemmDesc d = base_desc(128, 128, 2, 1, 128, 1, 128 * 128, 0);
+    d.g[d.ngroups++] = group(mkf(A32, 16384, 1, 0, 16384 * 128, 0), mkf(B32, 16384, 1, 0, 0, 0),
+                             16384, 1);
+    cases.push_back({d, 2 * 128 * 128});
+  }
   const int nc = std::min<int>((int)cases.size(), n_out);
   std::vector<double> host(2);
   for (int i = 0; i < nc; ++i) {
@@ -206,4 +239,73 @@ extern "C" int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out
 extern "C" size_t ttn_selftest_bytes(void) {
   const size_t big = 16384 * 128;
   return (4 * big * 2 + 2 * big + 64 * big / 4 + 64) * sizeof(double) + 4096;
+}
+
+// Diagnostic: the double-float Gram and apply products of the polar factor
+// (gemm_df.cu) against the FP64 engine on seeded operands.  Cases: Gram X X^T
+// for (P, n2) = (128, 16384) (split K) and (96, 1000) (ragged); apply F X for
+// (128, 16384) and (40, 1000).  out_rel[i] = max |C_df - C_fp64| / max |C_fp64|.
+extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_out,
+                               void* stream) {
+  if (!d_ws || !out_rel || n_out < 4) return TTN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* base = reinterpret_cast<double*>(d_ws);
+  const size_t cap = bytes / sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t n) -> double* {
+    off = (off + 31) & ~size_t(31);
+    double* p = base + off;
+    off += n;
+    return p;
+  };
+  const size_t big = 16384 * 128;
+  double* X = take(big);                     // P x n2, FP64
+  double* F = take(128 * 128);               // P x P, FP64
+  float* Xp = reinterpret_cast<float*>(take(big));        // hi then lo (P n2 floats each)
+  float* Fp = reinterpret_cast<float*>(take(128 * 128));
+  double* C1 = take(big);
+  double* C2 = take(big);
+  double* partial = take(128 * 128 * 128);
+  double* res = take(4);
+  if (off > cap) return TTN_ENOMEM;
+  fill_uniform<<<592, 256, 0, s>>>(X, big, 31);
+  fill_uniform<<<64, 256, 0, s>>>(F, 128 * 128, 37);
+  struct Case { int gram, P; long long n2; };
+  const Case cases[4] = {{1, 128, 16384}, {1, 96, 1000}, {0, 128, 16384}, {0, 40, 1000}};
+  std::vector<double> host(2);
+  for (int i = 0; i < 4; ++i) {
+    const int P = cases[i].P;
+    const long long n2 = cases[i].n2, PN = (long long)P * n2;
+    df_split(X, Xp, Xp + PN, PN, s);
+    GemmDesc r;
+    memset(&r, 0, sizeof(r));
+    r.B0 = 1; r.B1 = 1; r.alpha = 1.0; r.prec = 0; r.C = C1; r.sc_n = 1; r.partial = partial;
+    long long celems;
+    if (cases[i].gram) {
+      r.M = P; r.N = P; r.sc_m = P;
+      Group g;
+      g.a = mk(X, n2, 1); g.b = mk(X, n2, 1); g.K = (int)n2; g.k0_log2 = 0;
+      g.a.s_k1 = 1; g.b.s_k1 = 1;   // K0 = 1: any length through the K1 stride
+      r.g[r.ngroups++] = g;
+      df_gram(Xp, Xp + PN, P, n2, C2, partial, s);
+      celems = (long long)P * P;
+    } else {
+      r.M = P; r.N = (int)n2; r.sc_m = n2;
+      Group g;
+      g.a = mk(F, P, 1); g.b = mk(X, 1, n2); g.K = P; g.k0_log2 = 0;
+      g.a.s_k1 = 1; g.b.s_k1 = n2;
+      r.g[r.ngroups++] = g;
+      df_split(F, Fp, Fp + (long long)P * P, (long long)P * P, s);
+      df_apply(Fp, Fp + (long long)P * P, Xp, Xp + PN, P, n2, C2, s);
+      celems = PN;
+    }
+    r.splits = gemm_pick_splits(r);
+    if (gemm_partial_elems(r, r.splits) > 128 * 128 * 128) r.splits = 1;
+    gemm_launch(r, s);
+    max_abs_diff<<<1, 256, 0, s>>>(C2, C1, celems, res);
+    cudaMemcpyAsync(host.data(), res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TTN_ECUDA;
+    out_rel[i] = host[0] / std::max(host[1], 1e-300);
+  }
+  return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ECUDA;
 }

@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cstring>
 
+#include "fp_rn.cuh"
+
 #ifdef __CUDACC__
 #define TDF_HD __host__ __device__ __forceinline__
 #else
@@ -51,37 +53,37 @@ TDF_HD double to_double(DF a) { return (double)a.h + (double)a.l; }
 
 // s + e = a + b exactly (Knuth)
 TDF_HD void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = rn::add(a, b);
+  const float bb = rn::sub(s, a);
+  e = rn::add(rn::sub(a, rn::sub(s, bb)), rn::sub(b, bb));
 }
 TDF_HD DF add(DF a, DF b) {
   float s, e;
   two_sum(a.h, b.h, s, e);
-  e += a.l + b.l;
-  const float h = s + e;
-  return {h, e - (h - s)};
+  e = rn::add(e, rn::add(a.l, b.l));
+  const float h = rn::add(s, e);
+  return {h, rn::sub(e, rn::sub(h, s))};
 }
 TDF_HD DF neg(DF a) { return {-a.h, -a.l}; }
 TDF_HD DF sub(DF a, DF b) { return add(a, neg(b)); }
 // product with the FMA residual of the high parts (a.l b.l dropped)
 TDF_HD DF mul(DF a, DF b) {
-  const float p = a.h * b.h;
-  float pe = std::fma(a.h, b.h, -p);
-  pe = std::fma(a.h, b.l, std::fma(a.l, b.h, pe));
-  const float h = p + pe;
-  return {h, pe - (h - p)};
+  const float p = rn::mul(a.h, b.h);
+  float pe = rn::fma(a.h, b.h, -p);
+  pe = rn::fma(a.h, b.l, rn::fma(a.l, b.h, pe));
+  const float h = rn::add(p, pe);
+  return {h, rn::sub(pe, rn::sub(h, p))};
 }
 // quotient: FP32 estimate, one correction from the pair remainder
 TDF_HD DF div(DF a, DF b) {
   const float q1 = a.h / b.h;
   const DF r = sub(a, mul({q1, 0.f}, b));
   const float q2 = r.h / b.h;
-  const float h = q1 + q2;
-  return {h, q2 - (h - q1)};
+  const float h = rn::add(q1, q2);
+  return {h, rn::sub(q2, rn::sub(h, q1))};
 }
 TDF_HD bool is_neg(DF a) { return a.h < 0.f || (a.h == 0.f && a.l < 0.f); }
-TDF_HD DF scale(DF a, float s) { return {a.h * s, a.l * s}; }
+TDF_HD DF scale(DF a, float s) { return {rn::mul(a.h, s), rn::mul(a.l, s)}; }
 TDF_HD float fabs_hi(DF a) { return std::fabs(a.h); }
 
 // 2^-e for the binary exponent e of |x| (x normal), else 1

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -74,6 +75,13 @@ struct Instance {
   double* V = nullptr;
   double* Vprev = nullptr;
   double* E = nullptr;               // energy of the last top solve
+  // device status of the instance: dstat = [energy of the previous sweep,
+  // change per spin in the last sweep, convergence tolerance]; istat = [top
+  // solve of the last sweep converged, its Krylov dimension, |change| <
+  // tolerance, sweeps seen since the last reset, a polar factor of the last
+  // sweep missed an isometry, 3 unused]
+  double* dstat = nullptr;
+  int* istat = nullptr;
   // Identity part of the one-site operators, kept exactly in FP64: the true
   // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
   std::vector<double*> eoff;
@@ -89,6 +97,25 @@ struct Instance {
 
 struct PolarBlock {
   std::vector<std::pair<double, double>> steps;  // p(A) = a I - c A
+};
+
+// An autotuned launch configuration of one grouped product.
+struct Tuned {
+  int engine, tile, splits;
+  float ms;
+};
+
+// Serialised form of the autotuner's table (the ttn_options.tiles blob).
+struct TuneBlobHeader {
+  char magic[4];       // "TTNT"
+  uint32_t version;    // 1
+  uint32_t count;
+  uint32_t reserved;
+};
+struct TuneBlobEntry {
+  uint64_t key;
+  int32_t engine, tile, splits;
+  float ms;
 };
 
 }  // namespace ttn
@@ -148,6 +175,10 @@ struct ttn_ctx {
   // checked against the buffer it points into (no launch happens)
   std::vector<std::pair<size_t, size_t>> registry;
   std::string bounds_error;
+  // autotuner: launch configuration per product shape (key: tune_key)
+  std::map<uint64_t, Tuned> tuned;
+  bool tuning = false;
+  int tune_reps = 3;
   // profiling sweep: events around every product, by engine (0 FP64, 1 TC)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -259,10 +290,103 @@ void check_desc(ttn_ctx* h, const GemmDesc& d) {
   check_range(h, d.C, max_offset(c, d.M, d.N, 1, d.B0, d.B1), d.c_f32, "C output");
 }
 
+// Key of a product for the autotuner: its shape, groups and operand layouts
+// (strides, element type, 16-byte alignment), not its addresses.  FNV-1a.
+uint64_t tune_key(const GemmDesc& d) {
+  uint64_t h = 1469598103934665603ULL;
+  auto mix = [&](long long v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (uint64_t)((v >> (8 * i)) & 0xFF);
+      h *= 1099511628211ULL;
+    }
+  };
+  auto mix_op = [&](const Operand& o) {
+    mix(o.s_mn); mix(o.s_k0); mix(o.s_k1); mix(o.s_b0); mix(o.s_b1); mix(o.f32);
+    mix((long long)((uintptr_t)o.p & 15));
+  };
+  mix(d.prec); mix(d.M); mix(d.N); mix(d.B0); mix(d.B1); mix(d.c_f32); mix(d.sym);
+  mix(d.sc_m); mix(d.sc_n); mix(d.ngroups);
+  for (int g = 0; g < d.ngroups && g < kMaxGroups; ++g) {
+    mix(d.g[g].K); mix(d.g[g].k0_log2);
+    mix_op(d.g[g].a);
+    mix_op(d.g[g].b);
+  }
+  return h;
+}
+
+// Time every candidate configuration of one product on the library stream
+// (one warm-up launch, then h->tune_reps launches between events) and keep
+// the fastest.  Products are C = sum A B without accumulation into C, so the
+// repeated launches leave the sweep's data as one launch would.
+Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
+  struct Cand { int engine, tile, splits; };
+  std::vector<Cand> cands;
+  long long ksum = 0;
+  for (int g = 0; g < d0.ngroups; ++g) ksum += d0.g[g].K;
+  std::vector<int> splits;
+  for (int s = 1; s <= 64; s *= 2)
+    if (s == 1 || (s <= ksum / 64 && gemm_partial_elems(d0, s) <= h->partial_cap)) splits.push_back(s);
+  const bool tc = d0.prec != 0 && gemm_tc_supported(d0);
+  GemmDesc dd = d0;
+  dd.tile = 0;
+  const int def_splits = std::max(1, std::min(gemm_pick_splits(dd), (int)splits.back()));
+  cands.push_back({d0.tc_engine, 0, def_splits});   // the default configuration
+  for (int s : splits) {
+    if (tc) {
+      if (gemm_tma_eligible(d0)) {
+        for (int bn : {64, 128}) cands.push_back({0, bn, s});
+      }
+      for (int bn : {32, 64, 128})
+        if (bn <= std::max(32, d0.N)) cands.push_back({1, bn, s});
+    } else {
+      for (int t : {16, 32, 64})
+        if (t == 16 || t <= std::min(d0.M, d0.N)) cands.push_back({d0.tc_engine, t, s});
+    }
+  }
+  Tuned best{cands[0].engine, cands[0].tile, cands[0].splits, 1e30f};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (const Cand& c : cands) {
+    GemmDesc e = d0;
+    e.tc_engine = c.engine;
+    e.tile = c.tile;
+    e.splits = c.splits;
+    e.partial = h->partial;
+    e.err = h->iflags + 4;
+    gemm_launch(e, h->stream);
+    cudaEventRecord(a, h->stream);
+    for (int r = 0; r < h->tune_reps; ++r) gemm_launch(e, h->stream);
+    cudaEventRecord(b, h->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    ms /= (float)std::max(1, h->tune_reps);
+    if (ms < best.ms) best = Tuned{c.engine, c.tile, c.splits, ms};
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
 // Run (or, in the plan pass, size and bounds-check) one product.
 void run(ttn_ctx* h, GemmDesc d, int prec) {
   d.prec = prec;
-  int s = gemm_pick_splits(d);
+  d.tc_engine = h->opt.tc_engine;
+  int s;
+  const uint64_t key = h->tuned.empty() && !h->tuning ? 0 : tune_key(d);
+  auto it = key ? h->tuned.find(key) : h->tuned.end();
+  if (h->tuning && !h->measuring && it == h->tuned.end() && !d.skip && d.ngroups <= kMaxGroups &&
+      d.M > 0 && d.N > 0) {
+    it = h->tuned.emplace(key, tune_product(h, d)).first;
+  }
+  if (it != h->tuned.end()) {
+    d.tc_engine = it->second.engine;
+    d.tile = it->second.tile;
+    s = it->second.splits;
+  } else {
+    s = gemm_pick_splits(d);
+  }
   size_t need = gemm_partial_elems(d, s);
   if (h->measuring) {
     if (need > h->partial_cap) h->partial_cap = need;
@@ -462,6 +586,7 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
     h->launches += batched_dot(I.V, I.V, n, 0, 1, h->scal + 6, h->red, h->stream);
     h->launches += top_energy_sum(h->scal + 4, h->scal + 6, I.eoff[I.T], I.per_node ? 1 : 0,
                                   I.c * I.L, energy_out, h->stream);
+    h->launches += store_ints(I.istat, nullptr, 2, 1, h->stream);   // no solve to converge
     return;
   }
   const int m = (int)std::min<ll>(h->lz_m, n);
@@ -479,6 +604,7 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
       a.tol = lanczos_tolerance(h);
       a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
       a.err = h->iflags + 4;
+      a.max_spin = h->opt.wait_polls;
       a.df = h->opt.prec != 0 && h->opt.double_float;
       a.s0p = reinterpret_cast<float*>(h->lz_opsp);
       a.s1p = a.s0p + 2 * (ll)(1 + 2 * I.K) * n;
@@ -488,6 +614,8 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
       const int nl = grid > 0 ? lanczos_launch(a, grid, h->stream) : -1;
       if (nl < 0) h->compose_refused = true;
       else h->launches += nl;
+      // converged flag and Krylov dimension of this solve, kept per instance
+      h->launches += store_ints(I.istat, a.flags, 2, 0, h->stream);
     }
   } else {
   int* skip = h->iflags;
@@ -520,7 +648,11 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
     h->launches += lz_combine(h->lz_basis, n, tdim, h->lz_y, I.V, h->red, nrm2, tdim, skip, conv,
                               h->stream);
   }
-  if (!h->measuring) h->launches += align_sign(I.V, I.Vprev, n, h->red, dotv, h->stream);
+  if (!h->measuring) {
+    h->launches += align_sign(I.V, I.Vprev, n, h->red, dotv, h->stream);
+    h->launches += store_ints(I.istat, conv, 1, 0, h->stream);
+    h->launches += store_ints(I.istat + 1, tdim, 1, 0, h->stream);
+  }
   }
   if (h->measuring) { top_matvec(h, I, I.V, h->lz_w, nullptr); return; }
   // energy = <V, H V> + c L
@@ -676,6 +808,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
   }
   a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
   a.err = h->iflags + 4;
+  a.max_spin = h->opt.wait_polls;
   a.grid_share = h->profiling ? 1 : (int)h->lanes.size();
   cudaEvent_t ev[2];
   if (h->profiling) {
@@ -713,11 +846,13 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream);
   }
   // The polar factor is FP64 in every mode (the small singular directions
-  // must not drown in tensor-core rounding).  FP64 mode: short blocks (at most
-  // four composed steps per Gram matrix) for full accuracy; mixed modes: two
-  // Gram matrices and two long compositions.
+  // must not drown in tensor-core rounding).  FP64 mode, and layers too small
+  // for the double-float products (P < 32, negligible cost): short blocks (at
+  // most four composed steps per Gram matrix) for full accuracy; mixed modes
+  // otherwise: two Gram matrices and two long compositions, then one more
+  // Newton-Schulz step.
   const bool short_blocks =
-      h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && prec == 0);
+      h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && (prec == 0 || P < 32));
   const std::vector<PolarBlock>& sched = short_blocks ? h->polar_f64 : h->polar_tc;
   // Mixed modes: every block's Gram and apply products in double-float
   // arithmetic on the FP32 pipes (~48 bits: the rounding amplified by a
@@ -803,6 +938,10 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     df_begin(h);
     df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
            df_gram_flops(P, N));
+    // the final step converges quadratically only from |X X^T - I| << 1:
+    // flag the instance when the blocks left it above 1e-5 (the isometry
+    // would then miss 1e-10)
+    h->launches += flag_if_far_from_identity(h->pA, P, 1e-5, I.istat + 4, h->stream);
     h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
     h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
     df_begin(h);
@@ -892,6 +1031,7 @@ void forward(ttn_ctx* h, Instance& I, int prec) {
 
 void sweep_instance(ttn_ctx* h, Instance& I) {
   const int prec = h->opt.prec;
+  if (!h->measuring) h->launches += store_ints(I.istat + 4, nullptr, 1, 0, h->stream);
   forward(h, I, prec);
   top_solve(h, I, I.E);
   top_adjoints(h, I);
@@ -901,6 +1041,23 @@ void sweep_instance(ttn_ctx* h, Instance& I) {
     environment(h, I, t, prec, h->Gam);
     polar(h, I, t, prec, h->Gam);
     descend(h, I, t, prec);
+  }
+  // energy change per spin of this sweep (Sec. IV convergence test)
+  if (!h->measuring)
+    h->launches += sweep_delta(I.E, I.dstat, I.istat, 1.0 / I.n_spins, h->stream);
+}
+
+// Gram matrices W W^T of every isometry layer (FP64), each followed by its
+// statistics (trace, max |W W^T - I|, asymmetry) at res + 3 t.
+void isometry_grams(ttn_ctx* h, Instance& I, double* res) {
+  for (int t = 0; t < I.T; ++t) {
+    const LayerView v = view(I, t, 0);
+    const ll PP = (ll)v.P * v.P;
+    GemmDesc g = desc(v.P, v.P, 1, v.NJ, h->pA, v.P, 1, 0, PP);
+    add(g, grp(op(I.W[t], v.n2, 1, 0, 0, v.Pn2), op(I.W[t], v.n2, 1, 0, 0, v.Pn2), (int)v.n2));
+    g.sym = 1;
+    run(h, g, 0);
+    if (!h->measuring) h->launches += mat_stats(h->pA, v.P, v.NJ, PP, 1, res + 3 * t, h->stream);
   }
 }
 
@@ -943,6 +1100,8 @@ void layout(ttn_ctx* h, Arena& ar) {
     I.V = ar.take((size_t)c * c);
     I.Vprev = ar.take((size_t)c * c);
     I.E = ar.take(4);
+    I.dstat = ar.take(4);
+    I.istat = ar.take_int(8);
     c2_max = std::max(c2_max, (size_t)c * c);
     K_max = std::max(K_max, I.K);
   }
@@ -1039,6 +1198,7 @@ void plan(ttn_ctx* h) {
     sweep_instance(h, I);
     adjoints_only(h, I, 0);
     energy_only(h, I, nullptr);
+    isometry_grams(h, I, nullptr);
   }
   h->measuring = false;
 }
@@ -1051,8 +1211,14 @@ void setup_schedules(ttn_ctx* h) {
   // mixed modes: two blocks -- one long composition for the growth of the
   // small singular values (its ~1e-8 loss of accuracy on those directions is
   // below the rounding of the tensor-core contractions around it), then a
-  // fresh Gram matrix for the well-conditioned convergence to an exact isometry
-  h->polar_tc = polar_schedule(l0, 1e5, 1e-15, 1000);
+  // fresh Gram matrix for the well-conditioned convergence to an exact
+  // isometry.  The tensor-core rounding of the environment (up to 1e-4 in
+  // TF32) can take singular values of the damped environment below mu |Gamma|
+  // (measured: the top isometry layer of the 64 x 4 torus in TF32, by small
+  // factors), so the schedule starts at min(mu / 4, 1e-10): six more steps,
+  // the same two Gram matrices (growth up to 1e6 per block, ~3e-9 relative
+  // in double-float arithmetic)
+  h->polar_tc = polar_schedule(std::min(l0, 1e-10), 1e6, 1e-15, 1000);
 }
 
 }  // namespace
@@ -1078,6 +1244,31 @@ void ttn_default_options(ttn_options* o) {
   o->streams = 8;
   o->polar_blocks = 0;
   o->double_float = 1;
+  o->tc_engine = 0;
+  o->wait_polls = 0;
+  o->tiles = nullptr;
+  o->tiles_bytes = 0;
+}
+
+// Parse an autotuner blob (ttn_options.tiles) into the table.
+static int load_tiles(ttn_ctx* h, const void* blob, size_t bytes) {
+  if (!blob || bytes == 0) return TTN_OK;
+  if (bytes < sizeof(TuneBlobHeader)) return fail(h, TTN_EINVAL, "tiles blob too short");
+  TuneBlobHeader hd;
+  std::memcpy(&hd, blob, sizeof(hd));
+  if (std::memcmp(hd.magic, "TTNT", 4) != 0 || hd.version != 1 ||
+      bytes < sizeof(hd) + (size_t)hd.count * sizeof(TuneBlobEntry))
+    return fail(h, TTN_EINVAL, "not a tiles blob of this library");
+  const char* p = static_cast<const char*>(blob) + sizeof(hd);
+  for (uint32_t i = 0; i < hd.count; ++i) {
+    TuneBlobEntry e;
+    std::memcpy(&e, p + i * sizeof(e), sizeof(e));
+    if (e.engine < 0 || e.engine > 1 || e.splits < 1 || e.splits > 64 ||
+        !(e.tile == 0 || e.tile == 16 || e.tile == 32 || e.tile == 64 || e.tile == 128))
+      return fail(h, TTN_EINVAL, "tiles blob entry out of range");
+    h->tuned[e.key] = Tuned{e.engine, e.tile, e.splits, e.ms};
+  }
+  return TTN_OK;
 }
 
 // Instances go to min(streams, instances) lanes, longest first onto the least
@@ -1116,8 +1307,14 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   if (h->opt.lanczos_max < 2 || h->opt.lanczos_max > 120) return fail(h, TTN_EINVAL, "lanczos_max in [2,120]");
   if (h->opt.lanczos_restarts < 1) h->opt.lanczos_restarts = 1;
   if (!(h->opt.polar_damping >= 0.0)) return fail(h, TTN_EINVAL, "polar_damping < 0");
+  if (h->opt.wait_polls < 0) return fail(h, TTN_EINVAL, "wait_polls < 0");
+  if (h->opt.tc_engine != 0 && h->opt.tc_engine != 1) return fail(h, TTN_EINVAL, "tc_engine is 0 or 1");
   h->lz_m = h->opt.lanczos_max;
-  int rc = build_instances(h, probs, n);
+  int rc = load_tiles(h, h->opt.tiles, h->opt.tiles_bytes);
+  if (rc) return rc;
+  h->opt.tiles = nullptr;   // copied: the caller's blob is not kept
+  h->opt.tiles_bytes = 0;
+  rc = build_instances(h, probs, n);
   if (rc) return rc;
   if (h->opt.streams < 1 || h->opt.streams > 64) return fail(h, TTN_EINVAL, "streams in [1,64]");
   if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 2)
@@ -1170,6 +1367,11 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
   }
   for (size_t k = 0; k < h->lanes.size() && !rc; ++k)
     rc = check_cuda(h, cudaMemsetAsync(h->lanes[k].iflags, 0, 8 * sizeof(int), h->stream), "flags");
+  for (size_t i = 0; i < h->inst.size() && !rc; ++i) {
+    rc = check_cuda(h, cudaMemsetAsync(h->inst[i].istat, 0, 8 * sizeof(int), h->stream), "status");
+    if (!rc)
+      rc = check_cuda(h, cudaMemsetAsync(h->inst[i].dstat, 0, 4 * sizeof(double), h->stream), "status");
+  }
   if (rc) { *out = h; return rc; }
   // upload operators of site layer 0 (shifted one-site term)
   for (Instance& I : h->inst) {
@@ -1241,6 +1443,9 @@ int ttn_set_isometries(ttn_t h, int inst, const double* w, const double* v) {
   int rc = check_cuda(h, cudaMemcpyAsync(I.V, v, c2 * sizeof(double), cudaMemcpyDefault,
                                          h->stream), "set v");
   if (rc) return rc;
+  // a new state: no previous energy to compare the next sweep with
+  rc = check_cuda(h, cudaMemsetAsync(I.istat, 0, 4 * sizeof(int), h->stream), "set status");
+  if (rc) return rc;
   return check_cuda(h, cudaStreamSynchronize(h->stream), "set sync");
 }
 
@@ -1288,15 +1493,52 @@ static void enqueue_sweep(ttn_ctx* h) {
   }
 }
 
-int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
-  if (!h || n_sweeps < 0) return TTN_EINVAL;
-  if (n_sweeps == 0) return TTN_OK;
-  sync_user(h);
+// Device status after work on the library's streams: a raised "bounded wait
+// expired" flag of any lane (cleared once read, so that the context stays
+// usable) and, with conv, whether every instance's last top solve converged.
+static int read_status(ttn_ctx* h, bool conv) {
+  const size_t nl = h->lanes.size(), ni = h->inst.size();
+  std::vector<int> flag(nl, 0), top(ni, 1), pol(ni, 0);
+  int rc = TTN_OK;
+  for (size_t k = 0; k < nl && !rc; ++k)
+    rc = check_cuda(h, cudaMemcpyAsync(&flag[k], h->lanes[k].iflags + 4, sizeof(int),
+                                       cudaMemcpyDeviceToHost, h->stream), "status");
+  for (size_t i = 0; i < ni && conv && !rc; ++i) {
+    rc = check_cuda(h, cudaMemcpyAsync(&top[i], h->inst[i].istat, sizeof(int),
+                                       cudaMemcpyDeviceToHost, h->stream), "status");
+    if (!rc)
+      rc = check_cuda(h, cudaMemcpyAsync(&pol[i], h->inst[i].istat + 4, sizeof(int),
+                                         cudaMemcpyDeviceToHost, h->stream), "status");
+  }
+  if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "status sync");
+  if (rc) return rc;
+  bool expired = false;
+  for (int f : flag) expired = expired || f != 0;
+  if (expired) {
+    for (size_t k = 0; k < nl; ++k) cudaMemsetAsync(h->lanes[k].iflags + 4, 0, sizeof(int), h->stream);
+    rc = check_cuda(h, cudaStreamSynchronize(h->stream), "status clear");
+    if (rc) return rc;
+    return fail(h, TTN_ETIMEOUT, "a bounded wait in a kernel expired (flag cleared)");
+  }
+  for (size_t i = 0; i < ni && conv; ++i) {
+    if (!top[i])
+      return fail(h, TTN_ENOCONV, "instance " + std::to_string(i) +
+                                      ": the last top solve missed its residual tolerance");
+    if (pol[i])
+      return fail(h, TTN_ENOCONV, "instance " + std::to_string(i) +
+                                      ": a polar factor of the last sweep missed an isometry");
+  }
+  return TTN_OK;
+}
+
+// Enqueue n_sweeps sweeps (graph replays, captured on first use) and, with
+// host_energy, copy every sweep's energies out (synchronising per chunk).
+static int launch_sweeps(ttn_ctx* h, int n_sweeps, double* host_energy) {
   const int ni = (int)h->inst.size();
   int rc = TTN_OK;
-  h->launches = 0;
   const bool graph = h->opt.use_graph != 0;
   if (graph && !h->exec) {
+    h->launches = 0;
     rc = check_cuda(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "capture");
     if (rc) return rc;
     enqueue_sweep(h);
@@ -1307,11 +1549,9 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
     if (rc) return rc;
     h->launches_per_sweep = h->launches;
   }
-  h->launches = 0;
-  std::vector<double> buf;
   int done = 0;
   while (done < n_sweeps) {
-    const int chunk = std::min(n_sweeps - done, 4096 / 1);
+    const int chunk = std::min(n_sweeps - done, 4096);
     for (int s = 0; s < chunk; ++s) {
       if (graph) {
         rc = check_cuda(h, cudaGraphLaunch(h->exec, h->stream), "graph launch");
@@ -1337,27 +1577,128 @@ int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
     done += chunk;
   }
   h->sweeps_done += n_sweeps;
-  // make the user's stream wait for the sweeps
+  return check_cuda(h, cudaGetLastError(), "sweep");
+}
+
+// The user's stream waits for the library's work.
+static void fence_user(ttn_ctx* h) {
   cudaEvent_t ev;
   cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   cudaEventRecord(ev, h->stream);
   cudaStreamWaitEvent(h->user, ev, 0);
   cudaEventDestroy(ev);
-  rc = check_cuda(h, cudaGetLastError(), "sweep");
+}
+
+int ttn_sweep(ttn_t h, int n_sweeps, double* host_energy) {
+  if (!h || n_sweeps < 0) return TTN_EINVAL;
+  if (n_sweeps == 0) return TTN_OK;
+  sync_user(h);
+  h->launches = 0;
+  int rc = launch_sweeps(h, n_sweeps, host_energy);
+  fence_user(h);
   if (rc) return rc;
-  if (host_energy) {
-    std::vector<int> flag(h->lanes.size(), 0);
-    for (size_t k = 0; k < h->lanes.size(); ++k)
-      cudaMemcpyAsync(&flag[k], h->lanes[k].iflags + 4, sizeof(int), cudaMemcpyDeviceToHost,
-                      h->stream);
-    rc = check_cuda(h, cudaStreamSynchronize(h->stream), "flag sync");
-    if (rc) return rc;
-    for (int f : flag)
-      if (f) return fail(h, TTN_ETIMEOUT, "a bounded wait in a kernel expired");
-  }
+  // expired waits first (the state is then unspecified), then the energies,
+  // then the convergence of the last top solves
+  rc = read_status(h, false);
+  if (rc) return rc;
   if (host_energy)
-    for (int i = 0; i < n_sweeps * ni; ++i)
+    for (int i = 0; i < n_sweeps * (int)h->inst.size(); ++i)
       if (!std::isfinite(host_energy[i])) return fail(h, TTN_ENAN, "non-finite energy");
+  return read_status(h, true);
+}
+
+int ttn_sweep_until(ttn_t h, double tol, int max_sweeps, int* n_done, double* host_energy) {
+  if (n_done) *n_done = 0;
+  if (!h || !(tol > 0.0) || max_sweeps < 1) return TTN_EINVAL;
+  sync_user(h);
+  h->launches = 0;
+  const int ni = (int)h->inst.size();
+  int rc = TTN_OK;
+  // the tolerance, and no previous energy: the first sweep of the call never counts
+  for (int i = 0; i < ni && !rc; ++i) {
+    rc = check_cuda(h, cudaMemcpyAsync(h->inst[i].dstat + 2, &tol, sizeof(double),
+                                       cudaMemcpyHostToDevice, h->stream), "tolerance");
+    if (!rc)
+      rc = check_cuda(h, cudaMemsetAsync(h->inst[i].istat + 2, 0, 2 * sizeof(int), h->stream),
+                      "status");
+  }
+  if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "tolerance sync");
+  if (rc) return rc;
+  std::vector<int> conv(ni, 0);
+  int done = 0;
+  bool all = false;
+  while (done < max_sweeps && !all) {
+    const int chunk = std::min(8, max_sweeps - done);
+    rc = launch_sweeps(h, chunk, host_energy ? host_energy + (size_t)done * ni : nullptr);
+    if (rc) break;
+    for (int i = 0; i < ni && !rc; ++i)
+      rc = check_cuda(h, cudaMemcpyAsync(&conv[i], h->inst[i].istat + 2, sizeof(int),
+                                         cudaMemcpyDeviceToHost, h->stream), "convergence");
+    if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "convergence sync");
+    if (rc) break;
+    done += chunk;
+    all = true;
+    for (int c : conv) all = all && c != 0;
+  }
+  fence_user(h);
+  if (n_done) *n_done = done;
+  if (rc) return rc;
+  rc = read_status(h, false);
+  if (rc) return rc;
+  if (host_energy)
+    for (int i = 0; i < done * ni; ++i)
+      if (!std::isfinite(host_energy[i])) return fail(h, TTN_ENAN, "non-finite energy");
+  if (!all)
+    return fail(h, TTN_ENOCONV, "the energy change per spin stayed above the tolerance for " +
+                                    std::to_string(max_sweeps) + " sweeps");
+  return TTN_OK;
+}
+
+int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
+  if (!h || !out || n_out < 7 || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
+  sync_user(h);
+  Instance& I = h->inst[inst];
+  const int T = I.T;
+  // results in the (idle) Lanczos basis: 3 per site layer (traces of R,
+  // max |R|, asymmetry), 3 per isometry layer, then <v, v>
+  double* res = h->lz_basis;
+  adjoints_only(h, I, 0);
+  for (int t = 0; t <= T; ++t) {
+    const int n = I.chis[t];
+    h->launches += mat_stats(I.adj[t], n, I.sites(t), (ll)(1 + 2 * I.K) * n * n, 0,
+                             res + 3 * t, h->stream);
+  }
+  isometry_grams(h, I, res + 3 * (T + 1));
+  const ll c2 = (ll)I.chis[T] * I.chis[T];
+  h->launches += batched_dot(I.V, I.V, c2, 0, 1, res + 3 * (2 * T + 1), h->red, h->stream);
+  std::vector<double> r(3 * (2 * T + 1) + 1);
+  double dst[4];
+  int ist[8];
+  int rc = check_cuda(h, cudaMemcpyAsync(r.data(), res, r.size() * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream), "diagnostics");
+  if (!rc) rc = check_cuda(h, cudaMemcpyAsync(dst, I.dstat, sizeof(dst), cudaMemcpyDeviceToHost,
+                                              h->stream), "diagnostics");
+  if (!rc) rc = check_cuda(h, cudaMemcpyAsync(ist, I.istat, sizeof(ist), cudaMemcpyDeviceToHost,
+                                              h->stream), "diagnostics");
+  if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
+  if (rc) return rc;
+  rc = read_status(h, false);
+  if (rc) return rc;
+  double defect = 0.0, trace_err = 0.0, asym = 0.0;
+  for (int t = 0; t <= T; ++t) {
+    const double N = (double)(I.L >> t);
+    trace_err = std::max(trace_err, std::fabs(r[3 * t] - N) / N);
+    asym = std::max(asym, r[3 * t + 2] / N);
+  }
+  for (int t = 0; t < T; ++t) defect = std::max(defect, r[3 * (T + 1) + 3 * t + 1]);
+  out[0] = defect;
+  out[1] = trace_err;
+  out[2] = asym;
+  out[3] = std::fabs(r[3 * (2 * T + 1)] - 1.0);
+  out[4] = ist[3] >= 2 ? dst[1] : NAN;
+  out[5] = ist[0] ? 1.0 : 0.0;
+  out[6] = ist[1];
+  if (n_out >= 8) out[7] = ist[4] ? 1.0 : 0.0;
   return TTN_OK;
 }
 
@@ -1381,6 +1722,8 @@ int ttn_ascend(ttn_t h, int inst, int site_layer, int prec, double* host_out) {
   if (rc) return rc;
   rc = check_cuda(h, cudaStreamSynchronize(h->stream), "ascend sync");
   if (rc) return rc;
+  rc = read_status(h, false);
+  if (rc) return rc;
   const int n = I.chis[site_layer];
   const size_t ss = (size_t)(1 + 2 * I.K) * n * n;
   for (size_t j = 0; j < e.size(); ++j)
@@ -1397,7 +1740,8 @@ int ttn_energy(ttn_t h, int inst, double* E) {
   int rc = check_cuda(h, cudaMemcpyAsync(E, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost,
                                          h->stream), "energy");
   if (rc) return rc;
-  return check_cuda(h, cudaStreamSynchronize(h->stream), "energy sync");
+  rc = check_cuda(h, cudaStreamSynchronize(h->stream), "energy sync");
+  return rc ? rc : read_status(h, false);
 }
 
 int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
@@ -1416,6 +1760,8 @@ int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
                                            cudaMemcpyDeviceToHost, h->stream), "rdm");
     if (rc) return rc;
     rc = check_cuda(h, cudaStreamSynchronize(h->stream), "rdm sync");
+    if (rc) return rc;
+    rc = read_status(h, false);
     if (rc) return rc;
     const size_t ss = (1 + 2 * I.K) * n2;
     if (which == 1) {
@@ -1448,7 +1794,8 @@ int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
   }
   int rc = check_cuda(h, cudaMemcpyAsync(out, rho, n2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "rdm");
   if (rc) return rc;
-  return check_cuda(h, cudaStreamSynchronize(h->stream), "rdm sync");
+  rc = check_cuda(h, cudaStreamSynchronize(h->stream), "rdm sync");
+  return rc ? rc : read_status(h, false);
 }
 
 int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
@@ -1463,7 +1810,8 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
     forward(h, I, 0);
     top_matvec(h, I, I.V, h->lz_w, nullptr);
     h->launches += top_grad(d_out, h->lz_w, I.V, c2, I.eoff[I.T], I.per_node ? 1 : 0, h->stream);
-    return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+    const int rc_sync = check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+    return rc_sync ? rc_sync : read_status(h, false);
   }
   adjoints_only(h, I, layer < 0 ? 0 : layer + 1);
   if (layer >= 0) {
@@ -1471,7 +1819,8 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
     int rc = check_cuda(h, cudaMemcpyAsync(d_out, h->Gam, I.w_elems(layer) * sizeof(double),
                                            cudaMemcpyDeviceToDevice, h->stream), "env");
     if (rc) return rc;
-    return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+    const int rc_sync = check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+    return rc_sync ? rc_sync : read_status(h, false);
   }
   // all layers, concatenated as ttn_set_isometries lays them out, then the top
   size_t off = 0;
@@ -1485,7 +1834,8 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
   top_matvec(h, I, I.V, h->lz_w, nullptr);
   h->launches += top_grad(d_out + off, h->lz_w, I.V, c2, I.eoff[I.T], I.per_node ? 1 : 0,
                           h->stream);
-  return check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+  const int rc_end = check_cuda(h, cudaStreamSynchronize(h->stream), "env sync");
+  return rc_end ? rc_end : read_status(h, false);
 }
 
 int ttn_get_state(ttn_t h, void* buf, size_t* bytes) {
@@ -1583,7 +1933,58 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
     out[7] += cnt[2] + cnt[3];
   }
   h->sweeps_done += 1;
-  return rc;
+  return rc ? rc : read_status(h, false);
+}
+
+int ttn_autotune(ttn_t h, int reps, void* blob, size_t* blob_bytes) {
+  if (!h || reps < 0) return TTN_EINVAL;
+  int rc = TTN_OK;
+  if (reps > 0) {
+    sync_user(h);
+    h->tuned.clear();
+    h->tuning = true;
+    h->tune_reps = reps;
+    h->profiling = true;   // one stream, no capture, like the profiling sweep
+    h->launches = 0;
+    enqueue_sweep(h);
+    h->profiling = false;
+    h->tuning = false;
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    h->ev_flops.clear();
+    rc = check_cuda(h, cudaStreamSynchronize(h->stream), "autotune sync");
+    if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
+    if (!rc) rc = read_status(h, false);
+    h->sweeps_done += 1;
+    fence_user(h);
+    // the captured sweep used the previous configurations: capture again
+    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    if (rc) return rc;
+  }
+  if (blob_bytes) {
+    const size_t need = sizeof(TuneBlobHeader) + h->tuned.size() * sizeof(TuneBlobEntry);
+    if (!blob) {
+      *blob_bytes = need;
+      return TTN_OK;
+    }
+    if (*blob_bytes < need) return fail(h, TTN_EINVAL, "tiles buffer too small");
+    TuneBlobHeader hd;
+    std::memcpy(hd.magic, "TTNT", 4);
+    hd.version = 1;
+    hd.count = (uint32_t)h->tuned.size();
+    hd.reserved = 0;
+    char* p = static_cast<char*>(blob);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    for (const auto& kv : h->tuned) {
+      TuneBlobEntry e{kv.first, kv.second.engine, kv.second.tile, kv.second.splits, kv.second.ms};
+      std::memcpy(p, &e, sizeof(e));
+      p += sizeof(e);
+    }
+    *blob_bytes = need;
+  }
+  return TTN_OK;
 }
 
 const char* ttn_last_error(ttn_t h) { return h ? h->err.c_str() : "null handle"; }

@@ -119,3 +119,34 @@ def test_default_options_match_the_header(lib):
     assert (opt.lanczos_max, opt.lanczos_restarts) == (48, 3)
     assert (opt.persistent, opt.streams, opt.polar_blocks, opt.double_float) == (3, 8, 0, 1)
     assert opt.polar_damping == 1e-7
+
+
+def test_tiles_blob_is_validated_at_planning(lib):
+    """ttn_options.tiles (the autotuner's table) is parsed before the plan
+    pass: a foreign or damaged blob is rejected, an empty table accepted."""
+    import struct
+    import numpy as np
+    from paper_1905_01331_gb300 import _abi
+    import ttn_inputs as ti
+    m = ti.tfim_chain(64, 1.0)
+    o, A, B = (np.ascontiguousarray(x) for x in (m.o, m.A, m.B))
+    dp = ctypes.POINTER(ctypes.c_double)
+    p = _abi.Problem(64, 1, 2, 16, 1, 0, o.ctypes.data_as(dp), A.ctypes.data_as(dp),
+                     B.ctypes.data_as(dp))
+
+    def size_with(blob):
+        opt = _abi.Options()
+        lib.ttn_default_options(ctypes.byref(opt))
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        opt.tiles = ctypes.cast(buf, ctypes.c_void_p)
+        opt.tiles_bytes = len(blob)
+        return lib.ttn_workspace_bytes(ctypes.byref(p), 1, ctypes.byref(opt))
+
+    empty = b"TTNT" + struct.pack("<III", 1, 0, 0)
+    assert size_with(empty) > 0
+    assert size_with(b"garbage-garbage-garbage") == 0
+    entry = struct.pack("<QiiIf", 123, 0, 48, 4, 1.0)             # tile 48: not a tile width
+    assert size_with(b"TTNT" + struct.pack("<III", 1, 1, 0) + entry) == 0
+    entry = struct.pack("<Qiiif", 123, 1, 64, 2, 1.0)
+    assert size_with(b"TTNT" + struct.pack("<III", 1, 1, 0) + entry) > 0
+    assert size_with(b"TTNT" + struct.pack("<III", 1, 2, 0) + entry) == 0   # truncated

@@ -16,7 +16,7 @@ def test_split_and_to_f32_match_casts(tmp_path):
     if gxx is None:
         pytest.skip("g++ not available")
     exe = str(tmp_path / "f64_bits_driver")
-    subprocess.run([gxx, "-O2", "-std=c++17", "-o", exe, os.path.join(HERE, "f64_bits_driver.cpp")],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe, os.path.join(HERE, "f64_bits_driver.cpp")],
                    check=True)
     out = subprocess.run([exe, "2000000"], capture_output=True, text=True, check=True).stdout.split()
     bad, cases = int(out[0]), int(out[1])

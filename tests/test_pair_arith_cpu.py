@@ -20,7 +20,7 @@ def test_pair_dot_products_keep_about_48_bits(tmp_path):
     if gxx is None:
         pytest.skip("g++ not available")
     exe = str(tmp_path / "pair_arith_driver")
-    subprocess.run([gxx, "-O2", "-std=c++17", "-o", exe, os.path.join(HERE, "pair_arith_driver.cpp")],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe, os.path.join(HERE, "pair_arith_driver.cpp")],
                    check=True)
     out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
     rows = [line.split() for line in out if line.strip()]

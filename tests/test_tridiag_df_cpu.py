@@ -21,7 +21,7 @@ def driver(tmp_path_factory):
     if gxx is None:
         pytest.skip("g++ not available")
     exe = str(tmp_path_factory.mktemp("tdf") / "tridiag_df_driver")
-    subprocess.run([gxx, "-O2", "-std=c++17", "-o", exe, os.path.join(HERE, "tridiag_df_driver.cpp")],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe, os.path.join(HERE, "tridiag_df_driver.cpp")],
                    check=True)
     return exe
 
