@@ -34,12 +34,12 @@ WORKLOAD = {"workload": "tfim_chain_L1024_h1_chi128", "L": 1024, "h": 1.0, "chi"
             "seed": 1, "model": "transverse-field Ising chain, periodic",
             "tree": "binary TTN, one isometry per layer"}
 METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
-# DRAM bytes (read + write) per launch of a kernel family, averaged over one
-# sweep's launches of it (third sweep from the seeded start), from the ncu
-# captures summarised in profiles/gemm_df_kernel_tfim_L1024_chi128.md and
-# profiles/gemm_tc_kernel_tfim_L1024_chi128_tf32x3.md (None for a family
-# without one)
-TRAFFIC = {"df": 14.52e6, "tc": 15.74e6}
+# DRAM bytes (read + write) per launch of a kernel family, averaged over the
+# launches of one sweep (third sweep from the seeded start), from an ncu
+# capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum);
+# a family without a capture of its current kernel has none.  This is a
+# stored measurement, labelled as such in the line.
+TRAFFIC = {}
 
 
 def parse():
@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--prec", default=os.environ.get("TTN_BENCH_PREC", "tf32x3"))
     p.add_argument("--chi", type=int, default=128)
     p.add_argument("--no-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the launchers' default tiles")
+    p.add_argument("--cpu-1thread", action="store_true",
+                   help="also time the oracle with one BLAS thread (minutes at chi=128)")
     p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
@@ -155,6 +158,46 @@ def oracle_sweeps_per_s(n_sweeps: int, warm: int, chi: int):
     return n_sweeps / dt, dt
 
 
+def cpu_model():
+    """The host CPU's model string (lscpu), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_timing(chi, threads, warm=2, timed=3, timeout=900):
+    """Seconds of each of `timed` oracle sweeps of the headline workload after
+    `warm` warm-up sweeps from the seeded start, in a fresh process with the
+    BLAS limited to `threads` threads (None when it fails or runs out of time)."""
+    code = ("import json, time, ttn_inputs as ti\n"
+            "from oracle import ttn as oracle\n"
+            "m = ti.tfim_chain(1024, 1.0)\n"
+            f"ws, V = ti.initial_tensors(1024, 2, {chi}, 1)\n"
+            "st = oracle.make_state(m, ws, V)\n"
+            f"for _ in range({warm}): oracle.sweep(st)\n"
+            "ts = []\n"
+            f"for _ in range({timed}):\n"
+            "    t0 = time.perf_counter(); oracle.sweep(st); ts.append(time.perf_counter() - t0)\n"
+            "print(json.dumps(ts))\n")
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                             text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return None
+    if out.returncode != 0:
+        return None
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def threads_used():
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         if os.environ.get(k):
@@ -168,13 +211,16 @@ def run_reference(args):
         return
     # each step is one full oracle sweep of the workload
     v, dt = oracle_sweeps_per_s(args.steps, args.warmup, args.chi)
+    cores = threads_used()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded QR-orthonormalised Gaussian isometries)",
             "config": dict(WORKLOAD, precision="fp64", engine="numpy/LAPACK oracle"),
-            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": threads_used(), "kind": "oracle",
-                             "sample": f"{args.steps} full sweeps after {args.warmup} warm-up sweeps"},
+            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"{args.steps} full sweeps after {args.warmup} warm-up sweeps "
+                                       f"of the same workload, BLAS threads {cores}"},
             "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -221,7 +267,11 @@ def run_gpu(args):
     chis = s.chis(0)
     flops_per_sweep = ttn_flops.sweep_flops(1024, chis, 1, symmetric=True)
 
-    # warm-up (also builds the CUDA graph)
+    # warm-up: the autotuner's sweep (tile widths, engines, split counts of
+    # every product shape, timed), then the warm-up sweeps (graph capture)
+    tune_t0 = time.perf_counter()
+    tiles_blob = s.autotune(reps=3) if not args.no_autotune else b""
+    tune_s = time.perf_counter() - tune_t0
     s.sweep(args.warmup)
     stream = s.stream
     torch.cuda.synchronize()
@@ -292,7 +342,16 @@ def run_gpu(args):
     except Exception:
         pass
     sm_count, sm_ghz = 152, peaks.get("sm_max_mhz", 2070.0) * 1e-3
+    hbm = peaks.get("hbm_gbs", 6789.3)
     families = {
+        # the same tcgen05 products against HBM bandwidth: their algorithmic
+        # bytes (every operand read once, the output written once) over the
+        # same time; most are below the ridge of 3xTF32 (~47 flop/B)
+        "tc_hbm": {"bound": "hbm", "kernel": "gemm_tma_kernel / gemm_tc_kernel (tcgen05 grouped "
+                                             "products), algorithmic bytes",
+                   "ms": prof["tc_ms"], "achieved_units": prof.get("tc_bytes", 0.0) * 1e3,
+                   "launches": prof["tc_launches"], "peak": hbm, "unit": "GB/s",
+                   "peak_source": "MEASURED_PEAKS hbm_gbs (copy bandwidth)"},
         # tcgen05 products: algorithmic flops against the TF32 dense peak
         "tc": {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05 grouped products)",
                "ms": prof["tc_ms"], "achieved_units": prof["tc_flops"], "launches": prof["tc_launches"],
@@ -325,11 +384,16 @@ def run_gpu(args):
     for k, f in families.items():
         ach = f["achieved_units"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] > 0 else 0.0
         fam[k] = {"bound": f["bound"], "kernel": f["kernel"], "achieved": ach, "peak": f["peak"],
-                  "unit": "TFLOP/s", "frac": ach / f["peak"], "peak_source": f["peak_source"],
+                  "unit": f.get("unit", "TFLOP/s"), "frac": ach / f["peak"],
+                  "peak_source": f["peak_source"],
                   "launches_per_sweep": f["launches"], "ms_per_sweep": f["ms"],
                   "share_of_sweep": f["ms"] / prof["total_ms"]}
-    dom = max(fam, key=lambda k: fam[k]["ms_per_sweep"])
+    dom = max((k for k in fam if k != "tc_hbm"), key=lambda k: fam[k]["ms_per_sweep"])
+    if dom == "tc" and fam["tc_hbm"]["frac"] > fam["tc"]["frac"]:
+        dom = "tc_hbm"   # the products are bandwidth-bound: report that roofline
     roofline = dict(fam[dom], traffic=TRAFFIC.get(dom))
+    if TRAFFIC.get(dom) is not None:
+        roofline["traffic_source"] = "stored ncu capture of the current kernel (third sweep)"
 
     out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -342,6 +406,8 @@ def run_gpu(args):
            "tflops": flops_per_sweep * value / world / 1e12,
            "algorithmic_flops_per_sweep": flops_per_sweep,
            "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "roofline": roofline,
+           "autotune": {"seconds": tune_s, "table_bytes": len(tiles_blob),
+                        "product_shapes": max(0, (len(tiles_blob) - 16) // 32)},
            "roofline_families": fam,
            "profile": prof}
 
@@ -374,7 +440,7 @@ def run_gpu(args):
                   "fp64": {"sweeps": 200, "seconds": t_f, "E_fp64": E_ref,
                            "rel_err_vs_oracle_200": abs(E_ref - oracle_E) / abs(oracle_E) if oracle_E else None}}
         if args.prec != "fp64":
-            g = Sweeper(model, chi, prec=args.prec)
+            g = Sweeper(model, chi, prec=args.prec, tiles=tiles_blob or None)
             g.set_isometries(0, ws, V)
             g.sweep(1)
             done, secs, reached, E200 = 1, 0.0, None, None
@@ -397,10 +463,25 @@ def run_gpu(args):
         out["energy"] = energy
 
     if rank == 0 and not args.no_baseline and world == 1:
-        n = 1 if chi >= 128 else 3
-        v, dt = oracle_sweeps_per_s(n, 0, chi)
-        out["cpu_baseline"] = {"value": v, "unit": "sweeps/s", "cores": threads_used(), "kind": "oracle",
-                               "sample": f"{n} full oracle sweep(s) of the same workload from the seeded start"}
+        # the oracle on this host, the same way as the benchmark's plan: 2
+        # warm-up sweeps from the seeded start, then the median of 3 timed
+        # sweeps, in a fresh process with the BLAS on all cores (and, with
+        # --cpu-1thread, on one)
+        ncores = os.cpu_count()
+        ts = oracle_timing(chi, ncores)
+        if ts:
+            med = statistics.median(ts)
+            out["cpu_baseline"] = {"value": 1.0 / med, "unit": "sweeps/s", "cores": ncores,
+                                   "kind": "oracle", "cpu_model": cpu_model(),
+                                   "sample": "median of 3 full oracle sweeps of the same workload "
+                                             "after 2 warm-up sweeps from the seeded start "
+                                             f"(BLAS threads {ncores}; seconds {ts})"}
+        if args.cpu_1thread:
+            t1 = oracle_timing(chi, 1, timeout=1800)
+            if t1:
+                out["cpu_baseline_1thread"] = {"value": 1.0 / statistics.median(t1),
+                                               "unit": "sweeps/s", "cores": 1,
+                                               "seconds": t1}
     s.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -465,17 +546,19 @@ def run_paper_torus(args):
     s = Sweeper(m, chi, prec=args.prec)
     s.set_isometries(0, ws, V)
     t0 = time.perf_counter()
-    E = s.sweep(args.steps)[:, 0]
+    # Sec. IV: sweep until the energy per spin changes by less than 1e-10
+    converged, E = s.sweep_until(tol=1e-10, max_sweeps=args.steps)
+    E = E[:, 0]
     dt = time.perf_counter() - t0
     E_cert = s.energy(0)
     rho = s.rdm(0, 6, which=1)
     p = np.clip(np.linalg.eigvalsh(0.5 * (rho + rho.T))[::-1], 1e-300, None)
     lam = -np.log2(p)
     S = float(-np.sum(p * np.log2(p)))
-    marks = sorted({k for k in (1, 10, 50, 100, 200, 500, 1000, 2000, 5000) if k <= args.steps}
-                   | {args.steps})
+    n = len(E)
+    marks = sorted({k for k in (1, 10, 50, 100, 200, 500, 1000, 2000, 5000) if k <= n} | {n})
     print(json.dumps({"workload": "paper torus 128x5 h=2.9", "chi": chi, "precision": args.prec,
-                      "sweeps": args.steps, "sweeps_per_s": args.steps / dt,
+                      "sweeps": n, "converged_1e-10": bool(converged), "sweeps_per_s": n / dt,
                       "energy_per_spin_fp64": E_cert / m.n_spins,
                       "energy_per_spin_at_sweep": {str(k): float(E[k - 1] / m.n_spins) for k in marks},
                       "last_delta_e_per_spin": float(abs(E[-1] - E[-2]) / m.n_spins)

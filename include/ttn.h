@@ -119,6 +119,13 @@ typedef struct {
                                kernels before it expires and the sweep reports
                                TTN_ETIMEOUT (0, the default: 2^21 polls, about
                                one second) */
+  int recompute_ops;        /* 1: keep the ascended operators of site layers
+                               1..T-1 in two shared buffers and recompute them
+                               (ascending from the bottom through the current
+                               isometries) whenever the descent needs them:
+                               (T-3) fewer operator buffers in the workspace for
+                               O(T^2) instead of O(T) ascend steps per sweep or
+                               gradient; 0 (default): store every layer's */
   const void* tiles;        /* autotuner blob from ttn_autotune (NULL: the
                                launchers' default tile widths and split counts);
                                copied by ttn_create */
@@ -211,6 +218,17 @@ int ttn_ascend(ttn_t h, int inst, int site_layer, int prec, double* host_out);
  * top contraction, no re-optimisation). */
 int ttn_energy(ttn_t h, int inst, double* E_total);
 
+/* Energy of one instance's current tensors and, with d_grad != NULL, its
+ * derivative with respect to every isometry and the top tensor (the
+ * environments of Sec. III.A, laid out as ttn_env with layer -1; caller device
+ * memory, FP64), in one pass: ascend, top contraction, then the environment of
+ * every layer top-down while descending the density matrices (no update).  The
+ * ascend, environment and descend contractions run in precision prec (0..4;
+ * a mixed precision needs a context created with a mixed precision), the top
+ * contraction and the energy in FP64.  This is the forward and backward of the
+ * energy as a differentiable function. */
+int ttn_value_and_grad(ttn_t h, int inst, int prec, double* E_total, double* d_grad);
+
 /* Reduced density matrix on one site of site layer `site_layer` (0..T) of the
  * current tensors, chi_t x chi_t, to host (Sec. IV.B).  which = 0: average
  * over the sites of that layer (R / N_t); which = 1: the leftmost site. */
@@ -241,7 +259,10 @@ long long ttn_launch_count(ttn_t h);
  * n_out >= 15, out[9..11] = the same three for the double-float Gram and
  * apply products and out[12..14] for the double-float polar composition;
  * with 12 <= n_out < 15, out[9..11] = both together; with fewer they count as
- * "other".  The sweep updates the tensors like ttn_sweep.  n_out >= 9. */
+ * "other"; with n_out >= 17, out[15] and out[16] = the algorithmic bytes of
+ * the FP64-engine and tensor-core products (every group's operands read once,
+ * a batch index of stride 0 read once, the output written once).  The sweep
+ * updates the tensors like ttn_sweep.  n_out >= 9. */
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
@@ -287,7 +308,8 @@ int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, int Q, long l
  * layouts; not its addresses), every candidate configuration is timed with
  * CUDA events over `reps` launches after one warm-up launch: for tensor-core
  * products the engine (TMA-fed where eligible, thread-staged), its tile width
- * BN and the split count of K; for FP64 products the tile (16, 32, 64) and
+ * BN, the TMA-fed kernel's stage ring (192 KB, one CTA per SM, or 96 KB, two)
+ * and the split count of K; for FP64 products the tile (16, 32, 64) and
  * the split count; the split counts are limited to the context's split-K
  * buffer.  The fastest becomes the product's configuration (the next
  * ttn_sweep captures its graph again).  The sweep updates the tensors like

@@ -39,7 +39,7 @@ class Sweeper:
                  lanczos_tol=0.0, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
                  persistent=True, streams=8, polar_blocks=0, double_float=True, wait_polls=0,
-                 tc_engine=0, tiles=None):
+                 tc_engine=0, tiles=None, recompute_ops=False):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -75,6 +75,7 @@ class Sweeper:
         opt.top_mode = int(top_mode)
         opt.wait_polls = int(wait_polls)
         opt.tc_engine = int(tc_engine)
+        opt.recompute_ops = int(bool(recompute_ops))
         if tiles:
             self._tiles = ctypes.create_string_buffer(bytes(tiles), len(tiles))
             opt.tiles = ctypes.cast(self._tiles, ctypes.c_void_p)
@@ -231,11 +232,11 @@ class Sweeper:
 
     def profile_sweep(self):
         """One eagerly launched sweep with every product timed by CUDA events."""
-        out = np.zeros(15)
-        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 15), "profile_sweep")
+        out = np.zeros(17)
+        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 17), "profile_sweep")
         keys = ["fp64_ms", "fp64_flops", "fp64_launches", "tc_ms", "tc_flops", "tc_launches",
                 "other_ms", "other_launches", "total_ms", "df_ms", "df_flops", "df_launches",
-                "dfc_ms", "dfc_flops", "dfc_launches"]
+                "dfc_ms", "dfc_flops", "dfc_launches", "fp64_bytes", "tc_bytes"]
         return dict(zip(keys, out.tolist()))
 
     @property

@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int),
                 ("double_float", ctypes.c_int), ("tc_engine", ctypes.c_int),
-                ("wait_polls", ctypes.c_int), ("tiles", ctypes.c_void_p),
+                ("wait_polls", ctypes.c_int), ("recompute_ops", ctypes.c_int),
+                ("tiles", ctypes.c_void_p),
                 ("tiles_bytes", ctypes.c_size_t)]
 
 
@@ -50,6 +51,8 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int), _dp]),
     "ttn_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int]),
     "ttn_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "ttn_value_and_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp,
+                                          ctypes.c_void_p]),
     "ttn_ascend": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "ttn_rdm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "ttn_env": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),

@@ -50,6 +50,8 @@ struct GemmDesc {
   int tile;          // tile width chosen by the autotuner (0: the launcher's
                      // default): BN of a tensor-core kernel, the square tile of
                      // the FP64 engine
+  int occ;           // TMA-fed kernel: 2 = the 96 KB stage ring (two CTAs per
+                     // SM), else the 192 KB ring (one CTA per SM)
 };
 // passed by value as a kernel parameter (limit 32764 bytes)
 static_assert(sizeof(GemmDesc) + 64 < 32764, "GemmDesc too large for a kernel parameter");

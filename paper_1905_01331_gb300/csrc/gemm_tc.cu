@@ -691,7 +691,8 @@ int tc_total_tiles(const GemmDesc& d, int BK);
 
 constexpr int kTThreads = 192;
 constexpr int kTConv = 128;
-constexpr int kTSmem = 196608;           // bytes of the stage ring
+constexpr int kTSmem = 196608;           // bytes of the stage ring, one CTA per SM
+constexpr int kTSmem2 = 98304;           // two CTAs per SM
 
 struct TmaParams {
   CUtensorMap a[kMaxGroups];
@@ -857,14 +858,14 @@ __device__ __forceinline__ void store_row16(const GemmDesc& d, int b, int b0, in
     if (n + j < d.N) store_out(d, cb + static_cast<long long>(n + j) * d.sc_n, __uint_as_float(r[j]), af, bf);
 }
 
-template <bool kSplit, int BN>
-__global__ void __launch_bounds__(kTThreads, 1)
+template <bool kSplit, int BN, int kRing>
+__global__ void __launch_bounds__(kTThreads, kRing == kTSmem ? 1 : 2)
     gemm_tma_kernel(const GemmDesc d, const __grid_constant__ TmaParams tp) {
   constexpr int kA = kBM * 128;                     // raw A tile: 128 rows x 32 FP32
   constexpr int kB = BN * 128;
   constexpr int kHi = kA + kB;                      // raw tiles, TF32 heads after conversion
   constexpr int kStageBytes = (kSplit ? 2 : 1) * kHi;
-  constexpr int S = kTSmem / kStageBytes < 8 ? kTSmem / kStageBytes : 8;
+  constexpr int S = kRing / kStageBytes < 8 ? kRing / kStageBytes : 8;
   constexpr uint32_t kIdesc = instr_desc(2u, kBM, BN);
   static_assert(S >= 2, "stage ring");
   static_assert(BN == 64 || BN == 128, "tile width");
@@ -916,6 +917,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
   if (warp == 0) {
     if (lane == 0 && nk > 0) {
       // ---- TMA producer ----
+      for (int g = 0; g < d.ngroups; ++g) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tp.a[g])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tp.b[g])) : "memory");
+      }
       int kt = 0, t_global = 0;
       bool ok = true;
       for (int g = 0; g < d.ngroups && t_global < t_hi && ok; ++g) {
@@ -1056,10 +1061,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
-template <bool kSplit, int BN>
+template <bool kSplit, int BN, int kRing>
 void tma_configure() {
-  cudaFuncSetAttribute(gemm_tma_kernel<kSplit, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kTSmem + 1024);
+  cudaFuncSetAttribute(gemm_tma_kernel<kSplit, BN, kRing>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRing + 1024);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -1149,7 +1154,7 @@ bool encode_operand(const Operand& o, int k0_log2, int K, int rows, int B0, int 
 
 // Returns 1 (launched) or 0 (a tensor map could not be encoded: the caller
 // runs the thread-staged kernel instead).
-template <bool kSplit, int BN>
+template <bool kSplit, int BN, int kRing>
 int launch_tma(const GemmDesc& d, cudaStream_t s) {
   static TmaParams tp;   // host staging of the kernel parameter (launch copies it)
   static std::mutex mu;
@@ -1166,15 +1171,22 @@ int launch_tma(const GemmDesc& d, cudaStream_t s) {
   tp.err = d.err;
   const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
   dim3 grid(tiles, d.B0 * d.B1, d.splits);
-  gemm_tma_kernel<kSplit, BN><<<grid, kTThreads, kTSmem + 1024, s>>>(d, tp);
+  gemm_tma_kernel<kSplit, BN, kRing><<<grid, kTThreads, kRing + 1024, s>>>(d, tp);
   return 1;
 }
 
+// d.occ == 2 selects the 96 KB ring (two CTAs per SM) where a stage still
+// fits twice: BN = 64 in both forms, BN = 128 without the split.
 int launch_tma_bn(const GemmDesc& d, cudaStream_t s) {
   const bool split = d.prec == 2;
   const int bn = (d.tile == 64 || d.tile == 128) ? d.tile : tma_bn(d.N);
-  if (bn == 128) return split ? launch_tma<true, 128>(d, s) : launch_tma<false, 128>(d, s);
-  return split ? launch_tma<true, 64>(d, s) : launch_tma<false, 64>(d, s);
+  const bool two = d.occ == 2 && !(split && bn == 128);
+  if (bn == 128) {
+    if (split) return launch_tma<true, 128, kTSmem>(d, s);
+    return two ? launch_tma<false, 128, kTSmem2>(d, s) : launch_tma<false, 128, kTSmem>(d, s);
+  }
+  if (split) return two ? launch_tma<true, 64, kTSmem2>(d, s) : launch_tma<true, 64, kTSmem>(d, s);
+  return two ? launch_tma<false, 64, kTSmem2>(d, s) : launch_tma<false, 64, kTSmem>(d, s);
 }
 
 int tc_bn(int N) { return N >= 64 ? 64 : 32; }
@@ -1208,8 +1220,10 @@ int launch_tc_bn(const GemmDesc& d, cudaStream_t s, int* err) {
 }  // namespace
 
 void gemm_tc_init() {
-  tma_configure<false, 64>(); tma_configure<false, 128>();
-  tma_configure<true, 64>(); tma_configure<true, 128>();
+  tma_configure<false, 64, kTSmem>(); tma_configure<false, 128, kTSmem>();
+  tma_configure<true, 64, kTSmem>(); tma_configure<true, 128, kTSmem>();
+  tma_configure<false, 64, kTSmem2>(); tma_configure<false, 128, kTSmem2>();
+  tma_configure<true, 64, kTSmem2>();
   tc_configure<false, false, 32>(); tc_configure<false, false, 64>(); tc_configure<false, false, 128>();
   tc_configure<false, true, 32>(); tc_configure<false, true, 64>(); tc_configure<false, true, 128>();
   tc_configure<true, false, 32>(); tc_configure<true, false, 64>(); tc_configure<true, false, 128>();

@@ -388,19 +388,15 @@ __global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, d
 
 // flag[0] |= 1 when max |A - I| of the P x P matrix A exceeds thr (one CTA).
 __global__ void far_from_identity_kernel(const double* A, int P, double thr, int* flag) {
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  const long long n = (long long)P * P;
+  // one CTA per row block of 8 rows, a warp per row
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   int mine = 0;
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
-    const int i = (int)(e / P), j = (int)(e % P);
-    const double d = A[e] - (i == j ? 1.0 : 0.0);
-    if (!(fabs(d) <= thr)) mine = 1;   // NaN counts as far
-  }
-  if (mine) atomicOr(&any, 1);
-  __syncthreads();
-  if (threadIdx.x == 0 && any) atomicOr(flag, 1);
+  if (i < P)
+    for (int j = threadIdx.x & 31; j < P; j += 32) {
+      const double d = A[(long long)i * P + j] - (i == j ? 1.0 : 0.0);
+      if (!(fabs(d) <= thr)) mine = 1;   // NaN counts as far
+    }
+  if (__any_sync(0xffffffffu, mine) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 __global__ void store_ints_kernel(int* dst, const int* src, int n, int value) {
@@ -598,7 +594,7 @@ int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cu
 }
 
 int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s) {
-  far_from_identity_kernel<<<1, 256, 0, s>>>(A, P, thr, flag);
+  far_from_identity_kernel<<<(P + 7) / 8, 256, 0, s>>>(A, P, thr, flag);
   return 1;
 }
 

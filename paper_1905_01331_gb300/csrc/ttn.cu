@@ -87,6 +87,10 @@ struct Instance {
   std::vector<double*> eoff;
   // FP32 copies used by the tensor-core products (mixed modes)
   std::vector<float*> w32, ops32, adj32;
+  // ttn_options.recompute_ops: the operators of site layers 1..T-1 live in two
+  // ping-pong buffers (layer t in buffer t & 1); pp_holds[b] is the layer whose
+  // operators buffer b holds (-1: none)
+  int pp_holds[2] = {-1, -1};
   int sites(int t) const { return per_node ? (L >> t) : 1; }
   int nodes(int t) const { return per_node ? (L >> (t + 1)) : 1; }
   size_t w_elems(int t) const {
@@ -101,21 +105,22 @@ struct PolarBlock {
 
 // An autotuned launch configuration of one grouped product.
 struct Tuned {
-  int engine, tile, splits;
+  int engine, tile, splits, occ;
   float ms;
 };
 
 // Serialised form of the autotuner's table (the ttn_options.tiles blob).
 struct TuneBlobHeader {
   char magic[4];       // "TTNT"
-  uint32_t version;    // 1
+  uint32_t version;    // 2
   uint32_t count;
   uint32_t reserved;
 };
 struct TuneBlobEntry {
   uint64_t key;
-  int32_t engine, tile, splits;
+  int32_t engine, tile, splits, occ;
   float ms;
+  int32_t reserved;
 };
 
 }  // namespace ttn
@@ -183,6 +188,7 @@ struct ttn_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, double>> ev_flops;   // (engine, flops) per event pair
+  std::vector<double> ev_bytes;                   // algorithmic bytes per event pair
 };
 
 namespace {
@@ -319,7 +325,7 @@ uint64_t tune_key(const GemmDesc& d) {
 // the fastest.  Products are C = sum A B without accumulation into C, so the
 // repeated launches leave the sweep's data as one launch would.
 Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
-  struct Cand { int engine, tile, splits; };
+  struct Cand { int engine, tile, splits, occ; };
   std::vector<Cand> cands;
   long long ksum = 0;
   for (int g = 0; g < d0.ngroups; ++g) ksum += d0.g[g].K;
@@ -330,20 +336,22 @@ Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
   GemmDesc dd = d0;
   dd.tile = 0;
   const int def_splits = std::max(1, std::min(gemm_pick_splits(dd), (int)splits.back()));
-  cands.push_back({d0.tc_engine, 0, def_splits});   // the default configuration
+  cands.push_back({d0.tc_engine, 0, def_splits, 0});   // the default configuration
   for (int s : splits) {
     if (tc) {
       if (gemm_tma_eligible(d0)) {
-        for (int bn : {64, 128}) cands.push_back({0, bn, s});
+        for (int bn : {64, 128})
+          for (int occ : {1, 2})
+            if (!(occ == 2 && bn == 128 && d0.prec == 2)) cands.push_back({0, bn, s, occ});
       }
       for (int bn : {32, 64, 128})
-        if (bn <= std::max(32, d0.N)) cands.push_back({1, bn, s});
+        if (bn <= std::max(32, d0.N)) cands.push_back({1, bn, s, 0});
     } else {
       for (int t : {16, 32, 64})
-        if (t == 16 || t <= std::min(d0.M, d0.N)) cands.push_back({d0.tc_engine, t, s});
+        if (t == 16 || t <= std::min(d0.M, d0.N)) cands.push_back({d0.tc_engine, t, s, 0});
     }
   }
-  Tuned best{cands[0].engine, cands[0].tile, cands[0].splits, 1e30f};
+  Tuned best{cands[0].engine, cands[0].tile, cands[0].splits, cands[0].occ, 1e30f};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -352,6 +360,7 @@ Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
     e.tc_engine = c.engine;
     e.tile = c.tile;
     e.splits = c.splits;
+    e.occ = c.occ;
     e.partial = h->partial;
     e.err = h->iflags + 4;
     gemm_launch(e, h->stream);
@@ -362,7 +371,7 @@ Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
     ms /= (float)std::max(1, h->tune_reps);
-    if (ms < best.ms) best = Tuned{c.engine, c.tile, c.splits, ms};
+    if (ms < best.ms) best = Tuned{c.engine, c.tile, c.splits, c.occ, ms};
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -383,6 +392,7 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
   if (it != h->tuned.end()) {
     d.tc_engine = it->second.engine;
     d.tile = it->second.tile;
+    d.occ = it->second.occ;
     s = it->second.splits;
   } else {
     s = gemm_pick_splits(d);
@@ -412,6 +422,16 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
     for (int g = 0; g < d.ngroups; ++g) kk += d.g[g].K;
     const int engine = (d.prec != 0 && gemm_tc_supported(d)) ? 1 : 0;
     h->ev_flops.push_back({engine, 2.0 * d.M * d.N * kk * d.B0 * d.B1});
+    // algorithmic bytes: every group's operands read once (a batch index of
+    // stride 0 is a broadcast: read once), the output written once
+    double bytes = (double)d.M * d.N * d.B0 * d.B1 * (d.c_f32 ? 4 : 8);
+    for (int g = 0; g < d.ngroups; ++g) {
+      const Group& G = d.g[g];
+      const double ba = (G.a.s_b0 ? d.B0 : 1) * (double)(G.a.s_b1 ? d.B1 : 1);
+      const double bb = (G.b.s_b0 ? d.B0 : 1) * (double)(G.b.s_b1 ? d.B1 : 1);
+      bytes += (double)d.M * G.K * ba * (G.a.f32 ? 4 : 8) + (double)d.N * G.K * bb * (G.b.f32 ? 4 : 8);
+    }
+    h->ev_bytes.push_back(bytes);
     return;
   }
   h->launches += gemm_launch(d, h->stream);
@@ -535,6 +555,15 @@ void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
                                   I.per_node ? 1 : 0, I.eoff[t + 1], h->stream);
     if (v.f32) h->launches += to_f32(I.ops[t + 1], I.ops32[t + 1], I.op_elems(t + 1), h->stream);
   }
+  if (t + 1 < I.T) I.pp_holds[(t + 1) & 1] = t + 1;
+}
+
+// With recomputation (ttn_options.recompute_ops), make the operators of site
+// layer t available again: re-ascend from the bottom through the current (not
+// yet updated) isometries of layers 0..t-1.  A no-op when they are stored.
+void ensure_ops(ttn_ctx* h, Instance& I, int t, int prec) {
+  if (!h->opt.recompute_ops || t <= 0 || t >= I.T || I.pp_holds[t & 1] == t) return;
+  for (int u = 0; u < t; ++u) ascend_layer(h, I, u, prec);
 }
 
 // Top Hamiltonian on x (c x c): w = o_0 x + x o_1^T + sum_k (A_k0 x B_k1^T + B_k0 x A_k1^T)
@@ -792,6 +821,7 @@ void df_end(ttn_ctx* h, int launches, double flops) {
   cudaEventRecord(e, h->stream);
   h->ev_pool.push_back(e);
   h->ev_flops.push_back({2, flops});
+  h->ev_bytes.push_back(0.0);
 }
 
 // F = composed polynomial of one block from the Gram matrix in pA (one
@@ -828,6 +858,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
     h->ev_pool.push_back(ev[0]);
     h->ev_pool.push_back(ev[1]);
     h->ev_flops.push_back({df ? 3 : 0, compose_flops(P, NJ, a.nsteps)});
+    h->ev_bytes.push_back(0.0);
   }
 }
 
@@ -1038,6 +1069,7 @@ void sweep_instance(ttn_ctx* h, Instance& I) {
   if (prec != 0 && !h->measuring)
     h->launches += to_f32(I.adj[I.T], I.adj32[I.T], I.op_elems(I.T), h->stream);
   for (int t = I.T - 1; t >= 0; --t) {
+    ensure_ops(h, I, t, prec);
     environment(h, I, t, prec, h->Gam);
     polar(h, I, t, prec, h->Gam);
     descend(h, I, t, prec);
@@ -1065,7 +1097,42 @@ void isometry_grams(ttn_ctx* h, Instance& I, double* res) {
 void adjoints_only(ttn_ctx* h, Instance& I, int down_to) {
   forward(h, I, 0);
   top_adjoints(h, I);
-  for (int t = I.T - 1; t >= down_to; --t) descend(h, I, t, 0);
+  for (int t = I.T - 1; t >= down_to; --t) {
+    ensure_ops(h, I, t, 0);
+    descend(h, I, t, 0);
+  }
+}
+
+// Energy of the stored tensors and, with grad != nullptr, its derivative with
+// respect to every tensor (laid out as ttn_env with layer -1), with the
+// contractions of the ascend, environment and descend in precision prec (the
+// top contraction, the top adjoints and the energy FP64).
+void value_and_grad(ttn_ctx* h, Instance& I, int prec, double* energy_out, double* grad) {
+  forward(h, I, prec);
+  energy_only(h, I, energy_out);
+  if (!grad) return;
+  const ll c2 = (ll)I.chis[I.T] * I.chis[I.T];
+  size_t off = 0;
+  for (int t = 0; t < I.T; ++t) off += I.w_elems(t);
+  if (!h->measuring) {
+    top_matvec(h, I, I.V, h->lz_w, nullptr);
+    h->launches += top_grad(grad + off, h->lz_w, I.V, c2, I.eoff[I.T], I.per_node ? 1 : 0,
+                            h->stream);
+  } else {
+    top_matvec(h, I, I.V, h->lz_w, nullptr);
+  }
+  top_adjoints(h, I);
+  if (prec != 0 && !h->measuring)
+    h->launches += to_f32(I.adj[I.T], I.adj32[I.T], I.op_elems(I.T), h->stream);
+  for (int t = I.T - 1; t >= 0; --t) {
+    off -= I.w_elems(t);
+    ensure_ops(h, I, t, prec);
+    environment(h, I, t, prec, h->Gam);
+    if (!h->measuring)
+      cudaMemcpyAsync(grad + off, h->Gam, I.w_elems(t) * sizeof(double), cudaMemcpyDeviceToDevice,
+                      h->stream);
+    if (t > 0) descend(h, I, t, prec);
+  }
 }
 
 // Plan all scratch sizes (pass with base == nullptr) or carve them.
@@ -1087,12 +1154,25 @@ void layout(ttn_ctx* h, Arena& ar) {
       nj_max = std::max(nj_max, (size_t)I.nodes(t));
     }
     I.eoff.assign(I.T + 1, nullptr);
+    const bool rec = h->opt.recompute_ops != 0;
+    size_t pp_elems = 0;
+    for (int t = 1; t < I.T; ++t) pp_elems = std::max(pp_elems, I.op_elems(t));
+    double* pp[2] = {nullptr, nullptr};
+    float* pp32[2] = {nullptr, nullptr};
+    if (rec && pp_elems) {
+      for (int b = 0; b < 2; ++b) {
+        pp[b] = ar.take(pp_elems);
+        if (h->opt.prec != 0) pp32[b] = reinterpret_cast<float*>(ar.take((pp_elems + 1) / 2));
+      }
+    }
+    I.pp_holds[0] = I.pp_holds[1] = -1;
     for (int t = 0; t <= I.T; ++t) {
-      I.ops[t] = ar.take(I.op_elems(t));
+      const bool shared = rec && t > 0 && t < I.T;
+      I.ops[t] = shared ? pp[t & 1] : ar.take(I.op_elems(t));
       I.adj[t] = ar.take(I.op_elems(t));
       I.eoff[t] = ar.take(I.sites(t));
       if (h->opt.prec != 0) {
-        I.ops32[t] = reinterpret_cast<float*>(ar.take((I.op_elems(t) + 1) / 2));
+        I.ops32[t] = shared ? pp32[t & 1] : reinterpret_cast<float*>(ar.take((I.op_elems(t) + 1) / 2));
         I.adj32[t] = reinterpret_cast<float*>(ar.take((I.op_elems(t) + 1) / 2));
       }
     }
@@ -1199,6 +1279,7 @@ void plan(ttn_ctx* h) {
     adjoints_only(h, I, 0);
     energy_only(h, I, nullptr);
     isometry_grams(h, I, nullptr);
+    value_and_grad(h, I, h->opt.prec, nullptr, h->Gam);
   }
   h->measuring = false;
 }
@@ -1248,6 +1329,7 @@ void ttn_default_options(ttn_options* o) {
   o->wait_polls = 0;
   o->tiles = nullptr;
   o->tiles_bytes = 0;
+  o->recompute_ops = 0;
 }
 
 // Parse an autotuner blob (ttn_options.tiles) into the table.
@@ -1256,17 +1338,17 @@ static int load_tiles(ttn_ctx* h, const void* blob, size_t bytes) {
   if (bytes < sizeof(TuneBlobHeader)) return fail(h, TTN_EINVAL, "tiles blob too short");
   TuneBlobHeader hd;
   std::memcpy(&hd, blob, sizeof(hd));
-  if (std::memcmp(hd.magic, "TTNT", 4) != 0 || hd.version != 1 ||
+  if (std::memcmp(hd.magic, "TTNT", 4) != 0 || hd.version != 2 ||
       bytes < sizeof(hd) + (size_t)hd.count * sizeof(TuneBlobEntry))
     return fail(h, TTN_EINVAL, "not a tiles blob of this library");
   const char* p = static_cast<const char*>(blob) + sizeof(hd);
   for (uint32_t i = 0; i < hd.count; ++i) {
     TuneBlobEntry e;
     std::memcpy(&e, p + i * sizeof(e), sizeof(e));
-    if (e.engine < 0 || e.engine > 1 || e.splits < 1 || e.splits > 64 ||
-        !(e.tile == 0 || e.tile == 16 || e.tile == 32 || e.tile == 64 || e.tile == 128))
+    if (e.engine < 0 || e.engine > 1 || e.splits < 1 || e.splits > 64 || e.occ < 0 ||
+        e.occ > 2 || !(e.tile == 0 || e.tile == 16 || e.tile == 32 || e.tile == 64 || e.tile == 128))
       return fail(h, TTN_EINVAL, "tiles blob entry out of range");
-    h->tuned[e.key] = Tuned{e.engine, e.tile, e.splits, e.ms};
+    h->tuned[e.key] = Tuned{e.engine, e.tile, e.splits, e.occ, e.ms};
   }
   return TTN_OK;
 }
@@ -1744,6 +1826,22 @@ int ttn_energy(ttn_t h, int inst, double* E) {
   return rc ? rc : read_status(h, false);
 }
 
+int ttn_value_and_grad(ttn_t h, int inst, int prec, double* E, double* d_grad) {
+  if (!h || !E || inst < 0 || inst >= (int)h->inst.size() || prec < 0 || prec > 4)
+    return TTN_EINVAL;
+  if (prec != 0 && prec != h->opt.prec && h->opt.prec == 0)
+    return fail(h, TTN_EINVAL, "context was created for FP64 only");
+  sync_user(h);
+  Instance& I = h->inst[inst];
+  value_and_grad(h, I, prec, h->scal + 5, d_grad);
+  int rc = check_cuda(h, cudaMemcpyAsync(E, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost,
+                                         h->stream), "value_and_grad");
+  if (rc) return rc;
+  rc = check_cuda(h, cudaStreamSynchronize(h->stream), "value_and_grad sync");
+  fence_user(h);
+  return rc ? rc : read_status(h, false);
+}
+
 int ttn_rdm(ttn_t h, int inst, int site_layer, int which, double* out) {
   if (!h || !out || inst < 0 || inst >= (int)h->inst.size()) return TTN_EINVAL;
   Instance& I = h->inst[inst];
@@ -1815,6 +1913,7 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
   }
   adjoints_only(h, I, layer < 0 ? 0 : layer + 1);
   if (layer >= 0) {
+    ensure_ops(h, I, layer, 0);
     environment(h, I, layer, 0, h->Gam);
     int rc = check_cuda(h, cudaMemcpyAsync(d_out, h->Gam, I.w_elems(layer) * sizeof(double),
                                            cudaMemcpyDeviceToDevice, h->stream), "env");
@@ -1825,6 +1924,7 @@ int ttn_env(ttn_t h, int inst, int layer, double* d_out) {
   // all layers, concatenated as ttn_set_isometries lays them out, then the top
   size_t off = 0;
   for (int t = 0; t < I.T; ++t) {
+    ensure_ops(h, I, t, 0);
     environment(h, I, t, 0, h->Gam);
     int rc = check_cuda(h, cudaMemcpyAsync(d_out + off, h->Gam, I.w_elems(t) * sizeof(double),
                                            cudaMemcpyDeviceToDevice, h->stream), "env");
@@ -1902,7 +2002,7 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   h->profiling = false;
   int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
   if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
-  double ms[4] = {0, 0, 0, 0}, fl[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0};
+  double ms[4] = {0, 0, 0, 0}, fl[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, by[4] = {0, 0, 0, 0};
   for (size_t i = 0; i < h->ev_flops.size(); ++i) {
     float e = 0.f;
     cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
@@ -1910,12 +2010,14 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
     ms[g] += e;
     fl[g] += h->ev_flops[i].second;
     cnt[g] += 1;
+    if (i < h->ev_bytes.size()) by[g] += h->ev_bytes[i];
   }
   float tot = 0.f;
   cudaEventElapsedTime(&tot, t0, t1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
   h->ev_flops.clear();
+  h->ev_bytes.clear();
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
@@ -1923,6 +2025,10 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   out[6] = tot - ms[0] - ms[1] - ms[2] - ms[3];
   out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2] - cnt[3];
   out[8] = tot;
+  if (n_out >= 17) {
+    out[15] = by[0];
+    out[16] = by[1];
+  }
   if (n_out >= 15) {
     out[9] = ms[2]; out[10] = fl[2]; out[11] = cnt[2];
     out[12] = ms[3]; out[13] = fl[3]; out[14] = cnt[3];
@@ -1952,6 +2058,7 @@ int ttn_autotune(ttn_t h, int reps, void* blob, size_t* blob_bytes) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     h->ev_flops.clear();
+    h->ev_bytes.clear();
     rc = check_cuda(h, cudaStreamSynchronize(h->stream), "autotune sync");
     if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
     if (!rc) rc = read_status(h, false);
@@ -1971,14 +2078,15 @@ int ttn_autotune(ttn_t h, int reps, void* blob, size_t* blob_bytes) {
     if (*blob_bytes < need) return fail(h, TTN_EINVAL, "tiles buffer too small");
     TuneBlobHeader hd;
     std::memcpy(hd.magic, "TTNT", 4);
-    hd.version = 1;
+    hd.version = 2;
     hd.count = (uint32_t)h->tuned.size();
     hd.reserved = 0;
     char* p = static_cast<char*>(blob);
     std::memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
     for (const auto& kv : h->tuned) {
-      TuneBlobEntry e{kv.first, kv.second.engine, kv.second.tile, kv.second.splits, kv.second.ms};
+      TuneBlobEntry e{kv.first, kv.second.engine, kv.second.tile, kv.second.splits,
+                      kv.second.occ, kv.second.ms, 0};
       std::memcpy(p, &e, sizeof(e));
       p += sizeof(e);
     }

@@ -142,11 +142,12 @@ def test_tiles_blob_is_validated_at_planning(lib):
         opt.tiles_bytes = len(blob)
         return lib.ttn_workspace_bytes(ctypes.byref(p), 1, ctypes.byref(opt))
 
-    empty = b"TTNT" + struct.pack("<III", 1, 0, 0)
+    empty = b"TTNT" + struct.pack("<III", 2, 0, 0)
     assert size_with(empty) > 0
     assert size_with(b"garbage-garbage-garbage") == 0
-    entry = struct.pack("<QiiIf", 123, 0, 48, 4, 1.0)             # tile 48: not a tile width
-    assert size_with(b"TTNT" + struct.pack("<III", 1, 1, 0) + entry) == 0
-    entry = struct.pack("<Qiiif", 123, 1, 64, 2, 1.0)
-    assert size_with(b"TTNT" + struct.pack("<III", 1, 1, 0) + entry) > 0
-    assert size_with(b"TTNT" + struct.pack("<III", 1, 2, 0) + entry) == 0   # truncated
+    assert size_with(b"TTNT" + struct.pack("<III", 1, 0, 0)) == 0           # another version
+    entry = struct.pack("<Qiiiifi", 123, 0, 48, 4, 1, 1.0, 0)              # tile 48: not a width
+    assert size_with(b"TTNT" + struct.pack("<III", 2, 1, 0) + entry) == 0
+    entry = struct.pack("<Qiiiifi", 123, 1, 64, 2, 0, 1.0, 0)
+    assert size_with(b"TTNT" + struct.pack("<III", 2, 1, 0) + entry) > 0
+    assert size_with(b"TTNT" + struct.pack("<III", 2, 2, 0) + entry) == 0   # truncated
