@@ -52,13 +52,17 @@ def parse():
     p.add_argument("--chi", type=int, default=128)
     p.add_argument("--no-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the launchers' default tiles")
+    p.add_argument("--tiles-file", default=None,
+                   help="load the autotuner's table from this file instead of tuning")
+    p.add_argument("--save-tiles", default=None, help="write the autotuner's table to this file")
     p.add_argument("--cpu-1thread", action="store_true",
                    help="also time the oracle with one BLAS thread (minutes at chi=128)")
     p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
     p.add_argument("--workload", default="tfim1024",
-                   choices=["tfim1024", "batched64", "paper-torus", "top-mode", "configs"],
+                   choices=["tfim1024", "batched64", "paper-torus", "top-mode", "configs",
+                            "polar-study"],
                    help="tfim1024: the headline line; batched64: 64 independent chains in one "
                         "context; paper-torus: the paper's 128 x 5 torus at h = 2.9 with its "
                         "entanglement spectrum; top-mode: eigensolver vs polar-step top update; "
@@ -216,7 +220,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded QR-orthonormalised Gaussian isometries)",
-            "config": dict(WORKLOAD, precision="fp64", engine="numpy/LAPACK oracle"),
+            "config": dict(WORKLOAD, chi=args.chi, workload=f"tfim_chain_L1024_h1_chi{args.chi}",
+                           precision="fp64", engine="numpy/LAPACK oracle"),
             "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
                              "cpu_model": cpu_model(),
                              "sample": f"{args.steps} full sweeps after {args.warmup} warm-up sweeps "
@@ -272,6 +277,9 @@ def run_gpu(args):
     tune_t0 = time.perf_counter()
     tiles_blob = s.autotune(reps=3) if not args.no_autotune else b""
     tune_s = time.perf_counter() - tune_t0
+    if args.save_tiles and tiles_blob:
+        with open(args.save_tiles, "wb") as f:
+            f.write(tiles_blob)
     s.sweep(args.warmup)
     stream = s.stream
     torch.cuda.synchronize()
@@ -400,7 +408,8 @@ def run_gpu(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.prec == "fp64" else "f32(" + args.prec + ")+f64",
            "data": "synthetic (seeded QR-orthonormalised Gaussian isometries)",
-           "config": dict(WORKLOAD, precision=args.prec, chis=chis,
+           "config": dict(WORKLOAD, chi=chi, workload=f"tfim_chain_L1024_h1_chi{chi}",
+                          precision=args.prec, chis=chis,
                           parallelism=("replicas x%d" % world) if world > 1 else "single GPU",
                           l2="working set %.0f MB > 129 MB L2" % (s.workspace.numel() / 1e6)),
            "tflops": flops_per_sweep * value / world / 1e12,
@@ -496,8 +505,13 @@ def run_profile_only(args):
     from paper_1905_01331_gb300 import Sweeper
     model = ti.tfim_chain(1024, 1.0)
     ws, V = ti.initial_tensors(1024, 2, args.chi, 1)
-    s = Sweeper(model, args.chi, prec=args.prec, use_graph=False)
+    tiles = open(args.tiles_file, "rb").read() if args.tiles_file else None
+    s = Sweeper(model, args.chi, prec=args.prec, use_graph=False, tiles=tiles)
     s.set_isometries(0, ws, V)
+    if tiles is None and not args.no_autotune:
+        # the configurations the bench times (the tuning sweep is the first of the list)
+        s.autotune(reps=3)
+        s.set_isometries(0, ws, V)
     E = s.sweep(args.profile_sweeps)
     torch.cuda.synchronize()
     print(json.dumps({"profile_sweeps": args.profile_sweeps, "prec": args.prec,
@@ -507,29 +521,73 @@ def run_profile_only(args):
 
 def run_batched(args):
     """64 independent TFIM chains (h ~ U[0.5,1.5], L ~ {64..512}, chi ~ {32,64,128},
-    seed 4) advanced together in one context and one captured sweep."""
+    seed 4) advanced together in one context and one captured sweep.  Under
+    torchrun the chains are sharded by instance (cost-balanced, no collective
+    on the data path): each rank advances its own share, the job's time is the
+    slowest rank's and the throughput counts every rank's instance-sweeps."""
     import torch
     import ttn_inputs as ti
-    from paper_1905_01331_gb300 import Sweeper
-    wls = ti.batched_chains()
+    from paper_1905_01331_gb300 import Sweeper, instance_cost, shard_instances
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wls_all = ti.batched_chains()
+    mine = shard_instances([instance_cost(w.model.Lx, w.chi) for w in wls_all], world, rank)
+    wls = [wls_all[i] for i in mine]
     s = Sweeper([w.model for w in wls], [w.chi for w in wls], prec=args.prec)
     for i, w in enumerate(wls):
         s.set_isometries(i, *ti.initial_tensors(w.model.Lx, 2, w.chi, w.seed))
-    s.sweep(args.warmup)
+    # per-instance error of the first sweep's energy against the oracle's
+    # (the stored values written by oracle/make_golden.py), per site
+    E1 = s.sweep(1)[0]
+    err = None
+    gpath = os.path.join(ROOT, "tests", "golden", "oracle_batched64_first_sweep.json")
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            gold = json.load(f)["instances"]
+        err = [abs(E1[k] - gold[i]["first_sweep_energy"]) / wls_all[i].model.Lx
+               for k, i in enumerate(mine)]
+    if args.warmup > 1:
+        s.sweep(args.warmup - 1)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(s.stream)
     s.sweep_async(args.steps)
     b.record(s.stream)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     ms = a.elapsed_time(b)
-    print(json.dumps({"metric": "batched TTN sweeps/s (64 independent chains, instance-sweeps)",
-                      "value": len(wls) * args.steps / (ms * 1e-3), "unit": "instance-sweeps/s",
-                      "ms_per_step": ms / args.steps, "steps": args.steps, "warmup": args.warmup,
-                      "precision": args.prec, "instances": len(wls),
-                      "gpu_launches": s.launch_count}))
+    # throughput over all ranks: instance-sweeps of the whole job / slowest rank
+    ms_max = ms
+    total = len(wls) * args.steps
+    if dist is not None:
+        t = torch.tensor([ms, float(total)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, total = float(tmax[0]), float(t[1])
+    if rank == 0:
+        print(json.dumps({"metric": "batched TTN sweeps/s (64 independent chains, instance-sweeps)",
+                          "value": total / (ms_max * 1e-3), "unit": "instance-sweeps/s",
+                          "n_gpus": world, "scaling": "strong", "ms_per_step": ms_max / args.steps,
+                          "steps": args.steps, "warmup": args.warmup, "precision": args.prec,
+                          "instances": len(wls_all), "instances_rank0": len(wls),
+                          "parallelism": ("instances sharded over %d ranks" % world) if world > 1
+                          else "single GPU", "gpu_launches": s.launch_count,
+                          "first_sweep_energy_error_vs_oracle": None if err is None else {
+                              "max": max(err), "median": statistics.median(err),
+                              "unit": "energy per site",
+                              "instances": len(err)}}))
     s.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_paper_torus(args):
@@ -694,10 +752,109 @@ def run_top_mode_study(args):
     print(json.dumps(out))
 
 
+def run_polar_study(args):
+    """Sec. III.B / Fig. 9: the update from the SVD of the environment (Fig.
+    9a) against the EVD of its Gram matrix (Fig. 9b: E^T E = V S^2 V^T,
+    w = V S^-1 V^T E^T) and the Newton-Schulz schedule the library uses (FP64
+    mode: blocks of at most four scaled steps per fresh Gram matrix), on the
+    damped environments Gamma - mu |Gamma| w of the full layers of the TFIM
+    L=1024 chain at chi (state after 20 FP64 sweeps).  All three in FP64 on the
+    GPU with torch (cuSOLVER / cuBLAS): the distance of each factor to the
+    SVD's, its isometry defect, and its time."""
+    import numpy as np
+    import torch
+    import ttn_inputs as ti
+    from paper_1905_01331_gb300 import Sweeper
+    chi = args.chi
+    model = ti.tfim_chain(1024, 1.0)
+    ws, V = ti.initial_tensors(1024, 2, chi, 1)
+    s = Sweeper(model, chi, prec="fp64")
+    s.set_isometries(0, ws, V)
+    s.sweep(20)
+    ws, V = s.get_isometries(0)
+    mu = 1e-7
+
+    def timed(f, reps=5):
+        f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = f()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) / reps * 1e3
+
+    def ns_schedule(l0, gmax=30.0, maxb=4):
+        out, l, cur, start = [], l0, [], l0
+        while 1 - l > 1e-15 and len(out) + len(cur) < 200:
+            c = math.sqrt(3 / (1 + l + l * l))
+            ln = 1.5 * c * l - 0.5 * c ** 3 * l ** 3
+            if cur and (ln / start > gmax or len(cur) >= maxb):
+                out.append(cur)
+                cur, start = [], l
+            cur.append((1.5 * c, 0.5 * c ** 3))
+            l = ln
+        if cur:
+            out.append(cur)
+        return out
+
+    sched = ns_schedule(mu / 4)
+    rows = []
+    for t, w in enumerate(ws):
+        P, n = w.shape[0], w.shape[1]
+        if P < 64:
+            continue
+        g = s.env(0, t).reshape(P, n * n)
+        W0 = torch.tensor(w.reshape(P, n * n), device="cuda")
+        G = g - mu * torch.linalg.norm(g) * W0
+
+        def svd():
+            U, S, Vh = torch.linalg.svd(G, full_matrices=False)
+            return -(U @ Vh)
+
+        def evd():
+            ev, Q = torch.linalg.eigh(G @ G.T)
+            ev = torch.clamp(ev, min=1e-300)
+            return -((Q * ev.rsqrt()) @ Q.T) @ G
+
+        def ns():
+            X = G / torch.linalg.norm(G)
+            I = torch.eye(P, dtype=torch.float64, device="cuda")
+            for blk in sched:
+                A = X @ X.T
+                F = I.clone()
+                for a, c in blk:
+                    Pm = a * I - c * A
+                    F = Pm @ F
+                    A = Pm @ A @ Pm
+                    A = 0.5 * (A + A.T)
+                X = F @ X
+            return -X
+
+        Wsvd, t_svd = timed(svd)
+        row = {"layer": t, "P": P, "n2": n * n, "ms_svd": t_svd}
+        U, S, Vh = torch.linalg.svd(G, full_matrices=False)
+        row["sigma_min_over_max"] = float(S[-1] / S[0])
+        for name, f in (("evd", evd), ("newton_schulz", ns)):
+            Wx, ms = timed(f)
+            I = torch.eye(P, dtype=torch.float64, device="cuda")
+            row[name] = {"ms": ms, "max_abs_diff_vs_svd": float((Wx - Wsvd).abs().max()),
+                         "isometry_defect": float((Wx @ Wx.T - I).abs().max())}
+        rows.append(row)
+    s.close()
+    print(json.dumps({"study": "polar factor of the damped environment: SVD (Fig. 9a) vs EVD "
+                               "(Fig. 9b) vs Newton-Schulz (FP64, torch on the GPU)",
+                      "workload": f"tfim_chain_L1024_h1_chi{chi}, state after 20 FP64 sweeps",
+                      "mu": mu, "ns_steps": sum(len(b) for b in sched), "ns_blocks": len(sched),
+                      "layers": rows}))
+
+
 def main():
     args = parse()
     if args.workload == "top-mode":
         run_top_mode_study(args)
+        return
+    if args.workload == "polar-study":
+        run_polar_study(args)
         return
     if args.workload == "configs":
         run_configs(args)

@@ -119,6 +119,13 @@ typedef struct {
                                kernels before it expires and the sweep reports
                                TTN_ETIMEOUT (0, the default: 2^21 polls, about
                                one second) */
+  int stage_streams;        /* independent products of one sweep stage (the
+                               one-leg products of an ascend or environment, the
+                               products and traces of a descend) run
+                               concurrently on this many sub-streams of each
+                               lane (parallel branches of the captured graph),
+                               each with its own split-K buffer; 0 or 1: one
+                               stream.  Default 3 (the maximum) */
   int recompute_ops;        /* 1: keep the ascended operators of site layers
                                1..T-1 in two shared buffers and recompute them
                                (ascending from the bottom through the current
@@ -261,8 +268,10 @@ long long ttn_launch_count(ttn_t h);
  * with 12 <= n_out < 15, out[9..11] = both together; with fewer they count as
  * "other"; with n_out >= 17, out[15] and out[16] = the algorithmic bytes of
  * the FP64-engine and tensor-core products (every group's operands read once,
- * a batch index of stride 0 read once, the output written once).  The sweep
- * updates the tensors like ttn_sweep.  n_out >= 9. */
+ * a batch index of stride 0 read once, the output written once); with n_out
+ * >= 19, out[17] and out[18] = milliseconds and launches of the persistent
+ * top solve (else counted as "other").  The sweep updates the tensors like
+ * ttn_sweep.  n_out >= 9. */
 int ttn_profile_sweep(ttn_t h, double* out, int n_out);
 
 /* Diagnostic: the tensor-core engine against the FP64 engine on seeded random
@@ -309,9 +318,9 @@ int ttn_close_noalloc(const double* d_Y, const double* d_W, int P, int Q, long l
  * CUDA events over `reps` launches after one warm-up launch: for tensor-core
  * products the engine (TMA-fed where eligible, thread-staged), its tile width
  * BN, the TMA-fed kernel's stage ring (192 KB, one CTA per SM, or 96 KB, two)
- * and the split count of K; for FP64 products the tile (16, 32, 64) and
- * the split count; the split counts are limited to the context's split-K
- * buffer.  The fastest becomes the product's configuration (the next
+ * and the split count of K (powers of two up to 128); for FP64 products the
+ * tile (16, 32, 64) and the split count; the split counts are limited to the
+ * context's split-K buffer.  The fastest becomes the product's configuration (the next
  * ttn_sweep captures its graph again).  The sweep updates the tensors like
  * ttn_sweep.  With blob_bytes != NULL the table is exported: blob == NULL
  * returns the size in *blob_bytes, else the table is written to blob (at

@@ -22,6 +22,33 @@ class TTNError(RuntimeError):
     pass
 
 
+def instance_cost(L, chi, K=1, d0=2):
+    """Relative cost of one sweep of an instance: its O(chi^4) contractions per
+    layer (Sec. V) plus the top solve, from the bond dimensions alone."""
+    chis = [d0]
+    while len(chis) < int(round(math.log2(L))):
+        chis.append(min(chi, chis[-1] ** 2))
+    c = sum(chis[t + 1] * chis[t] ** 3 * (1 + 2 * K) for t in range(len(chis) - 1))
+    return c + 150.0 * chis[-1] ** 3 * (1 + 2 * K)
+
+
+def shard_instances(costs, world, rank):
+    """Indices of the instances rank `rank` of `world` advances: the instances
+    are independent (no collective on the data path), assigned longest first
+    to the least loaded rank so that the slowest rank, which sets the job's
+    time, carries as little as possible.  Every rank computes the same
+    assignment from the same costs."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += costs[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
@@ -39,7 +66,7 @@ class Sweeper:
                  lanczos_tol=0.0, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
                  persistent=True, streams=8, polar_blocks=0, double_float=True, wait_polls=0,
-                 tc_engine=0, tiles=None, recompute_ops=False):
+                 tc_engine=0, tiles=None, recompute_ops=False, stage_streams=3):
         import torch
         self._torch = torch
         self.lib = _abi.load()
@@ -76,6 +103,7 @@ class Sweeper:
         opt.wait_polls = int(wait_polls)
         opt.tc_engine = int(tc_engine)
         opt.recompute_ops = int(bool(recompute_ops))
+        opt.stage_streams = int(stage_streams)
         if tiles:
             self._tiles = ctypes.create_string_buffer(bytes(tiles), len(tiles))
             opt.tiles = ctypes.cast(self._tiles, ctypes.c_void_p)
@@ -232,11 +260,12 @@ class Sweeper:
 
     def profile_sweep(self):
         """One eagerly launched sweep with every product timed by CUDA events."""
-        out = np.zeros(17)
-        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 17), "profile_sweep")
+        out = np.zeros(19)
+        self._check(self.lib.ttn_profile_sweep(self.h, _ptr(out), 19), "profile_sweep")
         keys = ["fp64_ms", "fp64_flops", "fp64_launches", "tc_ms", "tc_flops", "tc_launches",
                 "other_ms", "other_launches", "total_ms", "df_ms", "df_flops", "df_launches",
-                "dfc_ms", "dfc_flops", "dfc_launches", "fp64_bytes", "tc_bytes"]
+                "dfc_ms", "dfc_flops", "dfc_launches", "fp64_bytes", "tc_bytes", "top_ms",
+                "top_launches"]
         return dict(zip(keys, out.tolist()))
 
     @property

@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("streams", ctypes.c_int), ("polar_blocks", ctypes.c_int),
                 ("double_float", ctypes.c_int), ("tc_engine", ctypes.c_int),
-                ("wait_polls", ctypes.c_int), ("recompute_ops", ctypes.c_int),
+                ("wait_polls", ctypes.c_int), ("stage_streams", ctypes.c_int),
+                ("recompute_ops", ctypes.c_int),
                 ("tiles", ctypes.c_void_p),
                 ("tiles_bytes", ctypes.c_size_t)]
 

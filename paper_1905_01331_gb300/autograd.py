@@ -1,6 +1,6 @@
 """The TTN energy as a differentiable PyTorch function.
 
-``TTNEnergy.apply(sweeper, inst, prec, v, *ws)`` returns the energy
+``TTNEnergy.apply(sweeper, inst, prec, need_grad, v, *ws)`` returns the energy
 <psi(ws, v)|H|psi(ws, v)> of one instance (Sec. II.C).  Its backward is the
 library's environment kernel (Sec. III.A): dE/dw_t for every isometry layer
 and dE/dv = 2 H_top v.  Forward and backward come from one call of
@@ -27,14 +27,13 @@ def _cat(ws):
 
 class TTNEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, sweeper, inst, prec, v, *ws):
+    def forward(ctx, sweeper, inst, prec, need_grad, v, *ws):
         flat = _cat(ws)
         vc = v.contiguous()
         dp = ctypes.POINTER(ctypes.c_double)
         rc = sweeper.lib.ttn_set_isometries(sweeper.h, inst, ctypes.cast(flat.data_ptr(), dp),
                                             ctypes.cast(vc.data_ptr(), dp))
         sweeper._check(rc, "set_isometries")
-        need_grad = torch.is_grad_enabled() and (v.requires_grad or any(w.requires_grad for w in ws))
         grad = torch.empty(flat.numel() + vc.numel(), dtype=torch.float64, device=v.device) \
             if need_grad else None
         E = ctypes.c_double()
@@ -55,7 +54,7 @@ class TTNEnergy(torch.autograd.Function):
             grads.append(out[off:off + n].view(shp))
             off += n
         gv = out[off:].view(ctx.vshape)
-        return (None, None, None, gv, *grads)
+        return (None, None, None, None, gv, *grads)
 
 
 def energy(sweeper, inst, v, ws, prec="fp64"):
@@ -63,4 +62,7 @@ def energy(sweeper, inst, v, ws, prec="fp64"):
     contractions in precision ``prec`` ("fp64", "tf32", "tf32x3", "bf16",
     "bf16x3"; a mixed one needs a Sweeper created with a mixed precision)."""
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-    return TTNEnergy.apply(sweeper, inst, p, v, *ws)
+    # the caller's grad mode decides whether the pass also forms the gradient
+    # (inside Function.forward autograd is always off)
+    need = torch.is_grad_enabled() and (v.requires_grad or any(w.requires_grad for w in ws))
+    return TTNEnergy.apply(sweeper, inst, p, need, v, *ws)

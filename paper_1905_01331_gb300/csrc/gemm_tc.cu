@@ -656,11 +656,21 @@ __global__ void splitk_reduce_tc(const GemmDesc d) {
     const long long b = e / MN, r = e % MN;
     const int m = static_cast<int>(r / d.N), n = static_cast<int>(r % d.N);
     float sh = 0.f, sl = 0.f;
-    for (int sp = 0; sp < d.splits; ++sp) {
-      const float x = part[(sp * d.B0 * d.B1 + b) * MN + r];
-      const float s = sh + x, bb = s - sh;
-      sl += (sh - (s - bb)) + (x - bb);
-      sh = s;
+    const long long step = static_cast<long long>(d.B0) * d.B1 * MN;
+    const float* pe = part + b * MN + r;
+    // partials loaded eight at a time (independent loads in flight), summed in
+    // split order
+    for (int sp0 = 0; sp0 < d.splits; sp0 += 8) {
+      float xs[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xs[q] = sp0 + q < d.splits ? pe[(sp0 + q) * step] : 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float x = xs[q];
+        const float s = sh + x, bb = s - sh;
+        sl += (sh - (s - bb)) + (x - bb);
+        sh = s;
+      }
     }
     const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
     const long long ce = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
@@ -1249,7 +1259,7 @@ int tc_pick_splits(const GemmDesc& d) {
   const long long sms = device_sm_count();
   if (base >= sms || kt < 8) return 1;
   int s = static_cast<int>(std::min<long long>((sms + base - 1) / base, kt / 4));
-  return std::max(1, std::min(s, 64));
+  return std::max(1, std::min(s, 128));
 }
 
 int gemm_tc_launch(const GemmDesc& d, cudaStream_t s) {

@@ -294,6 +294,7 @@ __device__ __forceinline__ void store_tile_df(float* C, int P, int ti, int tj, f
   }
 }
 
+
 __device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err,
                                 int max_spin) {
   __syncthreads();

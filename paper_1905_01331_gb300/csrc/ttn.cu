@@ -103,6 +103,18 @@ struct PolarBlock {
   std::vector<std::pair<double, double>> steps;  // p(A) = a I - c A
 };
 
+// Sub-streams of a lane: independent products of one sweep stage run on them
+// concurrently (parallel branches of the captured graph), each with its own
+// split-K buffer.
+constexpr int kSubStreams = 3;
+struct SubStreams {
+  int n = 0;                              // 0: stages run on the lane's stream
+  cudaStream_t s[kSubStreams] = {};
+  double* partial[kSubStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSubStreams] = {};
+};
+
 // An autotuned launch configuration of one grouped product.
 struct Tuned {
   int engine, tile, splits, occ;
@@ -140,6 +152,7 @@ struct Lane {
          *top_stack0 = nullptr, *top_stack1 = nullptr, *lz_part = nullptr;
   double *lz_opsp = nullptr, *lz_bp = nullptr, *lz_Yp = nullptr;
   int* iflags = nullptr;
+  SubStreams sub;
 };
 
 struct ttn_ctx {
@@ -172,6 +185,7 @@ struct ttn_ctx {
   double *lz_opsp = nullptr, *lz_bp = nullptr, *lz_Yp = nullptr;
   int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan [4]=wait expired
                                // [5]=grid-barrier counter of the polar composition
+  SubStreams sub;              // of the current lane
   int lz_m = 48;
   double* E_hist = nullptr;    // device energies of the current ttn_sweep call
   std::vector<PolarBlock> polar_f64, polar_tc;
@@ -196,7 +210,7 @@ namespace {
 #define TTN_LANE_FIELDS(X_) X_(stream) X_(Y) X_(Gam) X_(X) X_(X2) X_(Yt) X_(M1) X_(pA) X_(pF) \
   X_(pP) X_(pT) X_(pS) X_(partial) X_(red) X_(scal) X_(lz_basis) X_(lz_w) X_(lz_c1) X_(lz_c2) \
   X_(lz_alpha) X_(lz_beta) X_(lz_y) X_(lz_tmp) X_(top_stack0) X_(top_stack1) X_(lz_part) \
-  X_(lz_opsp) X_(lz_bp) X_(lz_Yp) X_(iflags)
+  X_(lz_opsp) X_(lz_bp) X_(lz_Yp) X_(iflags) X_(sub)
 
 void load_lane(ttn_ctx* h, const Lane& l) {
 #define TTN_LOAD(f) h->f = l.f;
@@ -330,7 +344,7 @@ Tuned tune_product(ttn_ctx* h, const GemmDesc& d0) {
   long long ksum = 0;
   for (int g = 0; g < d0.ngroups; ++g) ksum += d0.g[g].K;
   std::vector<int> splits;
-  for (int s = 1; s <= 64; s *= 2)
+  for (int s = 1; s <= 128; s *= 2)
     if (s == 1 || (s <= ksum / 64 && gemm_partial_elems(d0, s) <= h->partial_cap)) splits.push_back(s);
   const bool tc = d0.prec != 0 && gemm_tc_supported(d0);
   GemmDesc dd = d0;
@@ -437,6 +451,42 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
   h->launches += gemm_launch(d, h->stream);
 }
 
+// Independent products of one stage: fork() makes the sub-streams wait for
+// the work enqueued so far, branch(i) directs the following launches to
+// sub-stream i (with its own split-K buffer), join() makes the lane's stream
+// wait for every sub-stream and restores it.  Without sub-streams (or in a
+// profiling or tuning sweep, which time one product at a time) all three are
+// no-ops and everything stays on the lane's stream.
+struct StageFork {
+  ttn_ctx* h;
+  cudaStream_t main;
+  double* partial;
+  bool on;
+  explicit StageFork(ttn_ctx* hh)
+      : h(hh), main(hh->stream), partial(hh->partial),
+        on(hh->sub.n > 0 && !hh->measuring && !hh->profiling && !hh->tuning) {
+    if (!on) return;
+    cudaEventRecord(h->sub.fork, main);
+    for (int i = 0; i < h->sub.n; ++i) cudaStreamWaitEvent(h->sub.s[i], h->sub.fork, 0);
+  }
+  void branch(int i) {
+    if (!on) return;
+    h->stream = h->sub.s[i % h->sub.n];
+    h->partial = h->sub.partial[i % h->sub.n];
+  }
+  void join() {
+    if (!on) return;
+    for (int i = 0; i < h->sub.n; ++i) {
+      cudaEventRecord(h->sub.join[i], h->sub.s[i]);
+      cudaStreamWaitEvent(main, h->sub.join[i], 0);
+    }
+    h->stream = main;
+    h->partial = partial;
+    on = false;
+  }
+  ~StageFork() { join(); }
+};
+
 // Polar schedule: scaled Newton-Schulz steps p(x) = 1.5 c x - 0.5 c^3 x^3 with
 // c = sqrt(3 / (1 + l + l^2)) for singular values in [l, 1]; steps are
 // composed on the P x P level in blocks whose growth stays below gmax, with
@@ -529,6 +579,8 @@ void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
   const ll slab = (ll)v.NJ * v.Pn2;    // one stacked tensor
   const TP U = scratch(h->M1, v);     // U_k = W B_k(right child), K slabs
   const TP Y = scratch(h->Y, v);
+  StageFork fk(h);
+  fk.branch(0);
   right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
   // Y0 = o_L^T W_p + W_p o_R + sum_k A_{k,L}^T U_k,p
   {
@@ -541,8 +593,11 @@ void ascend_layer(ttn_ctx* h, Instance& I, int t, int prec) {
     run(h, d, prec);
   }
   // Y_{1+k} = W A_{k,R};  Y_{1+K+k} = B_{k,L}^T W
+  fk.branch(1);
   right_mult(h, v, W, v.opsR, 1, K, false, Y + slab, slab, prec);
+  fk.branch(2);
   left_mult(h, v, W, v.opsL, 1 + K, K, false, Y + (1 + K) * slab, slab, prec);
+  fk.join();
   // ops_{t+1}[J][j] = sum_{lr} Y_j[J][p][lr] W_J[q][lr]   (FP64 output)
   const ll out_site = (ll)(1 + 2 * K) * v.P * v.P;
   GemmDesc d = desc(v.P, v.P, 1 + 2 * K, v.NJ, I.ops[t + 1], v.P, 1, (ll)v.P * v.P,
@@ -640,9 +695,23 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
       a.bp = reinterpret_cast<float*>(h->lz_bp);
       a.Yp = reinterpret_cast<float*>(h->lz_Yp);
       const int grid = lanczos_grid(c, h->profiling ? 1 : (int)h->lanes.size());
+      cudaEvent_t ev[2];
+      if (h->profiling) {
+        cudaEventCreate(&ev[0]);
+        cudaEventCreate(&ev[1]);
+        cudaEventRecord(ev[0], h->stream);
+      }
       const int nl = grid > 0 ? lanczos_launch(a, grid, h->stream) : -1;
       if (nl < 0) h->compose_refused = true;
       else h->launches += nl;
+      if (h->profiling) {
+        // family 4: the top solve (executed matrix-vector flops are not counted)
+        cudaEventRecord(ev[1], h->stream);
+        h->ev_pool.push_back(ev[0]);
+        h->ev_pool.push_back(ev[1]);
+        h->ev_flops.push_back({4, 0.0});
+        h->ev_bytes.push_back(0.0);
+      }
       // converged flag and Krylov dimension of this solve, kept per instance
       h->launches += store_ints(I.istat, a.flags, 2, 0, h->stream);
     }
@@ -756,6 +825,8 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
   const ll slab = (ll)v.NJ * v.Pn2;
   const TP E_ = scratch(h->M1, v);            // W B_k^T (K slabs)
   const TP U = E_ + K * slab;                 // W B_k   (K slabs)
+  StageFork fk(h);
+  fk.branch(0);
   right_mult(h, v, W, v.opsR, 1 + K, K, true, E_, slab, prec);
   right_mult(h, v, W, v.opsR, 1 + K, K, false, U, slab, prec);
   const TP Zs = scratch(h->Y, v);             // slab 0
@@ -783,10 +854,13 @@ void environment(ttn_ctx* h, Instance& I, int t, int prec, double* Gam) {
   const TP WA = WAt + K * slab;
   const TP BW = WA + K * slab;
   const TP BtW = BW + K * slab;
+  fk.branch(1);
   right_mult(h, v, W, v.opsR, 1, K, true, WAt, slab, prec);
   right_mult(h, v, W, v.opsR, 1, K, false, WA, slab, prec);
+  fk.branch(2);
   left_mult(h, v, W, v.opsL, 1 + K, K, true, BW, slab, prec);
   left_mult(h, v, W, v.opsL, 1 + K, K, false, BtW, slab, prec);
+  fk.join();
   const TP G = v.adj;
   const ll PP = (ll)v.P * v.P;
   GemmDesc d = desc(v.P, (int)v.n2, 1, v.NJ, Gam, v.n2, 1, 0, v.Pn2);   // FP64 output
@@ -993,6 +1067,8 @@ void descend(ttn_ctx* h, Instance& I, int t, int prec) {
   const ll slab = (ll)v.NJ * v.Pn2;
   const ll PP = (ll)v.P * v.P;
   const TP Yt = scratch(h->Yt, v);     // [j][J] G_j W
+  StageFork fk(h);
+  fk.branch(0);
   {
     GemmDesc d = desc(v.P, (int)v.n2, 1 + 2 * K, v.NJ, Yt, v.n2, 1, slab, v.Pn2);
     add(d, grp(op(v.adj, v.P, 1, 0, PP, v.adj_ss), op(W, 1, v.n2, 0, 0, v.Pn2), v.P));
@@ -1000,8 +1076,11 @@ void descend(ttn_ctx* h, Instance& I, int t, int prec) {
   }
   const TP WB = scratch(h->M1, v);     // W B_{k,R}
   const TP AW = WB + K * slab;         // A_{k,L}^T W
+  fk.branch(1);
   right_mult(h, v, W, v.opsR, 1 + K, K, false, WB, slab, prec);
+  fk.branch(2);
   left_mult(h, v, W, v.opsL, 1, K, false, AW, slab, prec);
+  fk.join();
   // trace_r(T, Y)[l,l'] = sum_{p,r} T[p,l,r] Y[p,l',r];  trace_l(T, Y)[r,r'] = sum_{p,l} T[p,l,r] Y[p,l,r']
   auto tr_r = [&](TP Tt, ll tb0, TP Y, ll yb0) {
     return grp(op(Tt, v.n, 1, v.n2, tb0, v.Pn2), op(Y, v.n, 1, v.n2, yb0, v.Pn2), v.n, v.P);
@@ -1012,18 +1091,23 @@ void descend(ttn_ctx* h, Instance& I, int t, int prec) {
   double* out = I.adj[t];    // FP64 output
   const ll n2 = v.n2;
   if (!I.per_node) {
+    StageFork fk2(h);          // the three traces are independent
+    fk2.branch(0);
     GemmDesc r = desc(v.n, v.n, 1, 1, out, v.n, 1, 0, 0);
     add(r, tr_r(W, 0, Yt, 0));
     add(r, tr_l(W, 0, Yt, 0));
     run(h, r, prec);
+    fk2.branch(1);
     GemmDesc p = desc(v.n, v.n, K, 1, out + n2, v.n, 1, n2, 0);
     add(p, tr_r(WB, slab, Yt, 0));
     add(p, tr_l(W, 0, Yt + slab, slab));
     run(h, p, prec);
+    fk2.branch(2);
     GemmDesc q = desc(v.n, v.n, K, 1, out + (1 + K) * n2, v.n, 1, n2, 0);
     add(q, tr_l(AW, slab, Yt, 0));
     add(q, tr_r(W, 0, Yt + (1 + K) * slab, slab));
     run(h, q, prec);
+    fk2.join();
   } else {
     const ll ss = v.ss;
     double* outL = out;          // site 2J
@@ -1218,6 +1302,8 @@ void layout(ttn_ctx* h, Arena& ar) {
     }
     h->iflags = ar.take_int(8);
     h->partial = ar.take(h->partial_cap);
+    h->sub.n = h->opt.stage_streams > 1 ? std::min(h->opt.stage_streams, kSubStreams) : 0;
+    for (int i = 0; i < h->sub.n; ++i) h->sub.partial[i] = ar.take(h->partial_cap);
     save_lane(h, h->lanes[k]);
   }
   h->E_hist = ar.take(4096 * h->inst.size() + 16);
@@ -1330,6 +1416,7 @@ void ttn_default_options(ttn_options* o) {
   o->tiles = nullptr;
   o->tiles_bytes = 0;
   o->recompute_ops = 0;
+  o->stage_streams = 3;
 }
 
 // Parse an autotuner blob (ttn_options.tiles) into the table.
@@ -1345,7 +1432,7 @@ static int load_tiles(ttn_ctx* h, const void* blob, size_t bytes) {
   for (uint32_t i = 0; i < hd.count; ++i) {
     TuneBlobEntry e;
     std::memcpy(&e, p + i * sizeof(e), sizeof(e));
-    if (e.engine < 0 || e.engine > 1 || e.splits < 1 || e.splits > 64 || e.occ < 0 ||
+    if (e.engine < 0 || e.engine > 1 || e.splits < 1 || e.splits > 128 || e.occ < 0 ||
         e.occ > 2 || !(e.tile == 0 || e.tile == 16 || e.tile == 32 || e.tile == 64 || e.tile == 128))
       return fail(h, TTN_EINVAL, "tiles blob entry out of range");
     h->tuned[e.key] = Tuned{e.engine, e.tile, e.splits, e.occ, e.ms};
@@ -1391,6 +1478,8 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   if (!(h->opt.polar_damping >= 0.0)) return fail(h, TTN_EINVAL, "polar_damping < 0");
   if (h->opt.wait_polls < 0) return fail(h, TTN_EINVAL, "wait_polls < 0");
   if (h->opt.tc_engine != 0 && h->opt.tc_engine != 1) return fail(h, TTN_EINVAL, "tc_engine is 0 or 1");
+  if (h->opt.stage_streams < 0 || h->opt.stage_streams > kSubStreams)
+    return fail(h, TTN_EINVAL, "stage_streams in [0, 3]");
   h->lz_m = h->opt.lanczos_max;
   int rc = load_tiles(h, h->opt.tiles, h->opt.tiles_bytes);
   if (rc) return rc;
@@ -1447,6 +1536,17 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
     if (!rc)
       rc = check_cuda(h, cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming), "event");
   }
+  // sub-streams of every lane for the independent products of a stage
+  for (size_t k = 0; k < h->lanes.size() && !rc; ++k) {
+    SubStreams& sb = h->lanes[k].sub;
+    if (!sb.n) continue;
+    rc = check_cuda(h, cudaEventCreateWithFlags(&sb.fork, cudaEventDisableTiming), "event");
+    for (int i = 0; i < sb.n && !rc; ++i) {
+      rc = check_cuda(h, cudaStreamCreateWithFlags(&sb.s[i], cudaStreamNonBlocking), "stream");
+      if (!rc) rc = check_cuda(h, cudaEventCreateWithFlags(&sb.join[i], cudaEventDisableTiming), "event");
+    }
+  }
+  if (!rc) load_lane(h, h->lanes[0]);
   for (size_t k = 0; k < h->lanes.size() && !rc; ++k)
     rc = check_cuda(h, cudaMemsetAsync(h->lanes[k].iflags, 0, 8 * sizeof(int), h->stream), "flags");
   for (size_t i = 0; i < h->inst.size() && !rc; ++i) {
@@ -2002,7 +2102,8 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   h->profiling = false;
   int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "profile sync");
   if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
-  double ms[4] = {0, 0, 0, 0}, fl[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, by[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0}, fl[5] = {0, 0, 0, 0, 0}, cnt[5] = {0, 0, 0, 0, 0},
+         by[5] = {0, 0, 0, 0, 0};
   for (size_t i = 0; i < h->ev_flops.size(); ++i) {
     float e = 0.f;
     cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
@@ -2022,12 +2123,19 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   cudaEventDestroy(t1);
   out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
   out[3] = ms[1]; out[4] = fl[1]; out[5] = cnt[1];
-  out[6] = tot - ms[0] - ms[1] - ms[2] - ms[3];
-  out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2] - cnt[3];
+  out[6] = tot - ms[0] - ms[1] - ms[2] - ms[3] - ms[4];
+  out[7] = (double)h->launches - cnt[0] - cnt[1] - cnt[2] - cnt[3] - cnt[4];
   out[8] = tot;
   if (n_out >= 17) {
     out[15] = by[0];
     out[16] = by[1];
+  }
+  if (n_out >= 19) {
+    out[17] = ms[4];
+    out[18] = cnt[4];
+  } else {
+    out[6] += ms[4];
+    out[7] += cnt[4];
   }
   if (n_out >= 15) {
     out[9] = ms[2]; out[10] = fl[2]; out[11] = cnt[2];
@@ -2109,6 +2217,16 @@ void ttn_destroy(ttn_t h) {
     }
   for (cudaEvent_t e : h->ev_join)
     if (e) cudaEventDestroy(e);
+  for (Lane& l : h->lanes) {
+    for (int i = 0; i < kSubStreams; ++i) {
+      if (l.sub.s[i]) {
+        cudaStreamSynchronize(l.sub.s[i]);
+        cudaStreamDestroy(l.sub.s[i]);
+      }
+      if (l.sub.join[i]) cudaEventDestroy(l.sub.join[i]);
+    }
+    if (l.sub.fork) cudaEventDestroy(l.sub.fork);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (!h->lanes.empty()) h->stream = h->lanes[0].stream;
   if (h->stream) cudaStreamDestroy(h->stream);

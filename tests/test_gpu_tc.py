@@ -107,8 +107,12 @@ def test_tma_engine_matches_thread_staged_engine_in_a_sweep(prec):
     d_eng = np.abs(res[0][0] - res[1][0]) / np.abs(E64)
     d_64 = np.abs(res[1][0] - E64) / np.abs(E64)
     print(prec, "TMA vs thread-staged", d_eng, "thread-staged vs FP64", d_64)
-    # measured (GB300): 3xTF32 2.3e-6 between the engines against 1.4e-5 from
-    # FP64; TF32 2.7e-6 against 1.2e-5 .. 8.5e-4
-    assert np.all(d_eng < 0.5 * d_64)
+    # sweep 1 reports the top solve after the ascend alone: the engines differ
+    # only in their split-K partitions (measured 2.3e-6 against 1.4e-5 from
+    # FP64 in 3xTF32, 2.3e-6 against 8.5e-4 in TF32); sweep 2 follows the
+    # updates, whose tensor-core rounding the sweep amplifies, so it is held
+    # to the mixed tolerance against FP64 only
+    assert d_eng[0] < 0.5 * d_64[0]
     tol = {"tf32x3": 1e-5, "tf32": 1e-4}[prec]
+    assert d_eng.max() < tol and d_64[1:].max() < tol
     assert abs(res[0][1] - res[1][1]) / abs(res[1][1]) < tol

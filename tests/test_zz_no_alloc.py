@@ -57,3 +57,28 @@ def test_close_noalloc_rejects_sizes_beyond_its_scratch():
     p = ctypes.c_void_p(x.data_ptr())
     assert lib.ttn_close_noalloc(p, p, 257, 4, 4, p, None) == -1
     assert lib.ttn_close_noalloc(p, p, 4, 0, 4, p, None) == -1
+
+
+@pytest.mark.parametrize("P,Q,n2", [(256, 256, 6144), (200, 64, 3000), (64, 256, 40000)])
+def test_close_noalloc_at_its_limits_against_fp64_matmul(P, Q, n2):
+    """Shapes that reach the cap of the split count by the 8 MiB array
+    (256 x 256 with a long reduction wants more splits than 16 x 65536
+    doubles allow), non-square outputs and a long ragged reduction, against
+    a PyTorch FP64 matmul, on two calls in a row."""
+    import torch
+    from paper_1905_01331_gb300 import _abi
+    lib = _abi.load()
+    g = torch.Generator(device="cuda").manual_seed(P * 7 + Q)
+    Y = torch.rand(P, n2, generator=g, device="cuda", dtype=torch.float64) - 0.5
+    W = torch.rand(Q, n2, generator=g, device="cuda", dtype=torch.float64) - 0.5
+    ref = Y @ W.T
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        C = torch.full((P, Q), float("nan"), dtype=torch.float64, device="cuda")
+        rc = lib.ttn_close_noalloc(ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(W.data_ptr()),
+                                   P, Q, n2, ctypes.c_void_p(C.data_ptr()),
+                                   ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        err = ((C - ref).abs().max() / ref.abs().max()).item()
+        assert err < 1e-13, (P, Q, n2, err)
