@@ -60,6 +60,11 @@ def parse():
     p.add_argument("--quick", action="store_true", help="skip the 200-sweep energy-error runs")
     p.add_argument("--profile-sweeps", type=int, default=0,
                    help="only run this many eagerly launched sweeps (for an ncu launch list) and exit")
+    p.add_argument("--lanczos-tol", type=float, default=0.0,
+                   help="top-solve residual tolerance (0: the library's default for the precision)")
+    p.add_argument("--profile-start", type=int, default=0,
+                   help="with --profile-sweeps: sweeps run before the profiled ones, outside the "
+                        "cudaProfilerStart/Stop range (ncu --profile-from-start off)")
     p.add_argument("--workload", default="tfim1024",
                    choices=["tfim1024", "batched64", "paper-torus", "top-mode", "configs",
                             "polar-study"],
@@ -267,7 +272,7 @@ def run_gpu(args):
     chi = args.chi
     model = ti.tfim_chain(1024, 1.0)
     ws, V = ti.initial_tensors(1024, 2, chi, 1)
-    s = Sweeper(model, chi, prec=args.prec)
+    s = Sweeper(model, chi, prec=args.prec, lanczos_tol=args.lanczos_tol)
     s.set_isometries(0, ws, V)
     chis = s.chis(0)
     flops_per_sweep = ttn_flops.sweep_flops(1024, chis, 1, symmetric=True)
@@ -449,7 +454,8 @@ def run_gpu(args):
                   "fp64": {"sweeps": 200, "seconds": t_f, "E_fp64": E_ref,
                            "rel_err_vs_oracle_200": abs(E_ref - oracle_E) / abs(oracle_E) if oracle_E else None}}
         if args.prec != "fp64":
-            g = Sweeper(model, chi, prec=args.prec, tiles=tiles_blob or None)
+            g = Sweeper(model, chi, prec=args.prec, tiles=tiles_blob or None,
+                        lanczos_tol=args.lanczos_tol)
             g.set_isometries(0, ws, V)
             g.sweep(1)
             done, secs, reached, E200 = 1, 0.0, None, None
@@ -506,16 +512,28 @@ def run_profile_only(args):
     model = ti.tfim_chain(1024, 1.0)
     ws, V = ti.initial_tensors(1024, 2, args.chi, 1)
     tiles = open(args.tiles_file, "rb").read() if args.tiles_file else None
-    s = Sweeper(model, args.chi, prec=args.prec, use_graph=False, tiles=tiles)
+    s = Sweeper(model, args.chi, prec=args.prec, use_graph=False, tiles=tiles,
+                lanczos_tol=args.lanczos_tol)
     s.set_isometries(0, ws, V)
     if tiles is None and not args.no_autotune:
         # the configurations the bench times (the tuning sweep is the first of the list)
-        s.autotune(reps=3)
+        blob = s.autotune(reps=3)
         s.set_isometries(0, ws, V)
+        if args.save_tiles and blob:
+            # a later run under ncu loads this table: timings taken under the
+            # profiler would choose other configurations
+            with open(args.save_tiles, "wb") as f:
+                f.write(blob)
+    if args.profile_start:
+        s.sweep(args.profile_start)     # towards the steady state the bench times
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     E = s.sweep(args.profile_sweeps)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_sweeps": args.profile_sweeps, "prec": args.prec,
-                      "energies": E[:, 0].tolist(), "launches": s.launch_count}))
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_sweeps": args.profile_sweeps, "profile_start": args.profile_start,
+                      "prec": args.prec, "energies": E[:, 0].tolist(),
+                      "launches_per_sweep": s.launch_count / max(1, args.profile_sweeps)}))
     s.close()
 
 

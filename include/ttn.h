@@ -84,7 +84,9 @@ typedef struct {
                                factor of v's environment, the literal reading
                                of "updated similarly", Sec. III.B) */
   double lanczos_tol;       /* residual |Hv - Ev| <= tol * |E|; 0 (default): 1e-13 in
-                               FP64 mode, 1e-10 in the mixed modes */
+                               FP64 mode, 1e-8 in the mixed modes (whose top
+                               operators carry 1e-6 to 3e-5 of tensor-core
+                               rounding) */
   int lanczos_max;          /* Krylov dimension per restart (default 48) */
   int lanczos_restarts;     /* restarts per sweep (default 3) */
   double shift;             /* bond shift c; NaN = lambda_max of the bond term */
@@ -103,7 +105,17 @@ typedef struct {
                                fresh Gram matrix every <= 4 steps (accurate to
                                FP64 rounding), 2 = two long blocks (one Gram
                                matrix per ~1e5 of growth: half the FP64 work),
-                               0 (default) = 1 in FP64 mode, 2 in mixed modes */
+                               0 (default) = 1 in FP64 mode; in the mixed modes
+                               1 for layers with chi_{t+1} < 32 and otherwise
+                               an adaptive double-float schedule: block 1
+                               converges every singular value above 1e-5 of
+                               |X|_F; when it leaves max |X X^T - I| <= 1e-9,
+                               block 2 becomes one Newton-Schulz step and the
+                               final step is skipped (decided on the device),
+                               else block 2 covers the worst case down to
+                               min(mu / 4, 1e-10) and the final step runs;
+                               3 = as 0 with the fixed double-float schedule
+                               (two long blocks and the final step always) */
   int double_float;         /* mixed modes, 1 (default): the polar factor's products
                                (Gram matrices, composition, apply, plus one final
                                Newton-Schulz step: isometry to ~1e-14) and the
@@ -209,7 +221,9 @@ int ttn_sweep_until(ttn_t h, double tol, int max_sweeps, int* n_done, double* ho
  * the last sweep's top solve met its tolerance, else 0; out[6] = the Krylov
  * dimension of its last cycle; with n_out >= 8, out[7] = 1 if a polar factor
  * of the last sweep (mixed modes) was left more than 1e-5 from an isometry by
- * its Newton-Schulz blocks, else 0.  n_out >= 7.  Overwrites the context's
+ * its Newton-Schulz blocks, else 0; with n_out >= 9, out[8] = the number of
+ * isometry layers whose polar factor took the adaptive schedule's short path
+ * in the last sweep (ttn_options.polar_blocks).  n_out >= 7.  Overwrites the context's
  * density matrices (a sweep recomputes them). */
 int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out);
 
@@ -291,7 +305,10 @@ int ttn_selftest_gemm(void* d_ws, size_t bytes, int prec, double* out_rel, int n
  * operands: Gram X X^T for (P, n2) = (128, 16384) and (96, 1000), apply F X
  * for (128, 16384) and (40, 1000).  d_ws: caller device memory of at least
  * ttn_selftest_bytes(); out_rel[i] = max |C_df - C_fp64| / max |C_fp64|
- * (n_out >= 4). */
+ * (n_out >= 4); with n_out >= 5, out_rel[4] the Newton-Schulz step near
+ * convergence that the adaptive polar schedule uses, (1.5 I - 0.5 A) X for A
+ * within 1e-10 of I (P = 128, n2 = 16384), against the same product in
+ * FP64. */
 int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_out, void* stream);
 
 /* Allocation-free close product, for callers that cannot allocate device

@@ -100,6 +100,9 @@ int set_identity(double* F, int P, int nb, cudaStream_t s);
 
 // y = alpha * x + beta * y over n elements.
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s);
+// y = alpha * (*sel ? x1 : x0) over n elements (sel on the device).
+int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
+                 double alpha, cudaStream_t s);
 
 // Symmetrise P x P blocks in place: A = (A + A^T) / 2.
 int symmetrize(double* A, int P, int nb, cudaStream_t s);
@@ -151,9 +154,12 @@ struct ComposeArgs {
   int* err;
   int grid_share;   // concurrent streams sharing the GPU: the grid takes 1/grid_share of it
   int max_spin;     // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
+  // double-float kernel only (may be null): when *shortcut is 0 the kernel
+  // returns at once (the block is then one Newton-Schulz step, ns_correction)
+  const int* shortcut = nullptr;
 };
 bool compose_supported(int P, int nsteps);
-// FP64 flops the composition kernel executes (symmetric tiles only).
+// Flops the composition kernel executes (all tiles of every product).
 double compose_flops(int P, int NJ, int nsteps);
 // Returns the number of kernel launches (1), or -1 if the launch was refused.
 // df: the five buffers hold FP32 pairs (hi at p, lo at p + P*P floats; block b
@@ -219,11 +225,18 @@ int df_gram_splits(int P, int n2);
 // Multiply-adds x 2 of the tiles df_gram computes (upper triangle only).
 double df_gram_flops(int P, long long n2);
 // C (P x P, FP64) = X X^T for X (P x n2, row-major) given as (Xh, Xl).
+// run_if (device, may be null): when it points to 0 the launches return at once.
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-            cudaStream_t s);
+            cudaStream_t s, const int* run_if = nullptr);
 // C (P x n2, FP64) = F X for F (P x P) given as (Fh, Fl) and X as (Xh, Xl).
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-             long long n2, double* C, cudaStream_t s);
+             long long n2, double* C, cudaStream_t s, const int* run_if = nullptr);
+// C (P x n2) = (1.5 I - 0.5 A) X for A (P x P, as an FP32 pair: hi at A, lo
+// at A + P*P) within 1e-9 of I elementwise: C = X + 0.5 (I - A) X with the
+// correction product in FP32 on X's FP32 head Xh.  Runs only when *full
+// (device) is 0.
+int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
+                  double* C, const int* full, cudaStream_t s);
 
 // dst[i] = (float) src[i]
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s);

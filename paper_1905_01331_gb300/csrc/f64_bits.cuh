@@ -1,4 +1,4 @@
-// FP64 -> FP32 conversions from the IEEE-754 fields with integer operations.
+// FP64 <-> FP32 conversions from the IEEE-754 fields with integer operations.
 // On this GPU FP64 arithmetic and conversions run on two FP64 units per SM;
 // the streams of conversions of the mixed modes (FP32 copies of tensors,
 // FP32 pairs of the double-float products) would be bound by them.  Here the
@@ -35,6 +35,24 @@ F64B_HD float f_from_bits(uint32_t u) {
 #else
   float x;
   std::memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+F64B_HD uint32_t f_bits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+F64B_HD double d_from_bits(uint64_t u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(static_cast<long long>(u));
+#else
+  double x;
+  std::memcpy(&x, &u, 8);
   return x;
 #endif
 }
@@ -90,6 +108,21 @@ F64B_HD float to_f32(double x) {
   const uint32_t rem = static_cast<uint32_t>(m & 0x1FFFFFFFu);
   if (rem > (1u << 28) || (rem == (1u << 28) && (q & 1u))) ++q;
   return f_from_bits(sign | (((e - 896u) << 23) + (q - (1u << 23))));
+}
+
+// (double) x for an FP32 x from the IEEE-754 fields (sign, exponent rebiased
+// by 1023 - 127 = 896, mantissa shifted up by 29 bits) with integer
+// operations.  Zeros keep their sign; subnormal, infinite and NaN inputs take
+// the converting instruction.
+F64B_HD double from_f32(float x) {
+  const uint32_t b = f_bits(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((b & 0x7FFFFFFFu) == 0u) return d_from_bits(static_cast<uint64_t>(b & 0x80000000u) << 32);
+    return static_cast<double>(x);
+  }
+  const uint64_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return d_from_bits((hi << 32) | static_cast<uint64_t>(b << 29));
 }
 
 }  // namespace f64b

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "f64_bits.cuh"
 #include "pair_arith.cuh"
 
 namespace ttn {
@@ -66,7 +67,8 @@ template <int BM, int BN, int TM, int TN, bool kBKmajor, int MB>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     const float* __restrict__ Ah, const float* __restrict__ Al, long long lda,
     const float* __restrict__ Bh, const float* __restrict__ Bl, long long ldb, int M, int N, int K,
-    double* C, long long ldc, double* part, int splits, int sym) {
+    double* C, long long ldc, double* part, int splits, int sym, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   constexpr int TX = BN / TN, NT = (BM / TM) * TX;
   constexpr int LA = BM * kDBK / NT, LB = BN * kDBK / NT;
   static_assert(BM * kDBK % NT == 0 && BN * kDBK % NT == 0, "staging split");
@@ -181,7 +183,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
 // C[m][n] = sum_s part[s][m][n] in split order; for a symmetric product the
 // tiles below the diagonal were not computed and are read from the mirror.
 __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, int tile, int sym,
-                                 double* C, long long ldc) {
+                                 double* C, long long ldc, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   const long long MN = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
        e += (long long)gridDim.x * blockDim.x) {
@@ -195,6 +198,76 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
 
 int grid_n(long long n) { return (int)std::min<long long>((n + 255) / 256, 2048); }
 
+// One Newton-Schulz step near convergence, C = (1.5 I - 0.5 A) X = X + D X with
+// D = 0.5 (I - A), for A = X X^T within 1e-9 of I elementwise (the adaptive
+// polar schedule's short path).  |D| <= 5e-10 elementwise, so D X needs only
+// FP32 accuracy: D is formed in FP32 from A's pair (Ah, Al), X enters as its
+// FP32 head Xh, the product accumulates in FP32 (one FMA per multiply-add
+// against the pair product's twelve), and the epilogue adds the FP64 X (one
+// FP64 add per element; the FP32 -> FP64 conversion is integer, f64_bits.cuh).
+// BM x BN output tile per CTA, TM x TN per thread, K (= P) in tiles of kDBK.
+// Runs only when *full is 0.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) ns_correction_kernel(
+    const float* __restrict__ Ah, const float* __restrict__ Al, const double* __restrict__ X,
+    const float* __restrict__ Xh, int P, long long n2, double* __restrict__ C, const int* full) {
+  if (*full != 0) return;
+  constexpr int TX = BN / TN, NT = (BM / TM) * TX;
+  static_assert(BM * kDBK % NT == 0 && BN * kDBK % NT == 0, "staging split");
+  __shared__ __align__(16) float sD[kDBK][BM + 4], sX[kDBK][BN + 4];
+  const long long tiles_n = (n2 + BN - 1) / BN;
+  const int m0 = (int)(blockIdx.x / tiles_n) * BM;
+  const long long n0 = (blockIdx.x % tiles_n) * BN;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < P; k0 += kDBK) {
+#pragma unroll
+    for (int i = 0; i < BM * kDBK / NT; ++i) {
+      const int e = threadIdx.x + i * NT;
+      const int m = m0 + e / kDBK, k = k0 + e % kDBK;
+      float d = 0.f;
+      if (m < P && k < P) {
+        const long long a = (long long)m * P + k;
+        d = 0.5f * ((m == k ? 1.f : 0.f) - Ah[a]) - 0.5f * Al[a];
+      }
+      sD[e % kDBK][e / kDBK] = d;
+    }
+#pragma unroll
+    for (int i = 0; i < BN * kDBK / NT; ++i) {
+      const int e = threadIdx.x + i * NT;
+      const int k = k0 + e / BN;
+      const long long n = n0 + e % BN;
+      sX[e / BN][e % BN] = (k < P && n < n2) ? Xh[(long long)k * n2 + n] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kDBK; ++kk) {
+      float a[TM], b[TN];
+      lds_frag<TM>(&sD[kk][ty * TM], a);
+      lds_frag<TN>(&sX[kk][tx * TN], b);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty * TM + i;
+    if (m >= P) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const long long n = n0 + tx * TN + j;
+      if (n < n2) C[(long long)m * n2 + n] = X[(long long)m * n2 + n] + f64b::from_f32(acc[i][j]);
+    }
+  }
+}
+
 // Gram tiles of GB x GB (GT x GT per thread), the K range cut so that about
 // `target` CTAs run.
 int gram_splits(int P, int n2, int GB, int target) {
@@ -206,14 +279,15 @@ int gram_splits(int P, int n2, int GB, int target) {
 
 template <int GB, int GT, int MB>
 int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-                int splits, cudaStream_t s) {
+                int splits, cudaStream_t s, const int* run_if) {
   const int nt = (P + GB - 1) / GB;
   dim3 grid(nt * (nt + 1) / 2, 1, splits);
   gemm_df_kernel<GB, GB, GT, GT, true, MB><<<grid, (GB / GT) * (GB / GT), 0, s>>>(
-      Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1);
+      Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1, run_if);
   int launches = 1;
   if (splits > 1) {
-    df_reduce_kernel<<<grid_n((long long)P * P), 256, 0, s>>>(part, splits, P, P, GB, 1, C, P);
+    df_reduce_kernel<<<grid_n((long long)P * P), 256, 0, s>>>(part, splits, P, P, GB, 1, C, P,
+                                                             run_if);
     ++launches;
   }
   return launches;
@@ -221,10 +295,10 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
 
 template <int BM, int BN, int TM, int TN, int MB>
 int apply_launch(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-                 long long n2, double* C, cudaStream_t s) {
+                 long long n2, double* C, cudaStream_t s, const int* run_if) {
   const int tn = (int)((n2 + BN - 1) / BN), tm = (P + BM - 1) / BM;
   gemm_df_kernel<BM, BN, TM, TN, false, MB><<<tm * tn, (BM / TM) * (BN / TN), 0, s>>>(
-      Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0);
+      Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0, run_if);
   return 1;
 }
 
@@ -245,13 +319,25 @@ double df_gram_flops(int P, long long n2) {
 }
 
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-            cudaStream_t s) {
-  return gram_launch<kGramB, kGramT, 2>(Xh, Xl, P, n2, C, part, df_gram_splits(P, (int)n2), s);
+            cudaStream_t s, const int* run_if) {
+  return gram_launch<kGramB, kGramT, 2>(Xh, Xl, P, n2, C, part, df_gram_splits(P, (int)n2), s,
+                                        run_if);
 }
 
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-             long long n2, double* C, cudaStream_t s) {
-  return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s);
+             long long n2, double* C, cudaStream_t s, const int* run_if) {
+  return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s, run_if);
 }
+
+int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
+                  double* C, const int* full, cudaStream_t s) {
+  constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
+  const long long tiles = (long long)((P + BM - 1) / BM) * ((n2 + BN - 1) / BN);
+  ns_correction_kernel<BM, BN, TM, TN><<<(unsigned)tiles, (BM / TM) * (BN / TN), 0, s>>>(
+      A, A + (long long)P * P, X, Xh, P, n2, C, full);
+  return 1;
+}
+
+
 
 }  // namespace ttn

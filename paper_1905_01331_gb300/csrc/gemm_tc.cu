@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "f64_bits.cuh"
 
 namespace ttn {
 
@@ -395,21 +396,9 @@ __device__ __forceinline__ void store_f32(int path, const float* v, uint8_t* hi_
   }
 }
 
-// FP32 -> FP64 from the IEEE-754 fields (sign, exponent rebiased by
-// 1023 - 127 = 896, mantissa shifted up by 29 bits) with integer operations:
-// on this GPU the FP64 pipe (two operations per SM per clock) would bound
-// the epilogue of a tile.  Zeros keep their sign; subnormal, infinite and NaN
-// inputs take the converting instruction.
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) {
-    if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double(static_cast<int>(b & 0x80000000u), 0);
-    return static_cast<double>(x);
-  }
-  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
-}
+// FP32 -> FP64 with integer operations (f64_bits.cuh): on this GPU the FP64
+// pipe (two operations per SM per clock) would bound the epilogue of a tile.
+__device__ __forceinline__ double f32_to_f64(float x) { return f64b::from_f32(x); }
 
 // C = alpha x + beta C for one FP32 accumulator x.  With beta = 0 the scaling
 // is an FP32 multiply (exact for alpha = +-1 or a power of two; otherwise one

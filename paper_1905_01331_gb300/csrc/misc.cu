@@ -96,6 +96,14 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
     y[i] = alpha * x[i] + beta * y[i];
 }
 
+__global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
+                                    long long n, double alpha) {
+  const double* x = *sel ? x1 : x0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = alpha * x[i];
+}
+
 __global__ void symmetrize_kernel(double* A, int P) {
   const int b = blockIdx.y;
   double* a = A + (long long)b * P * P;
@@ -472,6 +480,12 @@ int set_identity(double* F, int P, int nb, cudaStream_t s) {
 
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s) {
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, alpha, beta);
+  return 1;
+}
+
+int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
+                 double alpha, cudaStream_t s) {
+  scale_select_kernel<<<grid_for(n), 256, 0, s>>>(x0, x1, sel, y, n, alpha);
   return 1;
 }
 

@@ -12,8 +12,11 @@
 // on full tiles.  A_j is read symmetrised, (A + A^T)/2, and Pm_j is formed from
 // it while the operands are staged.  In exact arithmetic every matrix here is
 // a polynomial in A_0 and symmetric; in rounding the products are not, and
-// keeping only one triangle of them (half the work) cost up to 20x in the
-// isometry defect of long blocks, so the full products are kept.
+// keeping only one triangle of them (half the work: the upper tiles computed
+// and mirrored) cost up to 20x in the isometry defect of long FP64 blocks and
+// ~1000x for a 14-step block in a float64 emulation of the double-float
+// kernel (whose long blocks then left the stable interval and diverged), so
+// the full products are kept.
 //
 // The products are small (P <= 256) and FP64, which on this GPU runs at two
 // DFMA per clock per SM: a separate launch per product leaves most SMs idle and
@@ -327,6 +330,10 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
   float* F = reinterpret_cast<float*>(a.F);
   float* S = reinterpret_cast<float*>(a.S);
   float* T = reinterpret_cast<float*>(a.T);
+  // the previous block already left X X^T within its threshold of I: the
+  // block is one Newton-Schulz step, applied by ns_correction instead (every
+  // CTA reads the same flag, so none reaches a grid barrier)
+  if (a.shortcut && *a.shortcut == 0) return;
   auto Fbuf = [&](int j) { return ((ns - j) & 1) ? S : F; };
   unsigned target = 0;
   for (int j = 0; j < ns; ++j) {

@@ -23,6 +23,14 @@ __global__ void fill_uniform(double* x, long long n, unsigned long long seed) {
   }
 }
 
+// A = I + eps (F + F^T) / 2 for F (P x P) with entries in [-1, 1).
+__global__ void near_identity(const double* F, double* A, int P, double eps) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P * P; e += gridDim.x * blockDim.x) {
+    const int i = e / P, j = e % P;
+    A[e] = (i == j ? 1.0 : 0.0) + eps * 0.5 * (F[(long long)i * P + j] + F[(long long)j * P + i]);
+  }
+}
+
 __global__ void max_abs_diff(const double* a, const double* b, long long n, double* out) {
   __shared__ double sd[256], sm[256];
   double d = 0.0, m = 0.0;
@@ -244,7 +252,10 @@ extern "C" size_t ttn_selftest_bytes(void) {
 // Diagnostic: the double-float Gram and apply products of the polar factor
 // (gemm_df.cu) against the FP64 engine on seeded operands.  Cases: Gram X X^T
 // for (P, n2) = (128, 16384) (split K) and (96, 1000) (ragged); apply F X for
-// (128, 16384) and (40, 1000).  out_rel[i] = max |C_df - C_fp64| / max |C_fp64|.
+// (128, 16384) and (40, 1000); with n_out >= 5, out_rel[4] the Newton-Schulz
+// step near convergence (ns_correction, A = I + 1e-10 (F + F^T) / 2, P = 128,
+// n2 = 16384) against (1.5 I - 0.5 A) X in FP64.
+// out_rel[i] = max |C_df - C_fp64| / max |C_fp64|.
 extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_out,
                                void* stream) {
   if (!d_ws || !out_rel || n_out < 4) return TTN_EINVAL;
@@ -267,6 +278,9 @@ extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_
   double* C2 = take(big);
   double* partial = take(128 * 128 * 128);
   double* res = take(4);
+  double* Aq = take(128 * 128);
+  double* Fm = take(128 * 128);
+  int* zero = reinterpret_cast<int*>(take(1));
   if (off > cap) return TTN_ENOMEM;
   fill_uniform<<<592, 256, 0, s>>>(X, big, 31);
   fill_uniform<<<64, 256, 0, s>>>(F, 128 * 128, 37);
@@ -274,14 +288,15 @@ extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_
   const Case cases[4] = {{1, 128, 16384}, {1, 96, 1000}, {0, 128, 16384}, {0, 40, 1000}};
   std::vector<double> host(2);
   for (int i = 0; i < 4; ++i) {
-    const int P = cases[i].P;
-    const long long n2 = cases[i].n2, PN = (long long)P * n2;
+    const Case& cs = cases[i];
+    const int P = cs.P;
+    const long long n2 = cs.n2, PN = (long long)P * n2;
     df_split(X, Xp, Xp + PN, PN, s);
     GemmDesc r;
     memset(&r, 0, sizeof(r));
     r.B0 = 1; r.B1 = 1; r.alpha = 1.0; r.prec = 0; r.C = C1; r.sc_n = 1; r.partial = partial;
     long long celems;
-    if (cases[i].gram) {
+    if (cs.gram) {
       r.M = P; r.N = P; r.sc_m = P;
       Group g;
       g.a = mk(X, n2, 1); g.b = mk(X, n2, 1); g.K = (int)n2; g.k0_log2 = 0;
@@ -306,6 +321,30 @@ extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_
     cudaMemcpyAsync(host.data(), res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return TTN_ECUDA;
     out_rel[i] = host[0] / std::max(host[1], 1e-300);
+  }
+  if (n_out >= 5) {
+    const int P = 128;
+    const long long n2 = 16384, PN = (long long)P * n2;
+    near_identity<<<64, 256, 0, s>>>(F, Aq, P, 1e-10);
+    poly_step_matrix(Aq, Fm, P, 1, 1.5, 0.5, s);   // 1.5 I - 0.5 A
+    cudaMemsetAsync(zero, 0, sizeof(int), s);
+    GemmDesc r;
+    memset(&r, 0, sizeof(r));
+    r.B0 = 1; r.B1 = 1; r.alpha = 1.0; r.prec = 0; r.C = C1; r.sc_n = 1; r.partial = partial;
+    r.M = P; r.N = (int)n2; r.sc_m = n2;
+    Group g;
+    g.a = mk(Fm, P, 1); g.b = mk(X, 1, n2); g.K = P; g.k0_log2 = 0;
+    g.a.s_k1 = 1; g.b.s_k1 = n2;
+    r.g[r.ngroups++] = g;
+    r.splits = 1;
+    gemm_launch(r, s);
+    df_split(X, Xp, Xp + PN, PN, s);
+    df_split(Aq, Fp, Fp + (long long)P * P, (long long)P * P, s);
+    ns_correction(Fp, X, Xp, P, n2, C2, zero, s);
+    max_abs_diff<<<1, 256, 0, s>>>(C2, C1, (long long)P * n2, res);
+    cudaMemcpyAsync(host.data(), res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TTN_ECUDA;
+    out_rel[4] = host[0] / std::max(host[1], 1e-300);
   }
   return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ECUDA;
 }

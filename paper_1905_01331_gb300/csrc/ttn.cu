@@ -82,6 +82,9 @@ struct Instance {
   // sweep missed an isometry, 3 unused]
   double* dstat = nullptr;
   int* istat = nullptr;
+  // per isometry layer (mixed modes, adaptive polar schedule): 1 = the second
+  // block ran in full and the final step ran, 0 = both were cut short
+  int* pfull = nullptr;
   // Identity part of the one-site operators, kept exactly in FP64: the true
   // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
   std::vector<double*> eoff;
@@ -189,6 +192,10 @@ struct ttn_ctx {
   int lz_m = 48;
   double* E_hist = nullptr;    // device energies of the current ttn_sweep call
   std::vector<PolarBlock> polar_f64, polar_tc;
+  // mixed modes, adaptive: a first block that converges every singular value
+  // above kPolarTry, then either one Newton-Schulz step (when the first block
+  // left an isometry) or a block for the worst case; empty if not applicable
+  std::vector<PolarBlock> polar_adapt;
   bool measuring = false;      // plan pass: only size the partial buffer
   // plan pass over a fake base address: every operand's address range is
   // checked against the buffer it points into (no launch happens)
@@ -202,6 +209,7 @@ struct ttn_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, double>> ev_flops;   // (engine, flops) per event pair
+  std::vector<const int*> ev_cond;   // per event pair: flops count only if *cond != 0
   std::vector<double> ev_bytes;                   // algorithmic bytes per event pair
 };
 
@@ -446,6 +454,7 @@ void run(ttn_ctx* h, GemmDesc d, int prec) {
       bytes += (double)d.M * G.K * ba * (G.a.f32 ? 4 : 8) + (double)d.N * G.K * bb * (G.b.f32 ? 4 : 8);
     }
     h->ev_bytes.push_back(bytes);
+    h->ev_cond.push_back(nullptr);
     return;
   }
   h->launches += gemm_launch(d, h->stream);
@@ -491,6 +500,17 @@ struct StageFork {
 // c = sqrt(3 / (1 + l + l^2)) for singular values in [l, 1]; steps are
 // composed on the P x P level in blocks whose growth stays below gmax, with
 // a fresh Gram matrix at the start of every block.
+// Adaptive schedule of the mixed modes: singular values (of X scaled to unit
+// Frobenius norm) above kPolarTry converge in the first block; the second is
+// cut to one step when max |X X^T - I| <= kPolarNear after it (one step then
+// leaves a defect of at most ~0.75 (P kPolarNear)^2, ~1e-14 for P = 128).
+// With kPolarTry = 1e-5 the worst case left for the second block needs a
+// growth of 1.5e4 (17 + 15 steps); with 1e-4 it needed 1.9e5 in one block,
+// whose rounding (48-bit emulation: 1e-12 to 5e-12; on the GPU 2e-11) the
+// final step no longer removed.
+constexpr double kPolarTry = 1e-5;
+constexpr double kPolarNear = 1e-9;
+
 std::vector<PolarBlock> polar_schedule(double l0, double gmax, double final_tol, int max_block) {
   std::vector<PolarBlock> out;
   double l = l0;
@@ -646,12 +666,14 @@ void top_matvec(ttn_ctx* h, Instance& I, const double* x, double* w, const int* 
 }
 
 // Residual tolerance of the top solve: the option, or by default 1e-13 in
-// FP64 mode and 1e-10 in the mixed modes, whose top operators carry the
+// FP64 mode and 1e-8 in the mixed modes, whose top operators carry the
 // tensor-core rounding of the ascended layers (1e-6 to 3e-5 relative): a
-// tighter solve of that operator would not move the state further.
+// tighter solve of that operator would not move the state further (the
+// residual is still two orders below the operator's own rounding; the energy
+// error of the solve is quadratic in it).
 double lanczos_tolerance(const ttn_ctx* h) {
   if (h->opt.lanczos_tol > 0.0) return h->opt.lanczos_tol;
-  return h->opt.prec == 0 ? 1e-13 : 1e-10;
+  return h->opt.prec == 0 ? 1e-13 : 1e-8;
 }
 
 void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
@@ -711,6 +733,7 @@ void top_solve(ttn_ctx* h, Instance& I, double* energy_out) {
         h->ev_pool.push_back(ev[1]);
         h->ev_flops.push_back({4, 0.0});
         h->ev_bytes.push_back(0.0);
+        h->ev_cond.push_back(nullptr);
       }
       // converged flag and Krylov dimension of this solve, kept per instance
       h->launches += store_ints(I.istat, a.flags, 2, 0, h->stream);
@@ -887,7 +910,7 @@ void df_begin(ttn_ctx* h) {
   cudaEventRecord(e, h->stream);
   h->ev_pool.push_back(e);
 }
-void df_end(ttn_ctx* h, int launches, double flops) {
+void df_end(ttn_ctx* h, int launches, double flops, const int* cond = nullptr) {
   h->launches += launches;
   if (!h->profiling) return;
   cudaEvent_t e;
@@ -896,11 +919,15 @@ void df_end(ttn_ctx* h, int launches, double flops) {
   h->ev_pool.push_back(e);
   h->ev_flops.push_back({2, flops});
   h->ev_bytes.push_back(0.0);
+  h->ev_cond.push_back(cond);
 }
 
 // F = composed polynomial of one block from the Gram matrix in pA (one
-// cooperative launch; pA, pP, pT, pS are overwritten).
-void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
+// cooperative launch; pA, pP, pT, pS are overwritten).  shortcut (double-float
+// only, device, may be null): when it holds 0 the block is one Newton-Schulz
+// step instead.
+void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df,
+                   const int* shortcut = nullptr) {
   ComposeArgs a;
   // double-float: A_0 arrives as pairs in pP (split from the FP64 Gram in pA)
   a.A0 = df ? h->pP : h->pA; a.A1 = df ? h->pA : h->pP;
@@ -914,6 +941,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
   a.err = h->iflags + 4;
   a.max_spin = h->opt.wait_polls;
   a.grid_share = h->profiling ? 1 : (int)h->lanes.size();
+  a.shortcut = df ? shortcut : nullptr;
   cudaEvent_t ev[2];
   if (h->profiling) {
     cudaEventCreate(&ev[0]);
@@ -933,6 +961,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df) {
     h->ev_pool.push_back(ev[1]);
     h->ev_flops.push_back({df ? 3 : 0, compose_flops(P, NJ, a.nsteps)});
     h->ev_bytes.push_back(0.0);
+    h->ev_cond.push_back(a.shortcut);
   }
 }
 
@@ -955,18 +984,33 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // for the double-float products (P < 32, negligible cost): short blocks (at
   // most four composed steps per Gram matrix) for full accuracy; mixed modes
   // otherwise: two Gram matrices and two long compositions, then one more
-  // Newton-Schulz step.
-  const bool short_blocks =
-      h->opt.polar_blocks == 1 || (h->opt.polar_blocks == 0 && (prec == 0 || P < 32));
-  const std::vector<PolarBlock>& sched = short_blocks ? h->polar_f64 : h->polar_tc;
+  // Newton-Schulz step (adaptive: the second composition and the final step
+  // become one Newton-Schulz step when the first block already converged).
+  const int pb = h->opt.polar_blocks;
+  const bool short_blocks = pb == 1 || ((pb == 0 || pb == 3) && (prec == 0 || P < 32));
+  const std::vector<PolarBlock>* schedp = short_blocks ? &h->polar_f64 : &h->polar_tc;
   // Mixed modes: every block's Gram and apply products in double-float
   // arithmetic on the FP32 pipes (~48 bits: the rounding amplified by a
   // block's growth stays far below the tensor-core rounding of the
   // environment), then one more Newton-Schulz step X <- (1.5 I - 0.5 X X^T) X
   // that takes the isometry defect from ~1e-11 to ~1e-14.  Operands in FP32
   // pairs: X in the one-leg scratch Y, F in Yt (both free during the polar
-  // step).
-  const bool df_ok = prec != 0 && h->opt.double_float && NJ == 1 && P >= 32 && sched.size() > 1;
+  // step).  (Splitting X while the products load it instead of in a separate
+  // pass was measured slower: the products are issue-bound and the Gram
+  // product would split every element four to five times.)
+  const bool df_ok = prec != 0 && h->opt.double_float && NJ == 1 && P >= 32 && schedp->size() > 1;
+  // Adaptive schedule (polar_blocks 0 in the mixed modes, double-float
+  // composition kernel): block 2 and the final step are cut short on the
+  // device when block 1 already left an isometry (flag pfull[t] = 0).
+  const bool adaptive =
+      df_ok && !short_blocks && pb == 0 && h->polar_adapt.size() == 2 && (h->opt.persistent & 1) &&
+      compose_supported(P, (int)h->polar_adapt[0].steps.size()) &&
+      compose_supported(P, (int)h->polar_adapt[1].steps.size());
+  if (adaptive) schedp = &h->polar_adapt;
+  const std::vector<PolarBlock>& sched = *schedp;
+  int* full = I.pfull + t;
+  if (df_ok && !h->measuring && !adaptive)
+    h->launches += store_ints(full, nullptr, 1, 1, h->stream);
   float* Xh = reinterpret_cast<float*>(h->Y);
   float* Xl = Xh + PN;
   float* Fh = reinterpret_cast<float*>(h->Yt);
@@ -979,8 +1023,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     if (df) {
       h->launches += df_split(X, Xh, Xl, PN, h->stream);
       df_begin(h);
-      df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
-             df_gram_flops(P, N));
+      df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream), df_gram_flops(P, N));
+      if (adaptive && bi + 1 == sched.size()) {
+        // far (1): the last block and the final step run in full
+        h->launches += store_ints(full, nullptr, 1, 0, h->stream);
+        h->launches += flag_if_far_from_identity(h->pA, P, kPolarNear, full, h->stream);
+      }
     } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
@@ -992,7 +1040,8 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     if (kernel) {
       if (df) h->launches += df_split(h->pA, reinterpret_cast<float*>(h->pP),
                                       reinterpret_cast<float*>(h->pP) + PP, PP, h->stream);
-      if (!h->measuring) compose_block(h, blk, P, NJ, df);
+      if (!h->measuring)
+        compose_block(h, blk, P, NJ, df, adaptive && bi + 1 == sched.size() ? full : nullptr);
     } else {
     if (!h->measuring) h->launches += set_identity(h->pF, P, NJ, h->stream);
     for (size_t j = 0; j < blk.steps.size(); ++j) {
@@ -1029,8 +1078,15 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
         Fah = Fh;
         Fal = Fl;
       }
+      // the adaptive schedule's last block: the composed F (full == 1) or one
+      // Newton-Schulz step from the Gram matrix still in pA (full == 0)
+      const int* cut = adaptive && bi + 1 == sched.size() ? full : nullptr;
       df_begin(h);
-      df_end(h, df_apply(Fah, Fal, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
+      df_end(h, df_apply(Fah, Fal, Xh, Xl, P, N, X2, h->stream, cut), 2.0 * P * P * (double)N,
+             cut);
+      if (cut)
+        h->launches += ns_correction(reinterpret_cast<const float*>(h->pP), X, Xh, P, N, X2, cut,
+                                     h->stream);
     } else {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
@@ -1038,11 +1094,14 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     }
     std::swap(X, X2);
   }
+  const double* X_block = X;   // the last block's result
   if (df_ok && !h->measuring) {
+    // (cut short: these products return at once and the result is X_block;
+    // the defect flag below then reads the last block's Gram matrix, within
+    // kPolarNear of I)
     h->launches += df_split(X, Xh, Xl, PN, h->stream);
     df_begin(h);
-    df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream),
-           df_gram_flops(P, N));
+    df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N), full);
     // the final step converges quadratically only from |X X^T - I| << 1:
     // flag the instance when the blocks left it above 1e-5 (the isometry
     // would then miss 1e-10)
@@ -1050,11 +1109,14 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
     h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
     df_begin(h);
-    df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream), 2.0 * P * P * (double)N);
+    df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream, full), 2.0 * P * P * (double)N, full);
     std::swap(X, X2);
   }
   if (!h->measuring) {
-    h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
+    if (df_ok)
+      h->launches += scale_select(X_block, X, full, W, NJ * PN, -1.0, h->stream);
+    else
+      h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
     if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
   }
 }
@@ -1266,6 +1328,7 @@ void layout(ttn_ctx* h, Arena& ar) {
     I.E = ar.take(4);
     I.dstat = ar.take(4);
     I.istat = ar.take_int(8);
+    I.pfull = ar.take_int(std::max(I.T, 1));
     c2_max = std::max(c2_max, (size_t)c * c);
     K_max = std::max(K_max, I.K);
   }
@@ -1386,6 +1449,22 @@ void setup_schedules(ttn_ctx* h) {
   // the same two Gram matrices (growth up to 1e6 per block, ~3e-9 relative
   // in double-float arithmetic)
   h->polar_tc = polar_schedule(std::min(l0, 1e-10), 1e6, 1e-15, 1000);
+  // Adaptive variant (mixed modes): block 1 is the full schedule from
+  // kPolarTry (it converges every singular value above it); block 2 assumes
+  // the worst case again -- the image of the same lower bound under block 1's
+  // polynomials -- and, when it fits one block, is replaced on the device by a
+  // single Newton-Schulz step whenever block 1 already left X X^T within
+  // kPolarNear of I (then the final step is not needed either).
+  h->polar_adapt.clear();
+  const std::vector<PolarBlock> first = polar_schedule(kPolarTry, 1e300, 1e-15, 1000);
+  if (first.size() == 1) {
+    double l = std::min(l0, 1e-10);
+    for (const auto& st : first[0].steps) l = st.first * l - st.second * l * l * l;
+    const std::vector<PolarBlock> second = polar_schedule(l, 1e6, 1e-15, 1000);
+    if (second.size() == 1 && (int)first[0].steps.size() <= kMaxComposeSteps &&
+        (int)second[0].steps.size() <= kMaxComposeSteps)
+      h->polar_adapt = {first[0], second[0]};
+  }
 }
 
 }  // namespace
@@ -1488,8 +1567,8 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   rc = build_instances(h, probs, n);
   if (rc) return rc;
   if (h->opt.streams < 1 || h->opt.streams > 64) return fail(h, TTN_EINVAL, "streams in [1,64]");
-  if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 2)
-    return fail(h, TTN_EINVAL, "polar_blocks is 0, 1 or 2");
+  if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 3)
+    return fail(h, TTN_EINVAL, "polar_blocks is 0, 1, 2 or 3");
   assign_lanes(h);
   setup_schedules(h);
   Arena a0;
@@ -1553,6 +1632,11 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
     rc = check_cuda(h, cudaMemsetAsync(h->inst[i].istat, 0, 8 * sizeof(int), h->stream), "status");
     if (!rc)
       rc = check_cuda(h, cudaMemsetAsync(h->inst[i].dstat, 0, 4 * sizeof(double), h->stream), "status");
+    if (!rc) {
+      // no polar block cut short yet
+      h->launches += store_ints(h->inst[i].pfull, nullptr, std::max(h->inst[i].T, 1), 1, h->stream);
+      rc = check_cuda(h, cudaPeekAtLastError(), "status");
+    }
   }
   if (rc) { *out = h; return rc; }
   // upload operators of site layer 0 (shifted one-site term)
@@ -1856,12 +1940,15 @@ int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
   std::vector<double> r(3 * (2 * T + 1) + 1);
   double dst[4];
   int ist[8];
+  std::vector<int> pf(std::max(T, 1));
   int rc = check_cuda(h, cudaMemcpyAsync(r.data(), res, r.size() * sizeof(double),
                                          cudaMemcpyDeviceToHost, h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaMemcpyAsync(dst, I.dstat, sizeof(dst), cudaMemcpyDeviceToHost,
                                               h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaMemcpyAsync(ist, I.istat, sizeof(ist), cudaMemcpyDeviceToHost,
                                               h->stream), "diagnostics");
+  if (!rc) rc = check_cuda(h, cudaMemcpyAsync(pf.data(), I.pfull, pf.size() * sizeof(int),
+                                              cudaMemcpyDeviceToHost, h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
   if (rc) return rc;
   rc = read_status(h, false);
@@ -1881,6 +1968,11 @@ int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
   out[5] = ist[0] ? 1.0 : 0.0;
   out[6] = ist[1];
   if (n_out >= 8) out[7] = ist[4] ? 1.0 : 0.0;
+  if (n_out >= 9) {
+    int cut = 0;
+    for (int t = 0; t < T; ++t) cut += pf[t] == 0;
+    out[8] = cut;
+  }
   return TTN_OK;
 }
 
@@ -2109,7 +2201,12 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
     cudaEventElapsedTime(&e, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]);
     const int g = h->ev_flops[i].first;
     ms[g] += e;
-    fl[g] += h->ev_flops[i].second;
+    // products cut short on the device (adaptive polar schedule) count no flops
+    int run = 1;
+    if (i < h->ev_cond.size() && h->ev_cond[i] && !rc)
+      rc = check_cuda(h, cudaMemcpy(&run, h->ev_cond[i], sizeof(int), cudaMemcpyDeviceToHost),
+                      "profile flags");
+    if (run) fl[g] += h->ev_flops[i].second;
     cnt[g] += 1;
     if (i < h->ev_bytes.size()) by[g] += h->ev_bytes[i];
   }
@@ -2119,6 +2216,7 @@ int ttn_profile_sweep(ttn_t h, double* out, int n_out) {
   h->ev_pool.clear();
   h->ev_flops.clear();
   h->ev_bytes.clear();
+  h->ev_cond.clear();
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   out[0] = ms[0]; out[1] = fl[0]; out[2] = cnt[0];
@@ -2167,6 +2265,7 @@ int ttn_autotune(ttn_t h, int reps, void* blob, size_t* blob_bytes) {
     h->ev_pool.clear();
     h->ev_flops.clear();
     h->ev_bytes.clear();
+    h->ev_cond.clear();
     rc = check_cuda(h, cudaStreamSynchronize(h->stream), "autotune sync");
     if (!rc && h->compose_refused) rc = fail(h, TTN_ECUDA, "cooperative launch refused");
     if (!rc) rc = read_status(h, false);

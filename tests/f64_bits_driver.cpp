@@ -1,7 +1,8 @@
 // Host driver: the integer FP64 -> FP32 conversions of
 // paper_1905_01331_gb300/csrc/f64_bits.cuh against the converting casts
 // (round to nearest even) on random bit patterns, values of ordinary
-// magnitude and exact ties.  Prints "<mismatches> <cases>".
+// magnitude and exact ties, and the FP32 -> FP64 conversion on random FP32
+// bit patterns (exact, bit for bit).  Prints "<mismatches> <cases>".
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,6 +37,19 @@ int main(int argc, char** argv) {
   }
   check(0.0);
   check(-0.0);
+  auto check32 = [&](float f) {
+    const double d = from_f32(f), r = (double)f;
+    ++cases;
+    if (std::memcmp(&d, &r, 8)) ++bad;
+  };
+  for (long i = 0; i < n; ++i) {
+    const uint32_t b = (uint32_t)g();
+    float f;
+    std::memcpy(&f, &b, 4);
+    if (!std::isnan(f)) check32(f);
+  }
+  check32(0.f);
+  check32(-0.f);
   std::printf("%ld %ld\n", bad, cases);
   return 0;
 }

@@ -20,5 +20,5 @@ def test_split_and_to_f32_match_casts(tmp_path):
                    check=True)
     out = subprocess.run([exe, "2000000"], capture_output=True, text=True, check=True).stdout.split()
     bad, cases = int(out[0]), int(out[1])
-    assert cases > 5_000_000
+    assert cases > 7_000_000
     assert bad == 0
