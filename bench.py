@@ -35,11 +35,18 @@ WORKLOAD = {"workload": "tfim_chain_L1024_h1_chi128", "L": 1024, "h": 1.0, "chi"
             "tree": "binary TTN, one isometry per layer"}
 METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
 # DRAM bytes (read + write) per launch of a kernel family, averaged over the
-# launches of one sweep (third sweep from the seeded start), from an ncu
-# capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum);
-# a family without a capture of its current kernel has none.  This is a
-# stored measurement, labelled as such in the line.
-TRAFFIC = {}
+# launches of one steady-state sweep of the headline workload (sweep 31 from
+# the seeded start, tuned table loaded), from an ncu capture of the current
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum; ncu flushes the caches
+# before each launch, so these are cold-cache figures, and writes still in L2
+# at the end of a launch are not counted).  A family without a capture of its
+# current kernel has none.  This is a stored measurement, labelled as such in
+# the line.
+TRAFFIC = {
+    "tc_hbm": 15.77e6,   # gemm_tma_kernel: 116 launches, 1.83 GB
+    "tc": 15.77e6,
+    "df": 8.49e6,        # gemm_df_kernel: 42 launches (10 cut short), 0.357 GB
+}
 
 
 def parse():
@@ -401,12 +408,17 @@ def run_gpu(args):
                   "peak_source": f["peak_source"],
                   "launches_per_sweep": f["launches"], "ms_per_sweep": f["ms"],
                   "share_of_sweep": f["ms"] / prof["total_ms"]}
+    if prof.get("tc_launches"):
+        # the bytes the traffic figure compares with: every operand read once
+        # and the output written once, per launch
+        fam["tc_hbm"]["algorithmic_bytes_per_launch"] = prof.get("tc_bytes", 0.0) / prof["tc_launches"]
     dom = max((k for k in fam if k != "tc_hbm"), key=lambda k: fam[k]["ms_per_sweep"])
     if dom == "tc" and fam["tc_hbm"]["frac"] > fam["tc"]["frac"]:
         dom = "tc_hbm"   # the products are bandwidth-bound: report that roofline
     roofline = dict(fam[dom], traffic=TRAFFIC.get(dom))
     if TRAFFIC.get(dom) is not None:
-        roofline["traffic_source"] = "stored ncu capture of the current kernel (third sweep)"
+        roofline["traffic_source"] = ("stored ncu capture of the current kernels (cold cache, "
+                                      "steady-state sweep 31), mean DRAM bytes per launch")
 
     out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

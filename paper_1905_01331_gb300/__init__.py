@@ -66,7 +66,7 @@ class Sweeper:
                  lanczos_tol=0.0, lanczos_max=48, lanczos_restarts=3,
                  polar_damping=1e-7, use_graph=True, shift=None, top_mode=0,
                  persistent=True, streams=8, polar_blocks=0, double_float=True, wait_polls=0,
-                 tc_engine=0, tiles=None, recompute_ops=False, stage_streams=3):
+                 tc_engine=0, tiles=None, recompute_ops=False, stage_streams=0):
         import torch
         self._torch = torch
         self.lib = _abi.load()

@@ -28,6 +28,8 @@ constexpr int kDBK = 16;
 
 // x -> (hi, lo) with hi = fl32(x), lo = fl32(x - hi)
 __global__ void split_f64_kernel(const double* x, float* hi, float* lo, long long n) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     split_d(x[i], hi[i], lo[i]);
@@ -68,6 +70,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     const float* __restrict__ Ah, const float* __restrict__ Al, long long lda,
     const float* __restrict__ Bh, const float* __restrict__ Bl, long long ldb, int M, int N, int K,
     double* C, long long ldc, double* part, int splits, int sym, const int* run_if) {
+  pdl_wait();
+  pdl_trigger();
   if (run_if && *run_if == 0) return;
   constexpr int TX = BN / TN, NT = (BM / TM) * TX;
   constexpr int LA = BM * kDBK / NT, LB = BN * kDBK / NT;
@@ -184,6 +188,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
 // tiles below the diagonal were not computed and are read from the mirror.
 __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, int tile, int sym,
                                  double* C, long long ldc, const int* run_if) {
+  pdl_wait();
+  pdl_trigger();
   if (run_if && *run_if == 0) return;
   const long long MN = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
@@ -205,28 +211,28 @@ int grid_n(long long n) { return (int)std::min<long long>((n + 255) / 256, 2048)
 // FP32 head Xh, the product accumulates in FP32 (one FMA per multiply-add
 // against the pair product's twelve), and the epilogue adds the FP64 X (one
 // FP64 add per element; the FP32 -> FP64 conversion is integer, f64_bits.cuh).
-// BM x BN output tile per CTA, TM x TN per thread, K (= P) in tiles of kDBK.
-// Runs only when *full is 0.
+// BM x BN output tile per CTA, TM x TN per thread, K (= P) in tiles of kDBK,
+// two shared-memory stages with the next tile held in registers (as in
+// gemm_df_kernel).  Runs only when *full is 0.
 template <int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) ns_correction_kernel(
     const float* __restrict__ Ah, const float* __restrict__ Al, const double* __restrict__ X,
     const float* __restrict__ Xh, int P, long long n2, double* __restrict__ C, const int* full) {
+  pdl_wait();
+  pdl_trigger();
   if (*full != 0) return;
   constexpr int TX = BN / TN, NT = (BM / TM) * TX;
+  constexpr int LA = BM * kDBK / NT, LB = BN * kDBK / NT;
   static_assert(BM * kDBK % NT == 0 && BN * kDBK % NT == 0, "staging split");
-  __shared__ __align__(16) float sD[kDBK][BM + 4], sX[kDBK][BN + 4];
+  __shared__ __align__(16) float sD[2][kDBK][BM + 4], sX[2][kDBK][BN + 4];
   const long long tiles_n = (n2 + BN - 1) / BN;
   const int m0 = (int)(blockIdx.x / tiles_n) * BM;
   const long long n0 = (blockIdx.x % tiles_n) * BN;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  float acc[TM][TN];
+  float rD[LA], rX[LB];
+  auto load = [&](int k0) {
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < P; k0 += kDBK) {
-#pragma unroll
-    for (int i = 0; i < BM * kDBK / NT; ++i) {
+    for (int i = 0; i < LA; ++i) {
       const int e = threadIdx.x + i * NT;
       const int m = m0 + e / kDBK, k = k0 + e % kDBK;
       float d = 0.f;
@@ -234,26 +240,50 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) ns_correction_kernel(
         const long long a = (long long)m * P + k;
         d = 0.5f * ((m == k ? 1.f : 0.f) - Ah[a]) - 0.5f * Al[a];
       }
-      sD[e % kDBK][e / kDBK] = d;
+      rD[i] = d;
     }
 #pragma unroll
-    for (int i = 0; i < BN * kDBK / NT; ++i) {
+    for (int i = 0; i < LB; ++i) {
       const int e = threadIdx.x + i * NT;
       const int k = k0 + e / BN;
       const long long n = n0 + e % BN;
-      sX[e / BN][e % BN] = (k < P && n < n2) ? Xh[(long long)k * n2 + n] : 0.f;
+      rX[i] = (k < P && n < n2) ? Xh[(long long)k * n2 + n] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int e = threadIdx.x + i * NT;
+      sD[buf][e % kDBK][e / kDBK] = rD[i];
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int e = threadIdx.x + i * NT;
+      sX[buf][e / BN][e % BN] = rX[i];
+    }
+  };
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int k0 = 0, buf = 0; k0 < P; k0 += kDBK, buf ^= 1) {
+    const bool more = k0 + kDBK < P;
+    if (more) load(k0 + kDBK);
 #pragma unroll
     for (int kk = 0; kk < kDBK; ++kk) {
       float a[TM], b[TN];
-      lds_frag<TM>(&sD[kk][ty * TM], a);
-      lds_frag<TN>(&sX[kk][tx * TN], b);
+      lds_frag<TM>(&sD[buf][kk][ty * TM], a);
+      lds_frag<TN>(&sX[buf][kk][tx * TN], b);
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
   }
 #pragma unroll
@@ -282,11 +312,11 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
                 int splits, cudaStream_t s, const int* run_if) {
   const int nt = (P + GB - 1) / GB;
   dim3 grid(nt * (nt + 1) / 2, 1, splits);
-  gemm_df_kernel<GB, GB, GT, GT, true, MB><<<grid, (GB / GT) * (GB / GT), 0, s>>>(
+  launch_k(gemm_df_kernel<GB, GB, GT, GT, true, MB>, grid, (GB / GT) * (GB / GT), 0, s,
       Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1, run_if);
   int launches = 1;
   if (splits > 1) {
-    df_reduce_kernel<<<grid_n((long long)P * P), 256, 0, s>>>(part, splits, P, P, GB, 1, C, P,
+    launch_k(df_reduce_kernel, grid_n((long long)P * P), 256, 0, s, part, splits, P, P, GB, 1, C, P,
                                                              run_if);
     ++launches;
   }
@@ -297,7 +327,7 @@ template <int BM, int BN, int TM, int TN, int MB>
 int apply_launch(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
                  long long n2, double* C, cudaStream_t s, const int* run_if) {
   const int tn = (int)((n2 + BN - 1) / BN), tm = (P + BM - 1) / BM;
-  gemm_df_kernel<BM, BN, TM, TN, false, MB><<<tm * tn, (BM / TM) * (BN / TN), 0, s>>>(
+  launch_k(gemm_df_kernel<BM, BN, TM, TN, false, MB>, tm * tn, (BM / TM) * (BN / TN), 0, s,
       Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0, run_if);
   return 1;
 }
@@ -307,7 +337,7 @@ constexpr int kGramB = 32, kGramT = 2, kGramTarget = 296;
 }  // namespace
 
 int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s) {
-  split_f64_kernel<<<grid_n(n), 256, 0, s>>>(x, hi, lo, n);
+  launch_k(split_f64_kernel, grid_n(n), 256, 0, s, x, hi, lo, n);
   return 1;
 }
 
@@ -331,9 +361,9 @@ int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl,
 
 int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
                   double* C, const int* full, cudaStream_t s) {
-  constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
+  constexpr int BM = 128, BN = 64, TM = 8, TN = 4;
   const long long tiles = (long long)((P + BM - 1) / BM) * ((n2 + BN - 1) / BN);
-  ns_correction_kernel<BM, BN, TM, TN><<<(unsigned)tiles, (BM / TM) * (BN / TN), 0, s>>>(
+  launch_k(ns_correction_kernel<BM, BN, TM, TN>, (unsigned)tiles, (BM / TM) * (BN / TN), 0, s,
       A, A + (long long)P * P, X, Xh, P, n2, C, full);
   return 1;
 }

@@ -6,6 +6,7 @@
 // that index permutations of the rank-3 tensors (Sec. V: "permuting indices of
 // rank-3 tensors") are folded into the address arithmetic and never stored.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 #include <mutex>
 
@@ -45,6 +46,8 @@ __device__ __forceinline__ void st_out(const GemmDesc& d, long long e, double ac
 // BM x BN output tile per CTA, 256 threads, each thread TM x TN outputs.
 template <int BM, int BN>
 __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, int total_tiles) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int TM = BM / 16, TN = BN / 16;
   if (d.skip && *d.skip) return;
   __shared__ double As[kBK][BM + 1];
@@ -146,6 +149,8 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
 
 // C = alpha * sum_s partial[s] + beta * C, summed in split order.
 __global__ void splitk_reduce_kernel(const GemmDesc d) {
+  pdl_wait();
+  pdl_trigger();
   if (d.skip && *d.skip) return;
   const long long MN = (long long)d.M * d.N;
   const long long total = MN * d.B0 * d.B1;
@@ -173,7 +178,7 @@ int launch_tile(const GemmDesc& d, cudaStream_t s) {
   const int tn = (d.N + BN - 1) / BN;
   const int tiles = d.sym ? tn * (tn + 1) / 2 : ((d.M + BM - 1) / BM) * tn;
   dim3 grid(tiles, d.B0 * d.B1, d.splits);
-  gemm_f64_kernel<BM, BN><<<grid, kThreads, 0, s>>>(d, total_k_tiles(d));
+  launch_k(gemm_f64_kernel<BM, BN>, grid, kThreads, 0, s, d, total_k_tiles(d));
   return 1;
 }
 
@@ -181,6 +186,14 @@ int launch_tile(const GemmDesc& d, cudaStream_t s) {
 
 // SM count of the current device, read once per device (152 on GB300, also
 // the value when no device is visible, e.g. when only sizes are planned).
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("TTN_PDL");
+    return e && e[0] && e[0] != '0';
+  }();
+  return on;
+}
+
 int device_sm_count() {
   static std::mutex mu;
   static int cache[64] = {0};
@@ -247,7 +260,7 @@ int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
   if (d.splits > 1) {
     const long long total = (long long)d.M * d.N * d.B0 * d.B1;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(d);
+    launch_k(splitk_reduce_kernel, blocks, 256, 0, s, d);
     ++n;
   }
   return n;

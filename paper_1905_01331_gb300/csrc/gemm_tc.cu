@@ -437,6 +437,8 @@ void tc_configure() {
 
 template <bool kBF16, bool kSplit, int BN>
 __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d, TCParams tp) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int BK = kBF16 ? 64 : 32;            // one 128-byte swizzle row
   constexpr int KSTEP = kBF16 ? 16 : 8;          // K of one tcgen05.mma
   constexpr int kA = kBM * 128;                  // bytes of one A tile (128 rows)
@@ -635,6 +637,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
 // summed in split order as an FP32 pair (error-free two-sum, low parts
 // accumulated), then rounded to FP32.
 __global__ void splitk_reduce_tc(const GemmDesc d) {
+  pdl_wait();
+  pdl_trigger();
   if (d.skip && *d.skip) return;
   const long long MN = static_cast<long long>(d.M) * d.N;
   const long long total = MN * d.B0 * d.B1;
@@ -860,6 +864,8 @@ __device__ __forceinline__ void store_row16(const GemmDesc& d, int b, int b0, in
 template <bool kSplit, int BN, int kRing>
 __global__ void __launch_bounds__(kTThreads, kRing == kTSmem ? 1 : 2)
     gemm_tma_kernel(const GemmDesc d, const __grid_constant__ TmaParams tp) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int kA = kBM * 128;                     // raw A tile: 128 rows x 32 FP32
   constexpr int kB = BN * 128;
   constexpr int kHi = kA + kB;                      // raw tiles, TF32 heads after conversion
@@ -1170,7 +1176,7 @@ int launch_tma(const GemmDesc& d, cudaStream_t s) {
   tp.err = d.err;
   const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
   dim3 grid(tiles, d.B0 * d.B1, d.splits);
-  gemm_tma_kernel<kSplit, BN, kRing><<<grid, kTThreads, kRing + 1024, s>>>(d, tp);
+  launch_k(gemm_tma_kernel<kSplit, BN, kRing>, grid, kTThreads, kRing + 1024, s, d, tp);
   return 1;
 }
 
@@ -1203,7 +1209,7 @@ int launch_tc(const GemmDesc& d, cudaStream_t s, int* err) {
   const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
   dim3 grid(tiles, d.B0 * d.B1, d.splits);
   TCParams tp{tc_total_tiles(d, BK), err};
-  gemm_tc_kernel<kBF16, kSplit, BN><<<grid, kThreadsTC, smem, s>>>(d, tp);
+  launch_k(gemm_tc_kernel<kBF16, kSplit, BN>, grid, kThreadsTC, smem, s, d, tp);
   return 1;
 }
 
@@ -1264,7 +1270,7 @@ int gemm_tc_launch(const GemmDesc& d, cudaStream_t s) {
   if (d.splits > 1) {
     const long long total = static_cast<long long>(d.M) * d.N * d.B0 * d.B1;
     const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 4096));
-    splitk_reduce_tc<<<blocks, 256, 0, s>>>(d);
+    launch_k(splitk_reduce_tc, blocks, 256, 0, s, d);
     ++n;
   }
   return n;

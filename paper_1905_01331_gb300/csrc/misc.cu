@@ -28,6 +28,8 @@ __device__ double block_sum(double v) {
 // partial[b * kDotBlocks + blk] = sum over this block's slice of x*y
 __global__ void dot_partial_kernel(const double* x, const double* y, long long n,
                                    long long stride, double* partial, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (skip && *skip) return;
   const int b = blockIdx.y, blk = blockIdx.x;
   const double* xb = x + b * stride;
@@ -48,6 +50,8 @@ __global__ void dot_partial_kernel(const double* x, const double* y, long long n
 // out[b] = sum of the kDotBlocks partial sums of batch b: one warp per batch,
 // lane-strided sums, then a fixed butterfly.
 __global__ void dot_final_kernel(const double* partial, int nb, double* out, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (skip && *skip) return;
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (b >= nb) return;
@@ -59,6 +63,8 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
                                    int P, double mu, const double* fro2, const double* gw) {
+  pdl_wait();
+  pdl_trigger();
   const int b = blockIdx.y;
   const double f2 = fro2[b];
   const double s = mu * sqrt(f2);
@@ -73,6 +79,8 @@ __global__ void polar_start_kernel(const double* G, const double* W, double* X, 
 }
 
 __global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, double c) {
+  pdl_wait();
+  pdl_trigger();
   const int b = blockIdx.y;
   const long long PP = (long long)P * P;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
@@ -83,6 +91,8 @@ __global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, d
 }
 
 __global__ void identity_kernel(double* F, int P) {
+  pdl_wait();
+  pdl_trigger();
   const int b = blockIdx.y;
   const long long PP = (long long)P * P;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
@@ -91,6 +101,8 @@ __global__ void identity_kernel(double* F, int P) {
 }
 
 __global__ void axpby_kernel(const double* x, double* y, long long n, double alpha, double beta) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = alpha * x[i] + beta * y[i];
@@ -98,6 +110,8 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
 
 __global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
                                     long long n, double alpha) {
+  pdl_wait();
+  pdl_trigger();
   const double* x = *sel ? x1 : x0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -105,6 +119,8 @@ __global__ void scale_select_kernel(const double* x0, const double* x1, const in
 }
 
 __global__ void symmetrize_kernel(double* A, int P) {
+  pdl_wait();
+  pdl_trigger();
   const int b = blockIdx.y;
   double* a = A + (long long)b * P * P;
   const long long PP = (long long)P * P;
@@ -124,6 +140,8 @@ __global__ void symmetrize_kernel(double* A, int P) {
 // partial[i * kDotBlocks + blk] = <basis_i, w> over this block's slice
 __global__ void lz_dots_partial(const double* basis, long long n, int count, const double* w,
                                 double* partial, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   const int i = blockIdx.y;
   if (i >= count) return;
@@ -137,6 +155,8 @@ __global__ void lz_dots_partial(const double* basis, long long n, int count, con
 }
 
 __global__ void lz_dots_final(const double* partial, int count, double* coef, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   const int i = threadIdx.x;
   if (i >= count) return;
@@ -147,6 +167,8 @@ __global__ void lz_dots_final(const double* partial, int count, double* coef, co
 
 __global__ void lz_sub_kernel(const double* basis, long long n, int count, double* w,
                               const double* coef, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -159,6 +181,8 @@ __global__ void lz_sub_kernel(const double* basis, long long n, int count, doubl
 // alpha_j from the two projection passes, beta_j = |w|; breakdown stops the run.
 __global__ void lz_step_scalars(const double* c1, const double* c2, int j, double* alpha,
                                 double* beta, const double* nrm2, int* skip, int* tdim) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   const double a = c1[j] + c2[j];
   alpha[j] = a;
@@ -171,6 +195,8 @@ __global__ void lz_step_scalars(const double* c1, const double* c2, int j, doubl
 
 __global__ void lz_scale_into(double* dst, const double* w, long long n, const double* beta, int j,
                               const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   const double inv = 1.0 / beta[j];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -196,6 +222,8 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
 __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const int* tdim, int jmax,
                                double* y, double* theta, double* res, int* conv, double tol,
                                const int* skip_before) {
+  pdl_wait();
+  pdl_trigger();
   // one warp: 32-way multisection of the Gershgorin interval for the lowest
   // eigenvalue (each lane counts eigenvalues below its own point), then lane 0
   // runs the inverse iteration
@@ -273,6 +301,8 @@ __global__ void lz_ritz_kernel(const double* alpha, const double* beta, const in
 
 __global__ void lz_combine_kernel(const double* basis, long long n, const int* tdim, const double* y,
                                   double* v) {
+  pdl_wait();
+  pdl_trigger();
   const int m = *tdim;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -283,6 +313,8 @@ __global__ void lz_combine_kernel(const double* basis, long long n, const int* t
 }
 
 __global__ void scale_by_inv_sqrt(double* v, long long n, const double* nrm2, double* dst0) {
+  pdl_wait();
+  pdl_trigger();
   const double inv = 1.0 / sqrt(nrm2[0]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -293,11 +325,15 @@ __global__ void scale_by_inv_sqrt(double* v, long long n, const double* nrm2, do
 }
 
 __global__ void lz_reset_kernel(int* tdim, int* skip, const int* conv) {
+  pdl_wait();
+  pdl_trigger();
   *tdim = 1;
   *skip = *conv;
 }
 
 __global__ void flip_if_negative(double* v, long long n, const double* dotv) {
+  pdl_wait();
+  pdl_trigger();
   if (dotv[0] >= 0.0) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -306,6 +342,8 @@ __global__ void flip_if_negative(double* v, long long n, const double* dotv) {
 
 __global__ void ordered_sum_kernel(const double* x, int count, double* out, double scale,
                                    double add) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
   for (int i = 0; i < count; ++i) s += x[i];
@@ -313,6 +351,8 @@ __global__ void ordered_sum_kernel(const double* x, int count, double* out, doub
 }
 
 __global__ void finite_kernel(const double* x, long long n, int* flag) {
+  pdl_wait();
+  pdl_trigger();
   int bad = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -322,6 +362,8 @@ __global__ void finite_kernel(const double* x, long long n, int* flag) {
 
 __global__ void split_identity_kernel(double* O, long long stride, int P, const double* e_in,
                                       int per_node, double* e_out) {
+  pdl_wait();
+  pdl_trigger();
   const int J = blockIdx.x;
   double* o = O + J * stride;
   __shared__ double sh[256];
@@ -344,6 +386,8 @@ __global__ void split_identity_kernel(double* O, long long stride, int P, const 
 template <typename T>
 __global__ void add_identity_kernel(T* Z, const T* W, long long elems, const double* e_in,
                                     int per_node, double coef) {
+  pdl_wait();
+  pdl_trigger();
   const int J = blockIdx.y;
   const double c = coef * (e_in[per_node ? 2 * J : 0] + e_in[per_node ? 2 * J + 1 : 0]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
@@ -354,6 +398,8 @@ __global__ void add_identity_kernel(T* Z, const T* W, long long elems, const dou
 // out = 2 (w + (e_0 + e_1) v): gradient of <v, H_top v> with the identity part
 __global__ void top_grad_kernel(double* out, const double* w, const double* v, long long n,
                                 const double* e, int per_node) {
+  pdl_wait();
+  pdl_trigger();
   const double sh = e[0] + e[per_node ? 1 : 0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -362,6 +408,8 @@ __global__ void top_grad_kernel(double* out, const double* w, const double* v, l
 
 __global__ void scale_normalise_kernel(const double* x, double* y, long long n, const double* nrm2,
                                        double sign) {
+  pdl_wait();
+  pdl_trigger();
   const double f = sign / sqrt(nrm2[0]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -370,11 +418,15 @@ __global__ void scale_normalise_kernel(const double* x, double* y, long long n, 
 
 __global__ void top_energy_kernel(const double* dot, const double* vv, const double* e,
                                   int per_node, double add, double* out) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x == 0 && blockIdx.x == 0)
     *out = dot[0] + (e[0] + e[per_node ? 1 : 0]) * vv[0] + add;
 }
 
 __global__ void to_f32_kernel(const double* src, float* dst, long long n) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     dst[i] = f64b::to_f32(src[i]);
@@ -385,6 +437,8 @@ __global__ void to_f32_kernel(const double* src, float* dst, long long n) {
 // dstat[2] = tolerance; istat[2] = 1 when |change| < tolerance and a previous
 // energy exists, istat[3] = sweeps seen since the last reset.
 __global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, double inv_spins) {
+  pdl_wait();
+  pdl_trigger();
   const double e = *E;
   const int seen = istat[3];
   const double d = (e - dstat[0]) * inv_spins;
@@ -396,6 +450,8 @@ __global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, d
 
 // flag[0] |= 1 when max |A - I| of the P x P matrix A exceeds thr (one CTA).
 __global__ void far_from_identity_kernel(const double* A, int P, double thr, int* flag) {
+  pdl_wait();
+  pdl_trigger();
   // one CTA per row block of 8 rows, a warp per row
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   int mine = 0;
@@ -408,6 +464,8 @@ __global__ void far_from_identity_kernel(const double* A, int P, double thr, int
 }
 
 __global__ void store_ints_kernel(int* dst, const int* src, int n, int value) {
+  pdl_wait();
+  pdl_trigger();
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src ? src[i] : value;
 }
 
@@ -416,6 +474,8 @@ __global__ void store_ints_kernel(int* dst, const int* src, int n, int value) {
 // max |M| , out[2] = max |M_ij - M_ji|.
 __global__ void mat_stats_kernel(const double* M, int n, int nb, long long stride,
                                  int sub_identity, double* out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double st[256], sd[256], sa[256];
   double tr = 0.0, dev = 0.0, asym = 0.0;
   const long long nn = (long long)n * n;
@@ -455,113 +515,113 @@ int grid_for(long long n, int per = 256, int cap = 1184) {
 
 int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
                 double* out, double* scratch, cudaStream_t s) {
-  dot_partial_kernel<<<dim3(kDotBlocks, nb), 256, 0, s>>>(x, y, n, stride, scratch, nullptr);
-  dot_final_kernel<<<(nb + 3) / 4, 128, 0, s>>>(scratch, nb, out, nullptr);
+  launch_k(dot_partial_kernel, dim3(kDotBlocks, nb), 256, 0, s, x, y, n, stride, scratch, nullptr);
+  launch_k(dot_final_kernel, (nb + 3) / 4, 128, 0, s, scratch, nb, out, nullptr);
   return 2;
 }
 
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
                 double mu, const double* fro2, const double* gw, cudaStream_t s) {
-  polar_start_kernel<<<dim3(grid_for(elems, 256, 512), nb), 256, 0, s>>>(G, W, X, elems, P, mu,
+  launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P, mu,
                                                                           fro2, gw);
   return 1;
 }
 
 int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
                      cudaStream_t s) {
-  poly_step_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(A, Pm, P, a, c);
+  launch_k(poly_step_kernel, dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s, A, Pm, P, a, c);
   return 1;
 }
 
 int set_identity(double* F, int P, int nb, cudaStream_t s) {
-  identity_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(F, P);
+  launch_k(identity_kernel, dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s, F, P);
   return 1;
 }
 
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s) {
-  axpby_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, alpha, beta);
+  launch_k(axpby_kernel, grid_for(n), 256, 0, s, x, y, n, alpha, beta);
   return 1;
 }
 
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
                  double alpha, cudaStream_t s) {
-  scale_select_kernel<<<grid_for(n), 256, 0, s>>>(x0, x1, sel, y, n, alpha);
+  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha);
   return 1;
 }
 
 int symmetrize(double* A, int P, int nb, cudaStream_t s) {
-  symmetrize_kernel<<<dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s>>>(A, P);
+  launch_k(symmetrize_kernel, dim3(grid_for((long long)P * P, 256, 64), nb), 256, 0, s, A, P);
   return 1;
 }
 
 int lz_dots(const double* basis, long long n, int count, const double* w, double* coef,
             double* scratch, const int* skip, cudaStream_t s) {
-  lz_dots_partial<<<dim3(kDotBlocks, count), 256, 0, s>>>(basis, n, count, w, scratch, skip);
-  lz_dots_final<<<1, 128, 0, s>>>(scratch, count, coef, skip);
+  launch_k(lz_dots_partial, dim3(kDotBlocks, count), 256, 0, s, basis, n, count, w, scratch, skip);
+  launch_k(lz_dots_final, 1, 128, 0, s, scratch, count, coef, skip);
   return 2;
 }
 
 int lz_sub(const double* basis, long long n, int count, double* w, const double* coef,
            const int* skip, cudaStream_t s) {
-  lz_sub_kernel<<<grid_for(n), 256, 0, s>>>(basis, n, count, w, coef, skip);
+  launch_k(lz_sub_kernel, grid_for(n), 256, 0, s, basis, n, count, w, coef, skip);
   return 1;
 }
 
 int lz_finish_step(double* basis, long long n, int j, double* w, const double* c1,
                    const double* c2, double* alpha, double* beta, double* scratch, double* nrm2,
                    int* skip, int* tdim, cudaStream_t s) {
-  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(w, w, n, 0, scratch, skip);
-  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, skip);
-  lz_step_scalars<<<1, 1, 0, s>>>(c1, c2, j, alpha, beta, nrm2, skip, tdim);
-  lz_scale_into<<<grid_for(n), 256, 0, s>>>(basis + (j + 1) * n, w, n, beta, j, skip);
+  launch_k(dot_partial_kernel, dim3(kDotBlocks, 1), 256, 0, s, w, w, n, 0, scratch, skip);
+  launch_k(dot_final_kernel, 1, 32, 0, s, scratch, 1, nrm2, skip);
+  launch_k(lz_step_scalars, 1, 1, 0, s, c1, c2, j, alpha, beta, nrm2, skip, tdim);
+  launch_k(lz_scale_into, grid_for(n), 256, 0, s, basis + (j + 1) * n, w, n, beta, j, skip);
   return 4;
 }
 
 int lz_ritz(const double* alpha, const double* beta, const int* tdim, int jmax, double* y,
             double* theta, double* res, int* conv, double tol, cudaStream_t s) {
-  lz_ritz_kernel<<<1, 32, 0, s>>>(alpha, beta, tdim, jmax, y, theta, res, conv, tol, nullptr);
+  launch_k(lz_ritz_kernel, 1, 32, 0, s, alpha, beta, tdim, jmax, y, theta, res, conv, tol, nullptr);
   return 1;
 }
 
 int lz_combine(double* basis, long long n, const int* tdim, const double* y, double* v,
                double* scratch, double* nrm2, int* tdim_rw, int* skip, const int* conv,
                cudaStream_t s) {
-  lz_combine_kernel<<<grid_for(n), 256, 0, s>>>(basis, n, tdim, y, v);
-  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, v, n, 0, scratch, nullptr);
-  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, nullptr);
-  scale_by_inv_sqrt<<<grid_for(n), 256, 0, s>>>(v, n, nrm2, basis);
-  lz_reset_kernel<<<1, 1, 0, s>>>(tdim_rw, skip, conv);
+  launch_k(lz_combine_kernel, grid_for(n), 256, 0, s, basis, n, tdim, y, v);
+  launch_k(dot_partial_kernel, dim3(kDotBlocks, 1), 256, 0, s, v, v, n, 0, scratch, nullptr);
+  launch_k(dot_final_kernel, 1, 32, 0, s, scratch, 1, nrm2, nullptr);
+  launch_k(scale_by_inv_sqrt, grid_for(n), 256, 0, s, v, n, nrm2, basis);
+  launch_k(lz_reset_kernel, 1, 1, 0, s, tdim_rw, skip, conv);
   return 5;
 }
 
 int lz_start(double* basis, long long n, const double* v, double* scratch, double* nrm2,
              int* tdim, int* skip, int* conv, cudaStream_t s) {
   cudaMemsetAsync(conv, 0, sizeof(int), s);
-  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, v, n, 0, scratch, nullptr);
-  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, nrm2, nullptr);
+  launch_k(dot_partial_kernel, dim3(kDotBlocks, 1), 256, 0, s, v, v, n, 0, scratch, nullptr);
+  launch_k(dot_final_kernel, 1, 32, 0, s, scratch, 1, nrm2, nullptr);
   cudaMemcpyAsync(basis, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  scale_by_inv_sqrt<<<grid_for(n), 256, 0, s>>>(basis, n, nrm2, nullptr);
-  lz_reset_kernel<<<1, 1, 0, s>>>(tdim, skip, conv);
+  launch_k(scale_by_inv_sqrt, grid_for(n), 256, 0, s, basis, n, nrm2, nullptr);
+  launch_k(lz_reset_kernel, 1, 1, 0, s, tdim, skip, conv);
   return 4;
 }
 
 int align_sign(double* v, const double* vprev, long long n, double* scratch, double* dotv,
                cudaStream_t s) {
-  dot_partial_kernel<<<dim3(kDotBlocks, 1), 256, 0, s>>>(v, vprev, n, 0, scratch, nullptr);
-  dot_final_kernel<<<1, 32, 0, s>>>(scratch, 1, dotv, nullptr);
-  flip_if_negative<<<grid_for(n), 256, 0, s>>>(v, n, dotv);
+  launch_k(dot_partial_kernel, dim3(kDotBlocks, 1), 256, 0, s, v, vprev, n, 0, scratch, nullptr);
+  launch_k(dot_final_kernel, 1, 32, 0, s, scratch, 1, dotv, nullptr);
+  launch_k(flip_if_negative, grid_for(n), 256, 0, s, v, n, dotv);
   return 3;
 }
 
 int ordered_sum(const double* x, int count, double* out, double scale, double add,
                 cudaStream_t s) {
-  ordered_sum_kernel<<<1, 32, 0, s>>>(x, count, out, scale, add);
+  launch_k(ordered_sum_kernel, 1, 32, 0, s, x, count, out, scale, add);
   return 1;
 }
 
 int split_identity(double* O, long long stride, int P, int nodes, const double* e_in,
                    int per_node, double* e_out, cudaStream_t s) {
-  split_identity_kernel<<<nodes, 256, 0, s>>>(O, stride, P, e_in, per_node, e_out);
+  launch_k(split_identity_kernel, nodes, 256, 0, s, O, stride, P, e_in, per_node, e_out);
   return 1;
 }
 
@@ -569,11 +629,11 @@ int add_identity_part(void* Z, const void* W, int f32, long long elems, int node
                       const double* e_in, int per_node, double coef, cudaStream_t s) {
   const dim3 grid(grid_for(elems, 256, 512), nodes);
   if (f32)
-    add_identity_kernel<float><<<grid, 256, 0, s>>>(static_cast<float*>(Z),
+    launch_k(add_identity_kernel<float>, grid, 256, 0, s, static_cast<float*>(Z),
                                                     static_cast<const float*>(W), elems, e_in,
                                                     per_node, coef);
   else
-    add_identity_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(Z),
+    launch_k(add_identity_kernel<double>, grid, 256, 0, s, static_cast<double*>(Z),
                                                      static_cast<const double*>(W), elems, e_in,
                                                      per_node, coef);
   return 1;
@@ -581,50 +641,50 @@ int add_identity_part(void* Z, const void* W, int f32, long long elems, int node
 
 int scale_normalise(const double* x, double* y, long long n, const double* nrm2, double sign,
                     cudaStream_t s) {
-  scale_normalise_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, nrm2, sign);
+  launch_k(scale_normalise_kernel, grid_for(n), 256, 0, s, x, y, n, nrm2, sign);
   return 1;
 }
 
 int top_grad(double* out, const double* w, const double* v, long long n, const double* e,
              int per_node, cudaStream_t s) {
-  top_grad_kernel<<<grid_for(n), 256, 0, s>>>(out, w, v, n, e, per_node);
+  launch_k(top_grad_kernel, grid_for(n), 256, 0, s, out, w, v, n, e, per_node);
   return 1;
 }
 
 int top_energy_sum(const double* dot, const double* vv, const double* e, int per_node, double add,
                    double* out, cudaStream_t s) {
-  top_energy_kernel<<<1, 32, 0, s>>>(dot, vv, e, per_node, add, out);
+  launch_k(top_energy_kernel, 1, 32, 0, s, dot, vv, e, per_node, add, out);
   return 1;
 }
 
 int to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
-  to_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  launch_k(to_f32_kernel, grid_for(n), 256, 0, s, src, dst, n);
   return 1;
 }
 
 int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cudaStream_t s) {
-  sweep_delta_kernel<<<1, 1, 0, s>>>(E, dstat, istat, inv_spins);
+  launch_k(sweep_delta_kernel, 1, 1, 0, s, E, dstat, istat, inv_spins);
   return 1;
 }
 
 int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s) {
-  far_from_identity_kernel<<<(P + 7) / 8, 256, 0, s>>>(A, P, thr, flag);
+  launch_k(far_from_identity_kernel, (P + 7) / 8, 256, 0, s, A, P, thr, flag);
   return 1;
 }
 
 int store_ints(int* dst, const int* src, int n, int value, cudaStream_t s) {
-  store_ints_kernel<<<1, 32, 0, s>>>(dst, src, n, value);
+  launch_k(store_ints_kernel, 1, 32, 0, s, dst, src, n, value);
   return 1;
 }
 
 int mat_stats(const double* M, int n, int nb, long long stride, int sub_identity, double* out,
               cudaStream_t s) {
-  mat_stats_kernel<<<1, 256, 0, s>>>(M, n, nb, stride, sub_identity, out);
+  launch_k(mat_stats_kernel, 1, 256, 0, s, M, n, nb, stride, sub_identity, out);
   return 1;
 }
 
 int finite_check(const double* x, long long n, int* flag, cudaStream_t s) {
-  finite_kernel<<<grid_for(n, 256, 296), 256, 0, s>>>(x, n, flag);
+  launch_k(finite_kernel, grid_for(n, 256, 296), 256, 0, s, x, n, flag);
   return 1;
 }
 

@@ -1365,7 +1365,9 @@ void layout(ttn_ctx* h, Arena& ar) {
     }
     h->iflags = ar.take_int(8);
     h->partial = ar.take(h->partial_cap);
-    h->sub.n = h->opt.stage_streams > 1 ? std::min(h->opt.stage_streams, kSubStreams) : 0;
+    const int ss = h->opt.stage_streams == 0 ? (h->lanes.size() == 1 ? kSubStreams : 1)
+                                             : h->opt.stage_streams;
+    h->sub.n = ss > 1 ? std::min(ss, kSubStreams) : 0;
     for (int i = 0; i < h->sub.n; ++i) h->sub.partial[i] = ar.take(h->partial_cap);
     save_lane(h, h->lanes[k]);
   }
@@ -1495,7 +1497,7 @@ void ttn_default_options(ttn_options* o) {
   o->tiles = nullptr;
   o->tiles_bytes = 0;
   o->recompute_ops = 0;
-  o->stage_streams = 3;
+  o->stage_streams = 0;
 }
 
 // Parse an autotuner blob (ttn_options.tiles) into the table.
