@@ -125,10 +125,18 @@ constexpr int kDotBlocks = 256;
 int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
                 double* out, double* scratch, cudaStream_t s);
 
+// out[b] = <x_b, x_b>, out[nb + b] = <x_b, y_b> (batch b at offset b * stride,
+// n elements) in one pass over x, each sum in the order of batched_dot.
+int dot_self_and_cross(const double* x, const double* y, long long n, long long stride, int nb,
+                       double* out, double* scratch, cudaStream_t s);
+
 // Polar start: per batch b (P x N rows), with fro2 = |G|^2, gw = <G, W>:
 //   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
+// With xh, xl (one batch only) X is also written as FP32 pairs (xh = fl32(X),
+// xl = fl32(X - xh)) for the double-float products.
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
-                int P, double mu, const double* fro2, const double* gw, cudaStream_t s);
+                int P, double mu, const double* fro2, const double* gw, cudaStream_t s,
+                float* xh = nullptr, float* xl = nullptr);
 
 // Pm[b] = a I - c A[b] (P x P), nb batches.
 int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
@@ -139,9 +147,10 @@ int set_identity(double* F, int P, int nb, cudaStream_t s);
 
 // y = alpha * x + beta * y over n elements.
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s);
-// y = alpha * (*sel ? x1 : x0) over n elements (sel on the device).
+// y = alpha * (*sel ? x1 : x0) over n elements (sel on the device); with y32
+// also its FP32 copy (as to_f32).
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
-                 double alpha, cudaStream_t s);
+                 double alpha, cudaStream_t s, float* y32 = nullptr);
 
 // Symmetrise P x P blocks in place: A = (A + A^T) / 2.
 int symmetrize(double* A, int P, int nb, cudaStream_t s);
@@ -267,9 +276,11 @@ double df_gram_flops(int P, long long n2);
 // run_if (device, may be null): when it points to 0 the launches return at once.
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
             cudaStream_t s, const int* run_if = nullptr);
-// C (P x n2, FP64) = F X for F (P x P) given as (Fh, Fl) and X as (Xh, Xl).
+// C (P x n2, FP64) = F X for F (P x P) given as (Fh, Fl) and X as (Xh, Xl);
+// with Ch, Cl also the normalised FP32 pair of C (the same as splitting C).
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-             long long n2, double* C, cudaStream_t s, const int* run_if = nullptr);
+             long long n2, double* C, cudaStream_t s, const int* run_if = nullptr,
+             float* Ch = nullptr, float* Cl = nullptr);
 // C (P x n2) = (1.5 I - 0.5 A) X for A (P x P, as an FP32 pair: hi at A, lo
 // at A + P*P) within 1e-9 of I elementwise: C = X + 0.5 (I - A) X with the
 // correction product in FP32 on X's FP32 head Xh.  Runs only when *full

@@ -69,7 +69,8 @@ template <int BM, int BN, int TM, int TN, bool kBKmajor, int MB>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     const float* __restrict__ Ah, const float* __restrict__ Al, long long lda,
     const float* __restrict__ Bh, const float* __restrict__ Bl, long long ldb, int M, int N, int K,
-    double* C, long long ldc, double* part, int splits, int sym, const int* run_if) {
+    double* C, long long ldc, double* part, int splits, int sym, const int* run_if, float* Ch,
+    float* Cl) {
   pdl_wait();
   pdl_trigger();
   if (run_if && *run_if == 0) return;
@@ -180,6 +181,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
       } else {
         C[m * ldc + nn] = v;
         if (sym && tm < tn) C[nn * ldc + m] = v;
+        // the pair is normalised (renormalised after the last K tile), so it
+        // is the FP32 split of v
+        if (Ch) {
+          Ch[m * ldc + nn] = sh[i][j];
+          Cl[m * ldc + nn] = sl[i][j];
+        }
       }
     }
 }
@@ -313,7 +320,7 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
   const int nt = (P + GB - 1) / GB;
   dim3 grid(nt * (nt + 1) / 2, 1, splits);
   launch_k(gemm_df_kernel<GB, GB, GT, GT, true, MB>, grid, (GB / GT) * (GB / GT), 0, s,
-      Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1, run_if);
+      Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1, run_if, nullptr, nullptr);
   int launches = 1;
   if (splits > 1) {
     launch_k(df_reduce_kernel, grid_n((long long)P * P), 256, 0, s, part, splits, P, P, GB, 1, C, P,
@@ -325,10 +332,11 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
 
 template <int BM, int BN, int TM, int TN, int MB>
 int apply_launch(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-                 long long n2, double* C, cudaStream_t s, const int* run_if) {
+                 long long n2, double* C, cudaStream_t s, const int* run_if, float* Ch,
+                 float* Cl) {
   const int tn = (int)((n2 + BN - 1) / BN), tm = (P + BM - 1) / BM;
   launch_k(gemm_df_kernel<BM, BN, TM, TN, false, MB>, tm * tn, (BM / TM) * (BN / TN), 0, s,
-      Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0, run_if);
+      Fh, Fl, P, Xh, Xl, n2, P, (int)n2, P, C, n2, nullptr, 1, 0, run_if, Ch, Cl);
   return 1;
 }
 
@@ -355,8 +363,8 @@ int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, do
 }
 
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
-             long long n2, double* C, cudaStream_t s, const int* run_if) {
-  return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s, run_if);
+             long long n2, double* C, cudaStream_t s, const int* run_if, float* Ch, float* Cl) {
+  return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s, run_if, Ch, Cl);
 }
 
 int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,

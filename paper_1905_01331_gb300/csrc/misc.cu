@@ -47,6 +47,38 @@ __global__ void dot_partial_kernel(const double* x, const double* y, long long n
   if (threadIdx.x == 0) partial[b * kDotBlocks + blk] = s;
 }
 
+// The two sums <x, x> and <x, y> of the damped polar start in one pass over x:
+// partial[b * kDotBlocks + blk] as dot_partial_kernel for <x, x>, and at
+// partial[(nb + b) * kDotBlocks + blk] for <x, y> (the same order of terms).
+__global__ void dot2_partial_kernel(const double* x, const double* y, long long n, long long stride,
+                                    int nb, double* partial) {
+  pdl_wait();
+  pdl_trigger();
+  const int b = blockIdx.y, blk = blockIdx.x;
+  const double* xb = x + b * stride;
+  const double* yb = y + b * stride;
+  double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  long long i = blk * (long long)blockDim.x + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    const double a = xb[i], c = xb[i + step];
+    s0 = fma(a, a, s0);
+    s1 = fma(c, c, s1);
+    t0 = fma(a, yb[i], t0);
+    t1 = fma(c, yb[i + step], t1);
+  }
+  if (i < n) {
+    const double a = xb[i];
+    s0 = fma(a, a, s0);
+    t0 = fma(a, yb[i], t0);
+  }
+  const double s = block_sum(s0 + s1);
+  if (threadIdx.x == 0) partial[b * kDotBlocks + blk] = s;
+  __syncthreads();   // block_sum's shared scratch is reused
+  const double t = block_sum(t0 + t1);
+  if (threadIdx.x == 0) partial[(nb + b) * kDotBlocks + blk] = t;
+}
+
 // out[b] = sum of the kDotBlocks partial sums of batch b: one warp per batch,
 // lane-strided sums, then a fixed butterfly.
 __global__ void dot_final_kernel(const double* partial, int nb, double* out, const int* skip) {
@@ -62,7 +94,8 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 }
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
-                                   int P, double mu, const double* fro2, const double* gw) {
+                                   int P, double mu, const double* fro2, const double* gw,
+                                   float* xh, float* xl) {
   pdl_wait();
   pdl_trigger();
   const int b = blockIdx.y;
@@ -74,8 +107,13 @@ __global__ void polar_start_kernel(const double* G, const double* W, double* X, 
   const double* w = W + b * elems;
   double* x = X + b * elems;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
-       i += (long long)gridDim.x * blockDim.x)
-    x[i] = (g[i] - s * w[i]) * inv;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (g[i] - s * w[i]) * inv;
+    x[i] = v;
+    // the FP32 pair of the double-float products, written here instead of
+    // by a separate split pass (one batch only)
+    if (xh) f64b::split(v, xh[i], xl[i]);
+  }
 }
 
 __global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, double c) {
@@ -109,13 +147,16 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
 }
 
 __global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
-                                    long long n, double alpha) {
+                                    long long n, double alpha, float* y32) {
   pdl_wait();
   pdl_trigger();
   const double* x = *sel ? x1 : x0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = alpha * x[i];
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = alpha * x[i];
+    y[i] = v;
+    if (y32) y32[i] = f64b::to_f32(v);
+  }
 }
 
 __global__ void symmetrize_kernel(double* A, int P) {
@@ -520,10 +561,19 @@ int batched_dot(const double* x, const double* y, long long n, long long stride,
   return 2;
 }
 
+int dot_self_and_cross(const double* x, const double* y, long long n, long long stride, int nb,
+                       double* out, double* scratch, cudaStream_t s) {
+  launch_k(dot2_partial_kernel, dim3(kDotBlocks, nb), 256, 0, s, x, y, n, stride, nb, scratch);
+  launch_k(dot_final_kernel, (2 * nb + 3) / 4, 128, 0, s, scratch, 2 * nb, out, nullptr);
+  return 2;
+}
+
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
-                double mu, const double* fro2, const double* gw, cudaStream_t s) {
-  launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P, mu,
-                                                                          fro2, gw);
+                double mu, const double* fro2, const double* gw, cudaStream_t s, float* xh,
+                float* xl) {
+  if (nb != 1) xh = xl = nullptr;
+  launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P,
+           mu, fro2, gw, xh, xl);
   return 1;
 }
 
@@ -544,8 +594,8 @@ int axpby(const double* x, double* y, long long n, double alpha, double beta, cu
 }
 
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
-                 double alpha, cudaStream_t s) {
-  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha);
+                 double alpha, cudaStream_t s, float* y32) {
+  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32);
   return 1;
 }
 

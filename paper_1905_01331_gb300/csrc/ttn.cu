@@ -974,11 +974,6 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   double* X2 = h->X2;
   double* fro2 = h->scal + 8;
   double* gw = fro2 + NJ;
-  if (!h->measuring) {
-    h->launches += batched_dot(Gam, Gam, PN, PN, NJ, fro2, h->red, h->stream);
-    h->launches += batched_dot(Gam, W, PN, PN, NJ, gw, h->red, h->stream);
-    h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream);
-  }
   // The polar factor is FP64 in every mode (the small singular directions
   // must not drown in tensor-core rounding).  FP64 mode, and layers too small
   // for the double-float products (P < 32, negligible cost): short blocks (at
@@ -994,10 +989,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // block's growth stays far below the tensor-core rounding of the
   // environment), then one more Newton-Schulz step X <- (1.5 I - 0.5 X X^T) X
   // that takes the isometry defect from ~1e-11 to ~1e-14.  Operands in FP32
-  // pairs: X in the one-leg scratch Y, F in Yt (both free during the polar
-  // step).  (Splitting X while the products load it instead of in a separate
-  // pass was measured slower: the products are issue-bound and the Gram
-  // product would split every element four to five times.)
+  // pairs, in the one-leg scratch Y and Yt (both free during the polar step).
   const bool df_ok = prec != 0 && h->opt.double_float && NJ == 1 && P >= 32 && schedp->size() > 1;
   // Adaptive schedule (polar_blocks 0 in the mixed modes, double-float
   // composition kernel): block 2 and the final step are cut short on the
@@ -1011,19 +1003,30 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   int* full = I.pfull + t;
   if (df_ok && !h->measuring && !adaptive)
     h->launches += store_ints(full, nullptr, 1, 1, h->stream);
-  float* Xh = reinterpret_cast<float*>(h->Y);
-  float* Xl = Xh + PN;
+  // X as FP32 pairs for the double-float products (hi at Xp, lo at Xp + PN),
+  // written by the kernel that produces X (the damped start, then every
+  // apply), in two buffers that alternate like X and X2; F as pairs in Yt.
+  // (Splitting X while the products load it was measured slower: the
+  // products are issue-bound and the Gram product would split every element
+  // four to five times.)
+  float* Xp = reinterpret_cast<float*>(h->Y);
+  float* Xp2 = reinterpret_cast<float*>(h->Y + PN);
   float* Fh = reinterpret_cast<float*>(h->Yt);
   float* Fl = Fh + PP;
+  if (!h->measuring) {
+    // fro2 and gw (= fro2 + NJ) from one pass over Gamma
+    h->launches += dot_self_and_cross(Gam, W, PN, PN, NJ, fro2, h->red, h->stream);
+    h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream,
+                               df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr);
+  }
   if (df_ok && h->measuring)
     h->partial_cap = std::max<size_t>(h->partial_cap, (size_t)df_gram_splits(P, (int)N) * PP);
   for (size_t bi = 0; bi < sched.size(); ++bi) {
     const PolarBlock& blk = sched[bi];
     const bool df = df_ok && !h->measuring;
     if (df) {
-      h->launches += df_split(X, Xh, Xl, PN, h->stream);
       df_begin(h);
-      df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream), df_gram_flops(P, N));
+      df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream), df_gram_flops(P, N));
       if (adaptive && bi + 1 == sched.size()) {
         // far (1): the last block and the final step run in full
         h->launches += store_ints(full, nullptr, 1, 0, h->stream);
@@ -1082,10 +1085,11 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // Newton-Schulz step from the Gram matrix still in pA (full == 0)
       const int* cut = adaptive && bi + 1 == sched.size() ? full : nullptr;
       df_begin(h);
-      df_end(h, df_apply(Fah, Fal, Xh, Xl, P, N, X2, h->stream, cut), 2.0 * P * P * (double)N,
-             cut);
+      df_end(h, df_apply(Fah, Fal, Xp, Xp + PN, P, N, X2, h->stream, cut, Xp2, Xp2 + PN),
+             2.0 * P * P * (double)N, cut);
+      // (no pairs after the short path: the final step's products do not run)
       if (cut)
-        h->launches += ns_correction(reinterpret_cast<const float*>(h->pP), X, Xh, P, N, X2, cut,
+        h->launches += ns_correction(reinterpret_cast<const float*>(h->pP), X, Xp, P, N, X2, cut,
                                      h->stream);
     } else {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
@@ -1093,15 +1097,16 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     run(h, f, 0);
     }
     std::swap(X, X2);
+    std::swap(Xp, Xp2);
   }
   const double* X_block = X;   // the last block's result
   if (df_ok && !h->measuring) {
     // (cut short: these products return at once and the result is X_block;
     // the defect flag below then reads the last block's Gram matrix, within
     // kPolarNear of I)
-    h->launches += df_split(X, Xh, Xl, PN, h->stream);
     df_begin(h);
-    df_end(h, df_gram(Xh, Xl, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N), full);
+    df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N),
+           full);
     // the final step converges quadratically only from |X X^T - I| << 1:
     // flag the instance when the blocks left it above 1e-5 (the isometry
     // would then miss 1e-10)
@@ -1109,15 +1114,18 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
     h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
     df_begin(h);
-    df_end(h, df_apply(Fh, Fl, Xh, Xl, P, N, X2, h->stream, full), 2.0 * P * P * (double)N, full);
+    df_end(h, df_apply(Fh, Fl, Xp, Xp + PN, P, N, X2, h->stream, full), 2.0 * P * P * (double)N,
+           full);
     std::swap(X, X2);
   }
   if (!h->measuring) {
-    if (df_ok)
-      h->launches += scale_select(X_block, X, full, W, NJ * PN, -1.0, h->stream);
-    else
+    if (df_ok) {
+      // W and its FP32 copy for the tensor-core products in one pass
+      h->launches += scale_select(X_block, X, full, W, NJ * PN, -1.0, h->stream, I.w32[t]);
+    } else {
       h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
-    if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
+      if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
+    }
   }
 }
 
