@@ -134,9 +134,15 @@ int dot_self_and_cross(const double* x, const double* y, long long n, long long 
 //   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
 // With xh, xl (one batch only) X is also written as FP32 pairs (xh = fl32(X),
 // xl = fl32(X - xh)) for the double-float products.
+// zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
                 int P, double mu, const double* fro2, const double* gw, cudaStream_t s,
-                float* xh = nullptr, float* xl = nullptr);
+                float* xh = nullptr, float* xl = nullptr, int* zero = nullptr);
+
+// For one P x P matrix A: (ph, pl) = FP32 pair of a I - c A (a = 0, c = -1:
+// of A itself, as df_split), and with flag: flag |= 1 when max |A - I| > thr.
+int check_split(const double* A, int P, double a, double c, float* ph, float* pl, double thr,
+                int* flag, cudaStream_t s);
 
 // Pm[b] = a I - c A[b] (P x P), nb batches.
 int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
@@ -207,6 +213,24 @@ struct ComposeArgs {
   const int* shortcut = nullptr;
 };
 bool compose_supported(int P, int nsteps);
+
+// The whole polar factor of a small layer in one CTA (mixed modes): every
+// block of the schedule -- Gram matrix, composed steps, apply -- on FP32 pairs
+// in shared memory.  X (P x N, FP64) is the damped, normalised start; W =
+// sign * result (FP64) and, with W32, its FP32 copy.  block_end[b] is one past
+// the last step of block b.
+constexpr int kSmallPolarMaxP = 32, kSmallPolarMaxBlocks = 16;
+struct SmallPolarArgs {
+  const double* X;
+  double* W;
+  float* W32;
+  int P, N, nblocks;
+  int block_end[kSmallPolarMaxBlocks];
+  double alpha[kMaxComposeSteps], beta[kMaxComposeSteps];
+  double sign;
+};
+bool small_polar_supported(int P, long long N, int nblocks, int nsteps);
+int small_polar(const SmallPolarArgs& a, cudaStream_t s);
 // Flops the composition kernel executes (all tiles of every product).
 double compose_flops(int P, int NJ, int nsteps);
 // Returns the number of kernel launches (1), or -1 if the launch was refused.
@@ -288,15 +312,13 @@ int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl,
 int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
                   double* C, const int* full, cudaStream_t s);
 
-// dst[i] = (float) src[i]
-int to_f32(const double* src, float* dst, long long n, cudaStream_t s);
-
 // Energy change per spin after a sweep (Sec. IV convergence test): dstat =
 // [previous energy, change per spin, tolerance], istat[2] = converged,
 // istat[3] = sweeps seen (the first is compared with nothing).
 int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cudaStream_t s);
-// flag[0] |= 1 when max |A - I| (P x P) exceeds thr or is not a number.
-int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s);
+
+// dst[i] = (float) src[i]
+int to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 // dst[i] = src ? src[i] : value for i < n.
 int store_ints(int* dst, const int* src, int n, int value, cudaStream_t s);
 // One CTA: out = [sum of traces, max |M - I| (or |M|), max |M - M^T|] over nb

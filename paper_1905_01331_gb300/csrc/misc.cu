@@ -95,9 +95,10 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
                                    int P, double mu, const double* fro2, const double* gw,
-                                   float* xh, float* xl) {
+                                   float* xh, float* xl, int* zero) {
   pdl_wait();
   pdl_trigger();
+  if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int b = blockIdx.y;
   const double f2 = fro2[b];
   const double s = mu * sqrt(f2);
@@ -490,18 +491,24 @@ __global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, d
 }
 
 // flag[0] |= 1 when max |A - I| of the P x P matrix A exceeds thr (one CTA).
-__global__ void far_from_identity_kernel(const double* A, int P, double thr, int* flag) {
+// For a P x P matrix A: the FP32 pair (ph, pl) of a I - c A (with a = 0,
+// c = -1: of A itself), and, with flag, flag |= 1 when max |A - I| > thr
+// (NaN counts as far).  Grid-stride over the elements, a warp vote per pass.
+__global__ void check_split_kernel(const double* A, int P, double a, double c, float* ph, float* pl,
+                                   double thr, int* flag) {
   pdl_wait();
   pdl_trigger();
-  // one CTA per row block of 8 rows, a warp per row
-  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-  int mine = 0;
-  if (i < P)
-    for (int j = threadIdx.x & 31; j < P; j += 32) {
-      const double d = A[(long long)i * P + j] - (i == j ? 1.0 : 0.0);
-      if (!(fabs(d) <= thr)) mine = 1;   // NaN counts as far
-    }
-  if (__any_sync(0xffffffffu, mine) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+  const long long PP = (long long)P * P;
+  int far = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / P), j = (int)(e % P);
+    const double x = A[e];
+    if (flag && !(fabs(x - (i == j ? 1.0 : 0.0)) <= thr)) far = 1;
+    const double v = c == -1.0 && a == 0.0 ? x : (i == j ? a : 0.0) - c * x;
+    f64b::split(v, ph[e], pl[e]);
+  }
+  if (flag && __any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 __global__ void store_ints_kernel(int* dst, const int* src, int n, int value) {
@@ -570,10 +577,17 @@ int dot_self_and_cross(const double* x, const double* y, long long n, long long 
 
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
                 double mu, const double* fro2, const double* gw, cudaStream_t s, float* xh,
-                float* xl) {
+                float* xl, int* zero) {
   if (nb != 1) xh = xl = nullptr;
   launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P,
-           mu, fro2, gw, xh, xl);
+           mu, fro2, gw, xh, xl, zero);
+  return 1;
+}
+
+int check_split(const double* A, int P, double a, double c, float* ph, float* pl, double thr,
+                int* flag, cudaStream_t s) {
+  launch_k(check_split_kernel, grid_for((long long)P * P, 256, 64), 256, 0, s, A, P, a, c, ph, pl,
+           thr, flag);
   return 1;
 }
 
@@ -714,11 +728,6 @@ int to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
 
 int sweep_delta(const double* E, double* dstat, int* istat, double inv_spins, cudaStream_t s) {
   launch_k(sweep_delta_kernel, 1, 1, 0, s, E, dstat, istat, inv_spins);
-  return 1;
-}
-
-int flag_if_far_from_identity(const double* A, int P, double thr, int* flag, cudaStream_t s) {
-  launch_k(far_from_identity_kernel, (P + 7) / 8, 256, 0, s, A, P, thr, flag);
   return 1;
 }
 

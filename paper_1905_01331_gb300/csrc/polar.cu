@@ -416,7 +416,117 @@ int compose_grid_cap(bool df) {
   return g.sms * (df ? g.per_sm_df : g.per_sm);
 }
 
+constexpr int kSPThreads = 256;
+
+// c[i][j] = sum_k x[i * xs_i + k * xs_k] y[k * ys_k + j * ys_j] over k < K in
+// pair arithmetic (renormalised every 8 terms), for the (i, j) this thread owns.
+__device__ __forceinline__ void sp_dot(const float* xh, const float* xl, int xs_i, int xs_k,
+                                      const float* yh, const float* yl, int ys_k, int ys_j, int i,
+                                      int j, int K, float& vh, float& vl) {
+  float sh = 0.f, sl = 0.f;
+  for (int k = 0; k < K; ++k) {
+    pair_mac(xh[i * xs_i + k * xs_k], xl[i * xs_i + k * xs_k], yh[k * ys_k + j * ys_j],
+             yl[k * ys_k + j * ys_j], sh, sl);
+    if ((k & 7) == 7) pair_renorm(sh, sl);
+  }
+  pair_renorm(sh, sl);
+  vh = sh;
+  vl = sl;
+}
+
+// One CTA; all matrices as FP32 pairs in shared memory: X (P x N), A, F, Pm,
+// T, U (P x P).  Per block: A = X X^T; F = I; per step Pm = alpha I - beta A,
+// F <- Pm F and (not in the last step) A <- Pm (A Pm); then X <- F X.
+__global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPolarArgs a) {
+  extern __shared__ __align__(16) float spm[];
+  const int P = a.P, N = a.N, PP = P * P, PN = P * N;
+  float* Xh = spm;
+  float* Xl = Xh + PN;
+  float* Yh = Xl + PN;   // F X, before it replaces X
+  float* Yl = Yh + PN;
+  float* Ah = Yl + PN;
+  float* Al = Ah + PP;
+  float* Fh = Al + PP;
+  float* Fl = Fh + PP;
+  float* Mh = Fl + PP;   // Pm
+  float* Ml = Mh + PP;
+  float* Th = Ml + PP;   // A Pm, then the new F
+  float* Tl = Th + PP;
+  for (int e = threadIdx.x; e < PN; e += kSPThreads) split_d(a.X[e], Xh[e], Xl[e]);
+  __syncthreads();
+  int step = 0;
+  for (int b = 0; b < a.nblocks; ++b) {
+    for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+      const int i = e / P, j = e % P;
+      sp_dot(Xh, Xl, N, 1, Xh, Xl, 1, N, i, j, N, Ah[e], Al[e]);
+      Fh[e] = i == j ? 1.f : 0.f;
+      Fl[e] = 0.f;
+    }
+    __syncthreads();
+    const int last = a.block_end[b] - 1;
+    for (; step <= last; ++step) {
+      float ah, al, bh, bl;
+      split_d(a.alpha[step], ah, al);
+      split_d(-a.beta[step], bh, bl);
+      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+        float h, l;
+        pair_mul(Ah[e], Al[e], bh, bl, h, l);
+        if (e / P == e % P) pair_add(h, l, ah, al, h, l);
+        Mh[e] = h;
+        Ml[e] = l;
+      }
+      __syncthreads();
+      // new F into T (Pm F), and, not in the last step, A Pm into ... F's old
+      // slot is still read, so A Pm goes to the X-sized scratch Y
+      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+        const int i = e / P, j = e % P;
+        sp_dot(Mh, Ml, P, 1, Fh, Fl, P, 1, i, j, P, Th[e], Tl[e]);
+        if (step < last) sp_dot(Ah, Al, P, 1, Mh, Ml, P, 1, i, j, P, Yh[e], Yl[e]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+        Fh[e] = Th[e];
+        Fl[e] = Tl[e];
+        if (step < last) {
+          const int i = e / P, j = e % P;
+          sp_dot(Mh, Ml, P, 1, Yh, Yl, P, 1, i, j, P, Ah[e], Al[e]);
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+      const int i = e / N, j = e % N;
+      sp_dot(Fh, Fl, P, 1, Xh, Xl, N, 1, i, j, P, Yh[e], Yl[e]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+      Xh[e] = Yh[e];
+      Xl[e] = Yl[e];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+    const double w = a.sign * ((double)Xh[e] + (double)Xl[e]);
+    a.W[e] = w;
+    if (a.W32) a.W32[e] = (float)w;
+  }
+}
+
 }  // namespace
+
+bool small_polar_supported(int P, long long N, int nblocks, int nsteps) {
+  // everything in the default 48 KB of shared memory: 4 P N + 8 P^2 floats
+  return P >= 1 && P <= kSmallPolarMaxP && N >= P && (4 * P * N + 8LL * P * P) * 4 <= 48 * 1024 &&
+         nblocks >= 1 && nblocks <= kSmallPolarMaxBlocks && nsteps >= 1 &&
+         nsteps <= kMaxComposeSteps;
+}
+
+int small_polar(const SmallPolarArgs& a, cudaStream_t s) {
+  if (!small_polar_supported(a.P, a.N, a.nblocks, a.block_end[a.nblocks - 1])) return -1;
+  const size_t smem = (4 * (size_t)a.P * a.N + 8 * (size_t)a.P * a.P) * sizeof(float);
+  launch_k(small_polar_kernel, 1, kSPThreads, smem, s, a);
+  return 1;
+}
 
 bool compose_supported(int P, int nsteps) {
   return P >= 1 && P <= kCMaxP && nsteps >= 1 && nsteps <= kMaxComposeSteps;

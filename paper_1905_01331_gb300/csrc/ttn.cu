@@ -1016,8 +1016,36 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   if (!h->measuring) {
     // fro2 and gw (= fro2 + NJ) from one pass over Gamma
     h->launches += dot_self_and_cross(Gam, W, PN, PN, NJ, fro2, h->red, h->stream);
+    // (the adaptive schedule's flag starts at 0: the check before the last
+    // block ORs 1 into it when that block and the final step must run)
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream,
-                               df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr);
+                               df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr,
+                               adaptive ? full : nullptr);
+  }
+  // Mixed modes, layers with P < 32 (short blocks): the whole factor in one
+  // CTA in pair arithmetic (small_polar) instead of a Gram, a composition and
+  // an apply launch per block, then the update and its FP32 copy.
+  int nsteps = 0;
+  for (const auto& b : sched) nsteps += (int)b.steps.size();
+  if (prec != 0 && short_blocks && NJ == 1 && (h->opt.persistent & 1) &&
+      small_polar_supported(P, N, (int)sched.size(), nsteps)) {
+    if (h->measuring) return;
+    SmallPolarArgs sa;
+    sa.X = X; sa.W = W; sa.W32 = I.w32[t];
+    sa.P = P; sa.N = (int)N; sa.nblocks = (int)sched.size(); sa.sign = -1.0;
+    int k = 0;
+    for (size_t b = 0; b < sched.size(); ++b) {
+      for (const auto& st : sched[b].steps) {
+        sa.alpha[k] = st.first;
+        sa.beta[k] = st.second;
+        ++k;
+      }
+      sa.block_end[b] = k;
+    }
+    const int n = small_polar(sa, h->stream);
+    if (n < 0) h->compose_refused = true;
+    else h->launches += n;
+    return;
   }
   if (df_ok && h->measuring)
     h->partial_cap = std::max<size_t>(h->partial_cap, (size_t)df_gram_splits(P, (int)N) * PP);
@@ -1027,11 +1055,6 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     if (df) {
       df_begin(h);
       df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream), df_gram_flops(P, N));
-      if (adaptive && bi + 1 == sched.size()) {
-        // far (1): the last block and the final step run in full
-        h->launches += store_ints(full, nullptr, 1, 0, h->stream);
-        h->launches += flag_if_far_from_identity(h->pA, P, kPolarNear, full, h->stream);
-      }
     } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
@@ -1041,8 +1064,13 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     }
     const bool kernel = (h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size());
     if (kernel) {
-      if (df) h->launches += df_split(h->pA, reinterpret_cast<float*>(h->pP),
-                                      reinterpret_cast<float*>(h->pP) + PP, PP, h->stream);
+      // A_0 as pairs for the composition; before the adaptive schedule's last
+      // block also the test max |X X^T - I| > kPolarNear (far: 1 into the
+      // flag, the block and the final step run in full)
+      if (df)
+        h->launches += check_split(h->pA, P, 0.0, -1.0, reinterpret_cast<float*>(h->pP),
+                                   reinterpret_cast<float*>(h->pP) + PP, kPolarNear,
+                                   adaptive && bi + 1 == sched.size() ? full : nullptr, h->stream);
       if (!h->measuring)
         compose_block(h, blk, P, NJ, df, adaptive && bi + 1 == sched.size() ? full : nullptr);
     } else {
@@ -1107,12 +1135,11 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     df_begin(h);
     df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N),
            full);
-    // the final step converges quadratically only from |X X^T - I| << 1:
-    // flag the instance when the blocks left it above 1e-5 (the isometry
-    // would then miss 1e-10)
-    h->launches += flag_if_far_from_identity(h->pA, P, 1e-5, I.istat + 4, h->stream);
-    h->launches += poly_step_matrix(h->pA, h->pF, P, 1, 1.5, 0.5, h->stream);
-    h->launches += df_split(h->pF, Fh, Fl, PP, h->stream);
+    // F = 1.5 I - 0.5 X X^T as pairs; the final step converges quadratically
+    // only from |X X^T - I| << 1, so the same pass over the Gram matrix flags
+    // the instance when the blocks left it above 1e-5 (the isometry would then
+    // miss 1e-10)
+    h->launches += check_split(h->pA, P, 1.5, 0.5, Fh, Fl, 1e-5, I.istat + 4, h->stream);
     df_begin(h);
     df_end(h, df_apply(Fh, Fl, Xp, Xp + PN, P, N, X2, h->stream, full), 2.0 * P * P * (double)N,
            full);
