@@ -142,7 +142,8 @@ __device__ __forceinline__ void tile_fma(const LzSmem& sm, int c, double& a0, do
 // Reduce the per-warp partial sums of a tile in warp order and store it,
 // minus sigma X when sigma != 0 (the shifted operator H - sigma I).
 __device__ void tile_store(LzSmem& sm, double a0, double a1, double* C, int c, int i0, int j0,
-                           const double* X = nullptr, double sigma = 0.0) {
+                           const double* X = nullptr, double sigma = 0.0,
+                           const double* Xprev = nullptr, double beta = 0.0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = lane >> 2, j = (lane & 3) * 2;
   sm.red[warp][i * kLT + j] = a0;
@@ -155,6 +156,7 @@ __device__ void tile_store(LzSmem& sm, double a0, double a1, double* C, int c, i
     if (i0 + r < c && j0 + cc < c) {
       const long long e = (long long)(i0 + r) * c + j0 + cc;
       if (sigma != 0.0) v = fma(-sigma, __ldcg(X + e), v);
+      if (beta != 0.0) v = fma(-beta, __ldcg(Xprev + e), v);
       __stcg(C + e, v);
     }
   }
@@ -457,7 +459,8 @@ __device__ __forceinline__ void tile_fma_p(LzSmem& sm, int c, float& a0h, float&
 // pairs (Cp) or as FP64 (Cd, minus sigma X when sigma != 0).
 __device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float a1l, float* Cp,
                              double* Cd, long long n, int c, int i0, int j0,
-                             const double* X = nullptr, double sigma = 0.0) {
+                             const double* X = nullptr, double sigma = 0.0,
+                             const double* Xprev = nullptr, double beta = 0.0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = lane >> 2, j = (lane & 3) * 2;
   float* rh = reinterpret_cast<float*>(&sm.red[0][0]);
@@ -477,6 +480,7 @@ __device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float 
       if (Cd) {
         double v = (double)vh + (double)vl;
         if (sigma != 0.0) v = fma(-sigma, __ldcg(X + e), v);
+        if (beta != 0.0) v = fma(-beta, __ldcg(Xprev + e), v);
         __stcg(Cd + e, v);
       }
     }
@@ -661,8 +665,20 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
     // would dwarf beta_j^2 and every step would need the second
     // Gram-Schmidt pass.
     double sigma = 0.0;
+    // Step j >= 1 also subtracts, while w is stored, the two recurrence terms
+    // it knows: sigma_j x_j with sigma_j = alpha_{j-1} of H (the previous
+    // step's diagonal entry, close to this one's) and beta_{j-1} x_{j-1}.  The
+    // projections then only remove what is left (rounding and the small
+    // alpha_j - sigma_j), so the one-pass test below passes in most steps and
+    // the second Gram-Schmidt pass with its two grid barriers is skipped.  The
+    // tridiagonal keeps the single shift sigma: its entry j is
+    // c_j + sigma_j - sigma.
+    double alpha_prev_h = 0.0;
     for (int j = 0; j < m; ++j) {
       const double* x = a.basis + (long long)j * n;
+      const double sigma_j = j == 0 ? 0.0 : (j == 1 ? sigma : alpha_prev_h);
+      const double* xprev = j > 0 ? x - n : nullptr;
+      const double beta_j1 = j > 0 ? beta_prev : 0.0;
       // phase A: Y_b = Op_b x for the 2K operators A_k0, B_k0 (stored after o_0)
       const float* xp = df ? a.bp + 2 * (long long)j * n : nullptr;
       for (int it = bid; it < 2 * K * ntiles; it += G) {
@@ -707,7 +723,8 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
           tile_fma_p(sm, c, a0h, a0l, a1h, a1l);
           __syncthreads();
         }
-        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0, x, sigma);
+        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0, x, sigma_j, xprev,
+                     beta_j1);
       }
       for (int t = bid; t < ntiles && !df; t += G) {
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
@@ -729,7 +746,7 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
           tile_fma(sm, c, a0, a1);
           __syncthreads();
         }
-        tile_store(sm, a0, a1, a.w, c, i0, j0, x, sigma);
+        tile_store(sm, a0, a1, a.w, c, i0, j0, x, sigma_j, xprev, beta_j1);
       }
       own_projections(a, part, ldp, j, nslot, nown, bid, G, nt, c, n);
       if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
@@ -788,7 +805,10 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
       if (j == 0) {
         sigma = alpha_j;
         alpha_j = 0.0;
+      } else {
+        alpha_j += sigma_j - sigma;
       }
+      alpha_prev_h = alpha_j + sigma;
       tdim = j + 1;
       const bool breakdown = !(beta_j > 1e-12 * fmax(fabs(alpha_j + sigma) + beta_prev, 1e-300));
       if (bid == 0 && threadIdx.x == 0) {
