@@ -191,21 +191,44 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     }
 }
 
-// C[m][n] = sum_s part[s][m][n] in split order; for a symmetric product the
-// tiles below the diagonal were not computed and are read from the mirror.
+// C[m][n] = sum_s part[s][m][n]; for a symmetric product the tiles below the
+// diagonal were not computed and are read from the mirror.  A CTA owns 32
+// consecutive outputs; its 8 warps each sum a contiguous eighth of the splits
+// in order (loads in flight together), warp 0 adds the eight sums in group
+// order (a fixed order of terms).
 __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, int tile, int sym,
                                  double* C, long long ldc, const int* run_if) {
   pdl_wait();
   pdl_trigger();
   if (run_if && *run_if == 0) return;
+  __shared__ double gs[8][32];
   const long long MN = (long long)M * N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / N), n = (int)(e % N);
-    const long long src = (sym && m / tile > n / tile) ? (long long)n * N + m : e;
-    double s = 0.0;
-    for (int sp = 0; sp < splits; ++sp) s += part[sp * MN + src];
-    C[m * ldc + n] = s;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int s_lo = (int)((long long)splits * g / 8), s_hi = (int)((long long)splits * (g + 1) / 8);
+  for (long long e0 = blockIdx.x * 32LL; e0 < MN; e0 += gridDim.x * 32LL) {
+    const long long e = e0 + lane;
+    double acc = 0.0;
+    int m = 0, n = 0;
+    if (e < MN) {
+      m = (int)(e / N);
+      n = (int)(e % N);
+      const long long src = (sym && m / tile > n / tile) ? (long long)n * N + m : e;
+      for (int sp0 = s_lo; sp0 < s_hi; sp0 += 8) {
+        double xs[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xs[q] = sp0 + q < s_hi ? part[(sp0 + q) * MN + src] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += xs[q];
+      }
+    }
+    gs[g][lane] = acc;
+    __syncthreads();
+    if (g == 0 && e < MN) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += gs[q][lane];
+      C[m * ldc + n] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -323,8 +346,8 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
       Xh, Xl, n2, Xh, Xl, n2, P, P, (int)n2, C, P, part, splits, 1, run_if, nullptr, nullptr);
   int launches = 1;
   if (splits > 1) {
-    launch_k(df_reduce_kernel, grid_n((long long)P * P), 256, 0, s, part, splits, P, P, GB, 1, C, P,
-                                                             run_if);
+    launch_k(df_reduce_kernel, (int)std::min<long long>(((long long)P * P + 31) / 32, 8192), 256,
+             0, s, part, splits, P, P, GB, 1, C, P, run_if);
     ++launches;
   }
   return launches;

@@ -634,40 +634,62 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
 }
 
 // C = alpha sum_s part[s] + beta C over the FP32 partials of the K splits,
-// summed in split order as an FP32 pair (error-free two-sum, low parts
-// accumulated), then rounded to FP32.
+// as an FP32 pair (error-free two-sum, low parts accumulated), then rounded
+// to FP32.  A CTA owns 32 consecutive outputs; its 8 warps each sum a
+// contiguous eighth of the splits in order (all of a warp's loads in flight
+// together), and warp 0 adds the eight pairs in group order: a fixed order of
+// terms, with 8x the parallelism of one thread per output.
 __global__ void splitk_reduce_tc(const GemmDesc d) {
   pdl_wait();
   pdl_trigger();
   if (d.skip && *d.skip) return;
+  __shared__ float gh[8][32], gl[8][32];
   const long long MN = static_cast<long long>(d.M) * d.N;
   const long long total = MN * d.B0 * d.B1;
   const float* part = reinterpret_cast<const float*>(d.partial);
   const float af = static_cast<float>(d.alpha), bf = static_cast<float>(d.beta);
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long b = e / MN, r = e % MN;
-    const int m = static_cast<int>(r / d.N), n = static_cast<int>(r % d.N);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int s_lo = static_cast<int>(static_cast<long long>(d.splits) * g / 8);
+  const int s_hi = static_cast<int>(static_cast<long long>(d.splits) * (g + 1) / 8);
+  const long long step = static_cast<long long>(d.B0) * d.B1 * MN;
+  for (long long e0 = blockIdx.x * 32LL; e0 < total; e0 += gridDim.x * 32LL) {
+    const long long e = e0 + lane;
     float sh = 0.f, sl = 0.f;
-    const long long step = static_cast<long long>(d.B0) * d.B1 * MN;
-    const float* pe = part + b * MN + r;
-    // partials loaded eight at a time (independent loads in flight), summed in
-    // split order
-    for (int sp0 = 0; sp0 < d.splits; sp0 += 8) {
-      float xs[8];
+    if (e < total) {
+      const float* pe = part + e;   // partial s of element e at part + s * step + e
+      for (int sp0 = s_lo; sp0 < s_hi; sp0 += 8) {
+        float xs[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xs[q] = sp0 + q < d.splits ? pe[(sp0 + q) * step] : 0.f;
+        for (int q = 0; q < 8; ++q) xs[q] = sp0 + q < s_hi ? pe[(sp0 + q) * step] : 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float x = xs[q];
-        const float s = sh + x, bb = s - sh;
-        sl += (sh - (s - bb)) + (x - bb);
-        sh = s;
+        for (int q = 0; q < 8; ++q) {
+          const float x = xs[q];
+          const float s = sh + x, bb = s - sh;
+          sl += (sh - (s - bb)) + (x - bb);
+          sh = s;
+        }
       }
     }
-    const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
-    const long long ce = b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
-    store_out(d, ce, sh + sl, af, bf);
+    gh[g][lane] = sh;
+    gl[g][lane] = sl;
+    __syncthreads();
+    if (g == 0 && e < total) {
+      float th = 0.f, tl = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const float x = gh[q][lane];
+        const float s = th + x, bb = s - th;
+        tl += (th - (s - bb)) + (x - bb);
+        th = s;
+        tl += gl[q][lane];
+      }
+      const long long b = e / MN, r = e % MN;
+      const int m = static_cast<int>(r / d.N), n = static_cast<int>(r % d.N);
+      const int b0 = static_cast<int>(b % d.B0), b1 = static_cast<int>(b / d.B0);
+      const long long ce =
+          b0 * d.sc_b0 + static_cast<long long>(b1) * d.sc_b1 + m * d.sc_m + n * d.sc_n;
+      store_out(d, ce, th + tl, af, bf);
+    }
+    __syncthreads();
   }
 }
 
@@ -1269,7 +1291,7 @@ int gemm_tc_launch(const GemmDesc& d, cudaStream_t s) {
   }
   if (d.splits > 1) {
     const long long total = static_cast<long long>(d.M) * d.N * d.B0 * d.B1;
-    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 4096));
+    const int blocks = static_cast<int>(std::min<long long>((total + 31) / 32, 8192));
     launch_k(splitk_reduce_tc, blocks, 256, 0, s, d);
     ++n;
   }

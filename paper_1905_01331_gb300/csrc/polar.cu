@@ -419,19 +419,30 @@ int compose_grid_cap(bool df) {
 constexpr int kSPThreads = 256;
 
 // c[i][j] = sum_k x[i * xs_i + k * xs_k] y[k * ys_k + j * ys_j] over k < K in
-// pair arithmetic (renormalised every 8 terms), for the (i, j) this thread owns.
+// pair arithmetic, for the (i, j) this thread owns: even and odd k in two
+// independent accumulators (half the dependent chain), each renormalised
+// every 8 terms, added at the end.
 __device__ __forceinline__ void sp_dot(const float* xh, const float* xl, int xs_i, int xs_k,
                                       const float* yh, const float* yl, int ys_k, int ys_j, int i,
                                       int j, int K, float& vh, float& vl) {
-  float sh = 0.f, sl = 0.f;
-  for (int k = 0; k < K; ++k) {
+  float sh0 = 0.f, sl0 = 0.f, sh1 = 0.f, sl1 = 0.f;
+  int k = 0;
+  for (; k + 1 < K; k += 2) {
     pair_mac(xh[i * xs_i + k * xs_k], xl[i * xs_i + k * xs_k], yh[k * ys_k + j * ys_j],
-             yl[k * ys_k + j * ys_j], sh, sl);
-    if ((k & 7) == 7) pair_renorm(sh, sl);
+             yl[k * ys_k + j * ys_j], sh0, sl0);
+    pair_mac(xh[i * xs_i + (k + 1) * xs_k], xl[i * xs_i + (k + 1) * xs_k],
+             yh[(k + 1) * ys_k + j * ys_j], yl[(k + 1) * ys_k + j * ys_j], sh1, sl1);
+    if ((k & 15) == 14) {
+      pair_renorm(sh0, sl0);
+      pair_renorm(sh1, sl1);
+    }
   }
-  pair_renorm(sh, sl);
-  vh = sh;
-  vl = sl;
+  if (k < K)
+    pair_mac(xh[i * xs_i + k * xs_k], xl[i * xs_i + k * xs_k], yh[k * ys_k + j * ys_j],
+             yl[k * ys_k + j * ys_j], sh0, sl0);
+  pair_renorm(sh0, sl0);
+  pair_renorm(sh1, sl1);
+  pair_add(sh0, sl0, sh1, sl1, vh, vl);
 }
 
 // One CTA; all matrices as FP32 pairs in shared memory: X (P x N), A, F, Pm,
