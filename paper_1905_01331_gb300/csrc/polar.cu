@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
   float* S = reinterpret_cast<float*>(a.S);
   float* T = reinterpret_cast<float*>(a.T);
   // the previous block already left X X^T within its threshold of I: the
-  // block is one Newton-Schulz step, applied by ns_correction instead (every
-  // CTA reads the same flag, so none reaches a grid barrier)
+  // block is one Newton-Schulz step, applied by its FP32 correction instead
+  // (every CTA reads the same flag, so none reaches a grid barrier)
   if (a.shortcut && *a.shortcut == 0) return;
   auto Fbuf = [&](int j) { return ((ns - j) & 1) ? S : F; };
   unsigned target = 0;

@@ -58,6 +58,13 @@ Operand mk(const double* p, long long mn, long long k0, long long k1 = 0, long l
   return o;
 }
 
+Operand mk32(const float* p, long long mn, long long k0) {
+  Operand o = mk(nullptr, mn, k0);
+  o.p = p;
+  o.f32 = 1;
+  return o;
+}
+
 int lg(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
 
 }  // namespace
@@ -253,8 +260,10 @@ extern "C" size_t ttn_selftest_bytes(void) {
 // (gemm_df.cu) against the FP64 engine on seeded operands.  Cases: Gram X X^T
 // for (P, n2) = (128, 16384) (split K) and (96, 1000) (ragged); apply F X for
 // (128, 16384) and (40, 1000); with n_out >= 5, out_rel[4] the Newton-Schulz
-// step near convergence (ns_correction, A = I + 1e-10 (F + F^T) / 2, P = 128,
-// n2 = 16384) against (1.5 I - 0.5 A) X in FP64.
+// step near convergence as the adaptive polar schedule takes it (D = 0.5 (I - A)
+// from check_split, the correction D X as a 3xTF32 tensor-core product on X's
+// FP32 head, X added in FP64 by scale_select; A = I + 1e-10 (F + F^T) / 2,
+// P = 128, n2 = 16384) against (1.5 I - 0.5 A) X in FP64.
 // out_rel[i] = max |C_df - C_fp64| / max |C_fp64|.
 extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_out,
                                void* stream) {
@@ -281,6 +290,8 @@ extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_
   double* Aq = take(128 * 128);
   double* Fm = take(128 * 128);
   int* zero = reinterpret_cast<int*>(take(1));
+  float* D32 = reinterpret_cast<float*>(take(128 * 128 / 2));
+  float* Corr = reinterpret_cast<float*>(take(big / 2));
   if (off > cap) return TTN_ENOMEM;
   fill_uniform<<<592, 256, 0, s>>>(X, big, 31);
   fill_uniform<<<64, 256, 0, s>>>(F, 128 * 128, 37);
@@ -339,8 +350,18 @@ extern "C" int ttn_selftest_df(void* d_ws, size_t bytes, double* out_rel, int n_
     r.splits = 1;
     gemm_launch(r, s);
     df_split(X, Xp, Xp + PN, PN, s);
-    df_split(Aq, Fp, Fp + (long long)P * P, (long long)P * P, s);
-    ns_correction(Fp, X, Xp, P, n2, C2, zero, s);
+    check_split(Aq, P, 0.0, -1.0, Fp, Fp + (long long)P * P, 1.0, nullptr, s, D32);
+    GemmDesc t;
+    memset(&t, 0, sizeof(t));
+    t.B0 = 1; t.B1 = 1; t.alpha = 1.0; t.prec = TTN_TF32X3; t.C = Corr; t.c_f32 = 1;
+    t.sc_n = 1; t.sc_m = n2; t.M = P; t.N = (int)n2; t.partial = partial;
+    Group g2;
+    g2.a = mk32(D32, P, 1); g2.b = mk32(Xp, 1, n2); g2.K = P; g2.k0_log2 = lg(P);
+    t.g[t.ngroups++] = g2;
+    t.splits = gemm_pick_splits(t);
+    if (gemm_partial_elems(t, t.splits) > 128 * 128 * 128) t.splits = 1;
+    gemm_launch(t, s);
+    scale_select(X, X, zero, C2, PN, 1.0, s, nullptr, Corr);
     max_abs_diff<<<1, 256, 0, s>>>(C2, C1, (long long)P * n2, res);
     cudaMemcpyAsync(host.data(), res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return TTN_ECUDA;

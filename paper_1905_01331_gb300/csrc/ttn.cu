@@ -1013,6 +1013,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   float* Xp2 = reinterpret_cast<float*>(h->Y + PN);
   float* Fh = reinterpret_cast<float*>(h->Yt);
   float* Fl = Fh + PP;
+  // the adaptive short path: D = 0.5 (I - X X^T) (FP32, in the composition's
+  // scratch pT) and its correction D X (FP32, after F in Yt); X_short is the
+  // last block's input
+  float* Dc = reinterpret_cast<float*>(h->pT);
+  float* Corr = Fh + 2 * PP;
+  const double* X_short = X;
   if (!h->measuring) {
     // fro2 and gw (= fro2 + NJ) from one pass over Gamma
     h->launches += dot_self_and_cross(Gam, W, PN, PN, NJ, fro2, h->red, h->stream);
@@ -1067,10 +1073,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // A_0 as pairs for the composition; before the adaptive schedule's last
       // block also the test max |X X^T - I| > kPolarNear (far: 1 into the
       // flag, the block and the final step run in full)
+      // (and D = 0.5 (I - X X^T) in FP32 for the short path's correction)
       if (df)
         h->launches += check_split(h->pA, P, 0.0, -1.0, reinterpret_cast<float*>(h->pP),
                                    reinterpret_cast<float*>(h->pP) + PP, kPolarNear,
-                                   adaptive && bi + 1 == sched.size() ? full : nullptr, h->stream);
+                                   adaptive && bi + 1 == sched.size() ? full : nullptr, h->stream,
+                                   adaptive && bi + 1 == sched.size() ? Dc : nullptr);
       if (!h->measuring)
         compose_block(h, blk, P, NJ, df, adaptive && bi + 1 == sched.size() ? full : nullptr);
     } else {
@@ -1115,23 +1123,28 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       df_begin(h);
       df_end(h, df_apply(Fah, Fal, Xp, Xp + PN, P, N, X2, h->stream, cut, Xp2, Xp2 + PN),
              2.0 * P * P * (double)N, cut);
-      // (no pairs after the short path: the final step's products do not run)
-      if (cut)
-        h->launches += ns_correction(reinterpret_cast<const float*>(h->pP), X, Xp, P, N, X2, cut,
-                                     h->stream);
     } else {
     GemmDesc f = desc(P, (int)N, 1, NJ, X2, N, 1, 0, PN);
     add(f, grp(op(h->pF, P, 1, 0, 0, PP), op(X, 1, N, 0, 0, PN), P));
     run(h, f, 0);
     }
+    if (adaptive && bi + 1 == sched.size()) {
+      // short path (full == 0): the block is one Newton-Schulz step,
+      // X + 0.5 (I - X X^T) X; its correction D X (entries <= 5e-10 of X)
+      // needs FP32 accuracy only: a 3xTF32 tensor-core product on X's FP32
+      // head, added to X in FP64 when W is written (skipped when full == 1)
+      GemmDesc c = desc(P, (int)N, 1, 1, TP{Corr, 1}, N, 1, 0, 0);
+      add(c, grp(op(TP{Dc, 1}, P, 1), op(TP{Xp, 1}, 1, N), P));
+      c.skip = full;
+      run(h, c, TTN_TF32X3);
+      X_short = X;
+    }
     std::swap(X, X2);
     std::swap(Xp, Xp2);
   }
-  const double* X_block = X;   // the last block's result
   if (df_ok && !h->measuring) {
-    // (cut short: these products return at once and the result is X_block;
-    // the defect flag below then reads the last block's Gram matrix, within
-    // kPolarNear of I)
+    // (cut short: these products return at once; the defect flag below then
+    // reads the last block's Gram matrix, within kPolarNear of I)
     df_begin(h);
     df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N),
            full);
@@ -1147,8 +1160,11 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   }
   if (!h->measuring) {
     if (df_ok) {
-      // W and its FP32 copy for the tensor-core products in one pass
-      h->launches += scale_select(X_block, X, full, W, NJ * PN, -1.0, h->stream, I.w32[t]);
+      // W and its FP32 copy for the tensor-core products in one pass: from the
+      // final step's result (full == 1), or from the last block's input plus
+      // the short path's correction (full == 0)
+      h->launches += scale_select(adaptive ? X_short : X, X, full, W, NJ * PN, -1.0, h->stream,
+                                  I.w32[t], adaptive ? Corr : nullptr);
     } else {
       h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
       if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);

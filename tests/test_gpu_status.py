@@ -107,9 +107,10 @@ def test_double_float_engine_matches_fp64():
     on seeded operands (uniform in [-1, 1], K up to 16384): the host pin of the
     same arithmetic measures ~3e-14 of sum |a b|; FP32 accumulation would give
     ~1e-7.  The Newton-Schulz step near convergence, (1.5 I - 0.5 A) X with
-    |A - I| <= 1e-10, whose correction product is FP32: within the FP64
-    rounding of a 128-term product (~1e-15; measured 1.7e-15), since the
-    correction is 1e-10 of X."""
+    |A - I| <= 1e-10, as the adaptive polar schedule takes it (the correction
+    0.5 (I - A) X as a 3xTF32 tensor-core product, added to X in FP64): within
+    the FP64 rounding of a 128-term product (~1e-15), since the correction is
+    1e-10 of X."""
     import torch
     from paper_1905_01331_gb300 import _abi
     lib = _abi.load()
