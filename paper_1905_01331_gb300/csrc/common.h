@@ -132,17 +132,19 @@ int dot_self_and_cross(const double* x, const double* y, long long n, long long 
 
 // Polar start: per batch b (P x N rows), with fro2 = |G|^2, gw = <G, W>:
 //   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
-// With xh, xl (one batch only) X is also written as FP32 pairs (xh = fl32(X),
-// xl = fl32(X - xh)) for the double-float products.
+// With xh, xl (one batch only) X is written as FP32 pairs for the double-float
+// products instead (computed in pair arithmetic, ~48 bits; X itself is not
+// written).
 // zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
                 int P, double mu, const double* fro2, const double* gw, cudaStream_t s,
                 float* xh = nullptr, float* xl = nullptr, int* zero = nullptr);
 
 // For one P x P matrix A: (ph, pl) = FP32 pair of a I - c A (a = 0, c = -1:
-// of A itself, as df_split), and with flag: flag |= 1 when max |A - I| > thr.
+// of A itself, as df_split), with flag: flag |= 1 when max |A - I| > thr, and
+// with d32: d32 = fl32(0.5 (I - A)).
 int check_split(const double* A, int P, double a, double c, float* ph, float* pl, double thr,
-                int* flag, cudaStream_t s);
+                int* flag, cudaStream_t s, float* d32 = nullptr);
 
 // Pm[b] = a I - c A[b] (P x P), nb batches.
 int poly_step_matrix(const double* A, double* Pm, int P, int nb, double a, double c,
@@ -153,10 +155,11 @@ int set_identity(double* F, int P, int nb, cudaStream_t s);
 
 // y = alpha * x + beta * y over n elements.
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s);
-// y = alpha * (*sel ? x1 : x0) over n elements (sel on the device); with y32
-// also its FP32 copy (as to_f32).
+// y = alpha * (*sel ? x1 : x0 + corr) over n elements (sel on the device; corr,
+// FP32, may be null); with y32 also its FP32 copy (as to_f32).
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
-                 double alpha, cudaStream_t s, float* y32 = nullptr);
+                 double alpha, cudaStream_t s, float* y32 = nullptr,
+                 const float* corr = nullptr);
 
 // Symmetrise P x P blocks in place: A = (A + A^T) / 2.
 int symmetrize(double* A, int P, int nb, cudaStream_t s);
@@ -209,7 +212,8 @@ struct ComposeArgs {
   int grid_share;   // concurrent streams sharing the GPU: the grid takes 1/grid_share of it
   int max_spin;     // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
   // double-float kernel only (may be null): when *shortcut is 0 the kernel
-  // returns at once (the block is then one Newton-Schulz step, ns_correction)
+  // returns at once (the block is then one Newton-Schulz step, corrected on
+  // the tensor cores)
   const int* shortcut = nullptr;
 };
 bool compose_supported(int P, int nsteps);
@@ -305,13 +309,6 @@ int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, do
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,
              long long n2, double* C, cudaStream_t s, const int* run_if = nullptr,
              float* Ch = nullptr, float* Cl = nullptr);
-// C (P x n2) = (1.5 I - 0.5 A) X for A (P x P, as an FP32 pair: hi at A, lo
-// at A + P*P) within 1e-9 of I elementwise: C = X + 0.5 (I - A) X with the
-// correction product in FP32 on X's FP32 head Xh.  Runs only when *full
-// (device) is 0.
-int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
-                  double* C, const int* full, cudaStream_t s);
-
 // Energy change per spin after a sweep (Sec. IV convergence test): dstat =
 // [previous energy, change per spin, tolerance], istat[2] = converged,
 // istat[3] = sweeps seen (the first is compared with nothing).

@@ -175,7 +175,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
     for (int j = 0; j < TN; ++j) {
       const int m = m0 + ty * TM + i, nn = n0 + tx * TN + j;
       if (m >= M || nn >= N) continue;
-      const double v = (double)sh[i][j] + (double)sl[i][j];
+      // FP32 -> FP64 by integer operations (f64_bits.cuh): the two converting
+      // instructions per element would run on the two FP64 units per SM
+      const double v = f64b::from_f32(sh[i][j]) + f64b::from_f32(sl[i][j]);
       if (splits > 1) {
         part[((long long)blockIdx.z * M + m) * N + nn] = v;
       } else {
@@ -233,100 +235,6 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
 }
 
 int grid_n(long long n) { return (int)std::min<long long>((n + 255) / 256, 2048); }
-
-// One Newton-Schulz step near convergence, C = (1.5 I - 0.5 A) X = X + D X with
-// D = 0.5 (I - A), for A = X X^T within 1e-9 of I elementwise (the adaptive
-// polar schedule's short path).  |D| <= 5e-10 elementwise, so D X needs only
-// FP32 accuracy: D is formed in FP32 from A's pair (Ah, Al), X enters as its
-// FP32 head Xh, the product accumulates in FP32 (one FMA per multiply-add
-// against the pair product's twelve), and the epilogue adds the FP64 X (one
-// FP64 add per element; the FP32 -> FP64 conversion is integer, f64_bits.cuh).
-// BM x BN output tile per CTA, TM x TN per thread, K (= P) in tiles of kDBK,
-// two shared-memory stages with the next tile held in registers (as in
-// gemm_df_kernel).  Runs only when *full is 0.
-template <int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN)) ns_correction_kernel(
-    const float* __restrict__ Ah, const float* __restrict__ Al, const double* __restrict__ X,
-    const float* __restrict__ Xh, int P, long long n2, double* __restrict__ C, const int* full) {
-  pdl_wait();
-  pdl_trigger();
-  if (*full != 0) return;
-  constexpr int TX = BN / TN, NT = (BM / TM) * TX;
-  constexpr int LA = BM * kDBK / NT, LB = BN * kDBK / NT;
-  static_assert(BM * kDBK % NT == 0 && BN * kDBK % NT == 0, "staging split");
-  __shared__ __align__(16) float sD[2][kDBK][BM + 4], sX[2][kDBK][BN + 4];
-  const long long tiles_n = (n2 + BN - 1) / BN;
-  const int m0 = (int)(blockIdx.x / tiles_n) * BM;
-  const long long n0 = (blockIdx.x % tiles_n) * BN;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  float rD[LA], rX[LB];
-  auto load = [&](int k0) {
-#pragma unroll
-    for (int i = 0; i < LA; ++i) {
-      const int e = threadIdx.x + i * NT;
-      const int m = m0 + e / kDBK, k = k0 + e % kDBK;
-      float d = 0.f;
-      if (m < P && k < P) {
-        const long long a = (long long)m * P + k;
-        d = 0.5f * ((m == k ? 1.f : 0.f) - Ah[a]) - 0.5f * Al[a];
-      }
-      rD[i] = d;
-    }
-#pragma unroll
-    for (int i = 0; i < LB; ++i) {
-      const int e = threadIdx.x + i * NT;
-      const int k = k0 + e / BN;
-      const long long n = n0 + e % BN;
-      rX[i] = (k < P && n < n2) ? Xh[(long long)k * n2 + n] : 0.f;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int i = 0; i < LA; ++i) {
-      const int e = threadIdx.x + i * NT;
-      sD[buf][e % kDBK][e / kDBK] = rD[i];
-    }
-#pragma unroll
-    for (int i = 0; i < LB; ++i) {
-      const int e = threadIdx.x + i * NT;
-      sX[buf][e / BN][e % BN] = rX[i];
-    }
-  };
-  float acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  load(0);
-  store(0);
-  __syncthreads();
-  for (int k0 = 0, buf = 0; k0 < P; k0 += kDBK, buf ^= 1) {
-    const bool more = k0 + kDBK < P;
-    if (more) load(k0 + kDBK);
-#pragma unroll
-    for (int kk = 0; kk < kDBK; ++kk) {
-      float a[TM], b[TN];
-      lds_frag<TM>(&sD[buf][kk][ty * TM], a);
-      lds_frag<TN>(&sX[buf][kk][tx * TN], b);
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    if (more) store(buf ^ 1);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int m = m0 + ty * TM + i;
-    if (m >= P) continue;
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const long long n = n0 + tx * TN + j;
-      if (n < n2) C[(long long)m * n2 + n] = X[(long long)m * n2 + n] + f64b::from_f32(acc[i][j]);
-    }
-  }
-}
 
 // Gram tiles of GB x GB (GT x GT per thread), the K range cut so that about
 // `target` CTAs run.
@@ -389,16 +297,5 @@ int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl,
              long long n2, double* C, cudaStream_t s, const int* run_if, float* Ch, float* Cl) {
   return apply_launch<64, 32, 4, 4, 4>(Fh, Fl, Xh, Xl, P, n2, C, s, run_if, Ch, Cl);
 }
-
-int ns_correction(const float* A, const double* X, const float* Xh, int P, long long n2,
-                  double* C, const int* full, cudaStream_t s) {
-  constexpr int BM = 128, BN = 64, TM = 8, TN = 4;
-  const long long tiles = (long long)((P + BM - 1) / BM) * ((n2 + BN - 1) / BN);
-  launch_k(ns_correction_kernel<BM, BN, TM, TN>, (unsigned)tiles, (BM / TM) * (BN / TN), 0, s,
-      A, A + (long long)P * P, X, Xh, P, n2, C, full);
-  return 1;
-}
-
-
 
 }  // namespace ttn

@@ -4,6 +4,7 @@
 
 #include "common.h"
 #include "f64_bits.cuh"
+#include "pair_arith.cuh"
 
 namespace ttn {
 
@@ -107,14 +108,28 @@ __global__ void polar_start_kernel(const double* G, const double* W, double* X, 
   const double* g = G + b * elems;
   const double* w = W + b * elems;
   double* x = X + b * elems;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double v = (g[i] - s * w[i]) * inv;
-    x[i] = v;
-    // the FP32 pair of the double-float products, written here instead of
-    // by a separate split pass (one batch only)
-    if (xh) f64b::split(v, xh[i], xl[i]);
+  if (xh) {
+    // mixed modes (one batch): only the FP32 pair of X, which is all that the
+    // double-float products read, computed in pair arithmetic on the FP32
+    // pipes (three FP64 operations per element would run on the two FP64
+    // units per SM)
+    float sh, sl, ih, il;
+    f64b::split(-s, sh, sl);
+    f64b::split(inv, ih, il);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
+         i += (long long)gridDim.x * blockDim.x) {
+      float gh, gl, wh, wl, th, tl;
+      f64b::split(g[i], gh, gl);
+      f64b::split(w[i], wh, wl);
+      pair_mul(wh, wl, sh, sl, th, tl);
+      pair_add(gh, gl, th, tl, th, tl);
+      pair_mul(th, tl, ih, il, xh[i], xl[i]);
+    }
+    return;
   }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (g[i] - s * w[i]) * inv;
 }
 
 __global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, double c) {
@@ -148,13 +163,16 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
 }
 
 __global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
-                                    long long n, double alpha, float* y32) {
+                                    long long n, double alpha, float* y32, const float* corr) {
   pdl_wait();
   pdl_trigger();
-  const double* x = *sel ? x1 : x0;
+  const bool one = *sel != 0;
+  const double* x = one ? x1 : x0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = alpha * x[i];
+    double xi = x[i];
+    if (!one && corr) xi += f64b::from_f32(corr[i]);
+    const double v = alpha * xi;
     y[i] = v;
     if (y32) y32[i] = f64b::to_f32(v);
   }
@@ -495,7 +513,7 @@ __global__ void sweep_delta_kernel(const double* E, double* dstat, int* istat, d
 // c = -1: of A itself), and, with flag, flag |= 1 when max |A - I| > thr
 // (NaN counts as far).  Grid-stride over the elements, a warp vote per pass.
 __global__ void check_split_kernel(const double* A, int P, double a, double c, float* ph, float* pl,
-                                   double thr, int* flag) {
+                                   double thr, int* flag, float* d32) {
   pdl_wait();
   pdl_trigger();
   const long long PP = (long long)P * P;
@@ -507,6 +525,7 @@ __global__ void check_split_kernel(const double* A, int P, double a, double c, f
     if (flag && !(fabs(x - (i == j ? 1.0 : 0.0)) <= thr)) far = 1;
     const double v = c == -1.0 && a == 0.0 ? x : (i == j ? a : 0.0) - c * x;
     f64b::split(v, ph[e], pl[e]);
+    if (d32) d32[e] = f64b::to_f32(0.5 * ((i == j ? 1.0 : 0.0) - x));
   }
   if (flag && __any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
@@ -585,9 +604,9 @@ int polar_start(const double* G, const double* W, double* X, long long elems, in
 }
 
 int check_split(const double* A, int P, double a, double c, float* ph, float* pl, double thr,
-                int* flag, cudaStream_t s) {
+                int* flag, cudaStream_t s, float* d32) {
   launch_k(check_split_kernel, grid_for((long long)P * P, 256, 64), 256, 0, s, A, P, a, c, ph, pl,
-           thr, flag);
+           thr, flag, d32);
   return 1;
 }
 
@@ -608,8 +627,8 @@ int axpby(const double* x, double* y, long long n, double alpha, double beta, cu
 }
 
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
-                 double alpha, cudaStream_t s, float* y32) {
-  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32);
+                 double alpha, cudaStream_t s, float* y32, const float* corr) {
+  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32, corr);
   return 1;
 }
 
