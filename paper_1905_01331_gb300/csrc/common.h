@@ -133,8 +133,7 @@ int dot_self_and_cross(const double* x, const double* y, long long n, long long 
 // Polar start: per batch b (P x N rows), with fro2 = |G|^2, gw = <G, W>:
 //   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
 // With xh, xl (one batch only) X is written as FP32 pairs for the double-float
-// products instead (computed in pair arithmetic, ~48 bits; X itself is not
-// written).
+// products instead (xh = fl32(X), xl = fl32(X - xh); X itself is not written).
 // zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
                 int P, double mu, const double* fro2, const double* gw, cudaStream_t s,

@@ -4,7 +4,6 @@
 
 #include "common.h"
 #include "f64_bits.cuh"
-#include "pair_arith.cuh"
 
 namespace ttn {
 
@@ -108,28 +107,16 @@ __global__ void polar_start_kernel(const double* G, const double* W, double* X, 
   const double* g = G + b * elems;
   const double* w = W + b * elems;
   double* x = X + b * elems;
-  if (xh) {
-    // mixed modes (one batch): only the FP32 pair of X, which is all that the
-    // double-float products read, computed in pair arithmetic on the FP32
-    // pipes (three FP64 operations per element would run on the two FP64
-    // units per SM)
-    float sh, sl, ih, il;
-    f64b::split(-s, sh, sl);
-    f64b::split(inv, ih, il);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
-         i += (long long)gridDim.x * blockDim.x) {
-      float gh, gl, wh, wl, th, tl;
-      f64b::split(g[i], gh, gl);
-      f64b::split(w[i], wh, wl);
-      pair_mul(wh, wl, sh, sl, th, tl);
-      pair_add(gh, gl, th, tl, th, tl);
-      pair_mul(th, tl, ih, il, xh[i], xl[i]);
-    }
-    return;
-  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < elems;
-       i += (long long)gridDim.x * blockDim.x)
-    x[i] = (g[i] - s * w[i]) * inv;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (g[i] - s * w[i]) * inv;
+    // mixed modes (one batch): only the FP32 pair of X, which is all that the
+    // double-float products read (X itself is not written)
+    if (xh)
+      f64b::split(v, xh[i], xl[i]);
+    else
+      x[i] = v;
+  }
 }
 
 __global__ void poly_step_kernel(const double* A, double* Pm, int P, double a, double c) {
