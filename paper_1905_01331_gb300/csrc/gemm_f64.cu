@@ -147,23 +147,50 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
   }
 }
 
-// C = alpha * sum_s partial[s] + beta * C, summed in split order.
+// C = alpha * sum_s partial[s] + beta * C (FP64) over the K splits.  A CTA
+// owns 32 consecutive outputs; its 8 warps each sum a contiguous eighth of the
+// splits in order (loads in flight together), and warp 0 adds the eight sums
+// in group order (a fixed order of terms).
 __global__ void splitk_reduce_kernel(const GemmDesc d) {
   pdl_wait();
   pdl_trigger();
   if (d.skip && *d.skip) return;
+  __shared__ double gs[8][32];
   const long long MN = (long long)d.M * d.N;
   const long long total = MN * d.B0 * d.B1;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long b = e / MN, r = e % MN;
-    const int m = (int)(r / d.N), n = (int)(r % d.N);
-    // symmetric product: below-diagonal tiles were not computed; read the mirror
-    const long long src = (d.sym && m / d.sym_tile > n / d.sym_tile) ? (long long)n * d.N + m : r;
-    double s = 0.0;
-    for (int sp = 0; sp < d.splits; ++sp) s += d.partial[(sp * d.B0 * d.B1 + b) * MN + src];
-    const int b0 = (int)(b % d.B0), b1 = (int)(b / d.B0);
-    st_out(d, b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n, s);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int s_lo = (int)((long long)d.splits * g / 8);
+  const int s_hi = (int)((long long)d.splits * (g + 1) / 8);
+  for (long long e0 = blockIdx.x * 32LL; e0 < total; e0 += gridDim.x * 32LL) {
+    const long long e = e0 + lane;
+    long long b = 0, r = 0;
+    double acc = 0.0;
+    if (e < total) {
+      b = e / MN;
+      r = e % MN;
+      const int m = (int)(r / d.N), n = (int)(r % d.N);
+      // symmetric product: below-diagonal tiles were not computed; read the mirror
+      const long long src =
+          (d.sym && m / d.sym_tile > n / d.sym_tile) ? (long long)n * d.N + m : r;
+      for (int sp0 = s_lo; sp0 < s_hi; sp0 += 8) {
+        double xs[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          xs[q] = sp0 + q < s_hi ? d.partial[((sp0 + q) * d.B0 * d.B1 + b) * MN + src] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += xs[q];
+      }
+    }
+    gs[g][lane] = acc;
+    __syncthreads();
+    if (g == 0 && e < total) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += gs[q][lane];
+      const int m = (int)(r / d.N), n = (int)(r % d.N);
+      const int b0 = (int)(b % d.B0), b1 = (int)(b / d.B0);
+      st_out(d, b0 * d.sc_b0 + (long long)b1 * d.sc_b1 + m * d.sc_m + n * d.sc_n, t);
+    }
+    __syncthreads();
   }
 }
 
@@ -259,7 +286,7 @@ int gemm_launch(const GemmDesc& d0, cudaStream_t s) {
   else n += launch_tile<16, 16>(d, s);
   if (d.splits > 1) {
     const long long total = (long long)d.M * d.N * d.B0 * d.B1;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    const int blocks = (int)std::min<long long>((total + 31) / 32, 8192);
     launch_k(splitk_reduce_kernel, blocks, 256, 0, s, d);
     ++n;
   }
