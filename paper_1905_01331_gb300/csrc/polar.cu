@@ -445,9 +445,10 @@ __device__ __forceinline__ void sp_dot(const float* xh, const float* xl, int xs_
   pair_add(sh0, sl0, sh1, sl1, vh, vl);
 }
 
-// One CTA; all matrices as FP32 pairs in shared memory: X (P x N), A, F, Pm,
-// T, U (P x P).  Per block: A = X X^T; F = I; per step Pm = alpha I - beta A,
-// F <- Pm F and (not in the last step) A <- Pm (A Pm); then X <- F X.
+// One CTA (up to 256 threads); all matrices as FP32 pairs in shared memory:
+// X (P x N), A, F, Pm, T, U (P x P).  Per block: A = X X^T; F = I; per step
+// Pm = alpha I - beta A, F <- Pm F and (not in the last step) A <- Pm (A Pm);
+// then X <- F X.
 __global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPolarArgs a) {
   extern __shared__ __align__(16) float spm[];
   const int P = a.P, N = a.N, PP = P * P, PN = P * N;
@@ -463,11 +464,11 @@ __global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPola
   float* Ml = Mh + PP;
   float* Th = Ml + PP;   // A Pm, then the new F
   float* Tl = Th + PP;
-  for (int e = threadIdx.x; e < PN; e += kSPThreads) split_d(a.X[e], Xh[e], Xl[e]);
+  for (int e = threadIdx.x; e < PN; e += blockDim.x) split_d(a.X[e], Xh[e], Xl[e]);
   __syncthreads();
   int step = 0;
   for (int b = 0; b < a.nblocks; ++b) {
-    for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+    for (int e = threadIdx.x; e < PP; e += blockDim.x) {
       const int i = e / P, j = e % P;
       sp_dot(Xh, Xl, N, 1, Xh, Xl, 1, N, i, j, N, Ah[e], Al[e]);
       Fh[e] = i == j ? 1.f : 0.f;
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPola
       float ah, al, bh, bl;
       split_d(a.alpha[step], ah, al);
       split_d(-a.beta[step], bh, bl);
-      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+      for (int e = threadIdx.x; e < PP; e += blockDim.x) {
         float h, l;
         pair_mul(Ah[e], Al[e], bh, bl, h, l);
         if (e / P == e % P) pair_add(h, l, ah, al, h, l);
@@ -489,13 +490,13 @@ __global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPola
       __syncthreads();
       // new F into T (Pm F), and, not in the last step, A Pm into ... F's old
       // slot is still read, so A Pm goes to the X-sized scratch Y
-      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+      for (int e = threadIdx.x; e < PP; e += blockDim.x) {
         const int i = e / P, j = e % P;
         sp_dot(Mh, Ml, P, 1, Fh, Fl, P, 1, i, j, P, Th[e], Tl[e]);
         if (step < last) sp_dot(Ah, Al, P, 1, Mh, Ml, P, 1, i, j, P, Yh[e], Yl[e]);
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < PP; e += kSPThreads) {
+      for (int e = threadIdx.x; e < PP; e += blockDim.x) {
         Fh[e] = Th[e];
         Fl[e] = Tl[e];
         if (step < last) {
@@ -505,18 +506,18 @@ __global__ void __launch_bounds__(kSPThreads) small_polar_kernel(const SmallPola
       }
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+    for (int e = threadIdx.x; e < PN; e += blockDim.x) {
       const int i = e / N, j = e % N;
       sp_dot(Fh, Fl, P, 1, Xh, Xl, N, 1, i, j, P, Yh[e], Yl[e]);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+    for (int e = threadIdx.x; e < PN; e += blockDim.x) {
       Xh[e] = Yh[e];
       Xl[e] = Yl[e];
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < PN; e += kSPThreads) {
+  for (int e = threadIdx.x; e < PN; e += blockDim.x) {
     const double w = a.sign * ((double)Xh[e] + (double)Xl[e]);
     a.W[e] = w;
     if (a.W32) a.W32[e] = (float)w;
@@ -535,7 +536,11 @@ bool small_polar_supported(int P, long long N, int nblocks, int nsteps) {
 int small_polar(const SmallPolarArgs& a, cudaStream_t s) {
   if (!small_polar_supported(a.P, a.N, a.nblocks, a.block_end[a.nblocks - 1])) return -1;
   const size_t smem = (4 * (size_t)a.P * a.N + 8 * (size_t)a.P * a.P) * sizeof(float);
-  launch_k(small_polar_kernel, 1, kSPThreads, smem, s, a);
+  // as many threads as the largest matrix has entries, in whole warps (one
+  // warp for the 4 x 4 layer: its barriers are then cheap), at most 256
+  const int elems = std::max(a.P * a.N, a.P * a.P);
+  const int threads = std::min(kSPThreads, (elems + 31) / 32 * 32);
+  launch_k(small_polar_kernel, 1, threads, smem, s, a);
   return 1;
 }
 
