@@ -490,10 +490,9 @@ def run_gpu(args):
         out["energy"] = energy
 
     if rank == 0 and not args.no_baseline and world == 1:
-        # the oracle on this host: 2 warm-up sweeps from the seeded start,
-        # then the median of 3 timed
-        # sweeps, in a fresh process with the BLAS on all cores (and, with
-        # --cpu-1thread, on one)
+        # the oracle on this host: 2 warm-up sweeps from the seeded start, then
+        # the median of 3 timed sweeps, in a fresh process with the BLAS on
+        # all cores (and, with --cpu-1thread, on one)
         ncores = os.cpu_count()
         ts = oracle_timing(chi, ncores)
         if ts:

@@ -125,19 +125,22 @@ constexpr int kDotBlocks = 256;
 int batched_dot(const double* x, const double* y, long long n, long long stride, int nb,
                 double* out, double* scratch, cudaStream_t s);
 
-// out[b] = <x_b, x_b>, out[nb + b] = <x_b, y_b> (batch b at offset b * stride,
-// n elements) in one pass over x, each sum in the order of batched_dot.
-int dot_self_and_cross(const double* x, const double* y, long long n, long long stride, int nb,
-                       double* out, double* scratch, cudaStream_t s);
+// Partial sums of <x_b, x_b> and <x_b, y_b> (batch b at offset b * stride, n
+// elements) in one pass over x: scratch[b * kDotBlocks + i] and
+// scratch[(nb + b) * kDotBlocks + i], i < kDotBlocks, each in the order of
+// batched_dot (polar_start completes the two sums).
+int dot_self_and_cross_partial(const double* x, const double* y, long long n, long long stride,
+                               int nb, double* scratch, cudaStream_t s);
 
-// Polar start: per batch b (P x N rows), with fro2 = |G|^2, gw = <G, W>:
+// Polar start: per batch b (P x N rows), with fro2 = |G|^2 and gw = <G, W>
+// summed from the partial sums `part` of dot_self_and_cross_partial:
 //   s = mu * sqrt(fro2);  X = (G - s W) / sqrt(fro2 - 2 s gw + s^2 P).
+// zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 // With xh, xl (one batch only) X is written as FP32 pairs for the double-float
 // products instead (xh = fl32(X), xl = fl32(X - xh); X itself is not written).
-// zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
-                int P, double mu, const double* fro2, const double* gw, cudaStream_t s,
-                float* xh = nullptr, float* xl = nullptr, int* zero = nullptr);
+                int P, double mu, const double* part, cudaStream_t s, float* xh = nullptr,
+                float* xl = nullptr, int* zero = nullptr);
 
 // For one P x P matrix A: (ph, pl) = FP32 pair of a I - c A (a = 0, c = -1:
 // of A itself, as df_split), with flag: flag |= 1 when max |A - I| > thr, and

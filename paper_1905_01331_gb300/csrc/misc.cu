@@ -94,15 +94,32 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 }
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
-                                   int P, double mu, const double* fro2, const double* gw,
-                                   float* xh, float* xl, int* zero) {
+                                   int P, double mu, const double* part, int nb, float* xh,
+                                   float* xl, int* zero) {
   pdl_wait();
   pdl_trigger();
   if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int b = blockIdx.y;
-  const double f2 = fro2[b];
+  // |G|^2 and <G, W> from the partial sums of dot2_partial_kernel, summed by
+  // warp 0 of every CTA exactly as dot_final_kernel sums them (lane-strided,
+  // then a fixed butterfly): the same two values in every CTA
+  __shared__ double sums[2];
+  if (threadIdx.x < 32) {
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += 32) {
+      a += part[b * kDotBlocks + i];
+      c += part[(nb + b) * kDotBlocks + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (threadIdx.x == 0) { sums[0] = a; sums[1] = c; }
+  }
+  __syncthreads();
+  const double f2 = sums[0];
   const double s = mu * sqrt(f2);
-  const double nrm2 = f2 - 2.0 * s * gw[b] + s * s * P;
+  const double nrm2 = f2 - 2.0 * s * sums[1] + s * s * P;
   const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   const double* g = G + b * elems;
   const double* w = W + b * elems;
@@ -574,19 +591,17 @@ int batched_dot(const double* x, const double* y, long long n, long long stride,
   return 2;
 }
 
-int dot_self_and_cross(const double* x, const double* y, long long n, long long stride, int nb,
-                       double* out, double* scratch, cudaStream_t s) {
+int dot_self_and_cross_partial(const double* x, const double* y, long long n, long long stride,
+                               int nb, double* scratch, cudaStream_t s) {
   launch_k(dot2_partial_kernel, dim3(kDotBlocks, nb), 256, 0, s, x, y, n, stride, nb, scratch);
-  launch_k(dot_final_kernel, (2 * nb + 3) / 4, 128, 0, s, scratch, 2 * nb, out, nullptr);
-  return 2;
+  return 1;
 }
 
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
-                double mu, const double* fro2, const double* gw, cudaStream_t s, float* xh,
-                float* xl, int* zero) {
+                double mu, const double* part, cudaStream_t s, float* xh, float* xl, int* zero) {
   if (nb != 1) xh = xl = nullptr;
   launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P,
-           mu, fro2, gw, xh, xl, zero);
+           mu, part, nb, xh, xl, zero);
   return 1;
 }
 

@@ -972,8 +972,6 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   double* W = I.W[t];
   double* X = h->X;
   double* X2 = h->X2;
-  double* fro2 = h->scal + 8;
-  double* gw = fro2 + NJ;
   // The polar factor is FP64 in every mode (the small singular directions
   // must not drown in tensor-core rounding).  FP64 mode, and layers too small
   // for the double-float products (P < 32, negligible cost): short blocks (at
@@ -1020,11 +1018,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   float* Corr = Fh + 2 * PP;
   const double* X_short = X;
   if (!h->measuring) {
-    // fro2 and gw (= fro2 + NJ) from one pass over Gamma
-    h->launches += dot_self_and_cross(Gam, W, PN, PN, NJ, fro2, h->red, h->stream);
+    // |Gamma|^2 and <Gamma, W> from one pass over Gamma (partial sums, completed
+    // inside the polar start)
+    h->launches += dot_self_and_cross_partial(Gam, W, PN, PN, NJ, h->red, h->stream);
     // (the adaptive schedule's flag starts at 0: the check before the last
     // block ORs 1 into it when that block and the final step must run)
-    h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, fro2, gw, h->stream,
+    h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, h->red, h->stream,
                                df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr,
                                adaptive ? full : nullptr);
   }
