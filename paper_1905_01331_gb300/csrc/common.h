@@ -201,6 +201,8 @@ int top_energy_sum(const double* dot, const double* vv, const double* e, int per
 // err is raised (|= 2) if a grid barrier wait expires.
 // ---------------------------------------------------------------------------
 constexpr int kMaxComposeSteps = 64;
+// row or column blocks of 8 of a composition (P <= 256)
+constexpr int kComposeMaxTiles = 32;
 struct ComposeArgs {
   double* A0;
   double* A1;
@@ -209,7 +211,9 @@ struct ComposeArgs {
   double* S;
   int P, NJ, nsteps;
   double alpha[kMaxComposeSteps], beta[kMaxComposeSteps];
-  unsigned* bar;
+  unsigned* bar;    // FP64 kernel: grid-barrier counter (zeroed by polar_compose)
+  // double-float kernel: 3 * kComposeMaxTiles tile counters (zeroed by polar_compose)
+  unsigned* cnt;
   int* err;
   int grid_share;   // concurrent streams sharing the GPU: the grid takes 1/grid_share of it
   int max_spin;     // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
@@ -272,7 +276,9 @@ struct LanczosArgs {
   int* flags;
   int c, K, m, restarts;
   double tol;
-  unsigned* bar;
+  unsigned* bar;    // FP64 kernel: grid-barrier counter (zeroed by polar_compose)
+  // double-float kernel: 3 * kComposeMaxTiles tile counters (zeroed by polar_compose)
+  unsigned* cnt;
   int* err;
   int max_spin;       // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
   // double-float matrix-vector products (mixed modes): df != 0 and pair

@@ -196,14 +196,59 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_kernel(const ComposeA
 // and the polar factor's final Newton-Schulz step restores the isometry.
 // Without the transposed reads the staging takes half as long.  F ends as
 // pairs, the operand format of the double-float apply.
+//
+// Work items and their order.  One item is one 8 x 8 output tile (b, ti, tj):
+//   phase 1 of step j:  F_{j+1}(ti, tj) = Pm_j(ti, :) F_j(:, tj)   (F_1 = Pm_0 elementwise)
+//                       T(ti, tj)       = A_j(ti, :) Pm_j(:, tj)   (not on the last step)
+//   phase 2 of step j:  A_{j+1}(ti, tj) = Pm_j(ti, :) T(:, tj)
+// The two phase-1 tiles share the staged rows of A_j, so one item computes
+// both.  Instead of a grid barrier between phases, items wait only for the
+// tiles they read, through three arrays of counters (one per row or column
+// block, shared by the NJ matrices):
+//   cT[tj]  phase-1 items of column block tj done,
+//   rA[ti]  phase-2 items of row block ti done,   cA[tj]  ... of column block tj.
+// A phase-1 item of step j >= 1 waits for rA[ti] and cA[tj] to reach nt NJ j
+// (rows ti of A_j: its own rows and those of Pm_j; columns tj of A_j; and,
+// through the phase-1 items those phase-2 items waited for, columns tj of F_j
+// and every earlier reader of the T and F tiles it overwrites); a phase-2 item
+// of step j waits for cT[tj] to reach nt NJ (j + 1) (columns tj of T, and,
+// through those items, rows ti of A_j and every reader of the A_{j-1} tile it
+// overwrites).  Every CTA finishes its items of one phase before the next
+// phase, and items only wait for items of earlier phases, so a co-resident
+// grid always progresses; each wait is bounded (error flag, then return).
 // ---------------------------------------------------------------------------
 
-struct ComposeDFSmem {
-  float Xh[kCT][kCMaxP + 1], Xl[kCT][kCMaxP + 1];
-  float Yh[kCT][kCMaxP + 1], Yl[kCT][kCMaxP + 1];
-  float rh[kCWarps][kCT * kCT], rl[kCWarps][kCT * kCT];
-  int ok;
+constexpr int kDFArrays = 8;   // Rh Rl Ph Pl Uh Ul Vh Vl
+static_assert(kCMaxP / kCT <= kComposeMaxTiles, "one counter per row or column block");
+
+// Row stride of the staged arrays: P + 4 rounded so that the stride is 4 mod
+// 32 banks (the eight rows or columns of a tile then start in distinct banks
+// for the compute reads, and a staging pass of four k by eight columns hits
+// 32 distinct banks).
+__host__ __device__ __forceinline__ int df_ld(int P) { return P + (36 - P % 32) % 32; }
+
+size_t compose_df_smem(int P) {
+  return ((size_t)kDFArrays * kCT * df_ld(P) + 4 * kCWarps * kCT * kCT) * sizeof(float) + 16;
+}
+
+struct DFSmem {
+  float *Rh, *Rl;   // rows i0.. of A_j as stored
+  float *Ph, *Pl;   // the same rows of Pm_j = alpha_j I - beta_j A_j
+  float *Uh, *Ul;   // columns j0.. of the first product's right factor (as stored)
+  float *Vh, *Vl;   // columns j0.. of Pm_j (the second product's right factor)
+  float* red;       // [product][hi, lo][warp][64] partial sums
+  int* ok;
 };
+
+__device__ __forceinline__ DFSmem df_carve(float* base, int ld) {
+  DFSmem s;
+  const int a = kCT * ld;
+  s.Rh = base; s.Rl = base + a; s.Ph = base + 2 * a; s.Pl = base + 3 * a;
+  s.Uh = base + 4 * a; s.Ul = base + 5 * a; s.Vh = base + 6 * a; s.Vl = base + 7 * a;
+  s.red = base + kDFArrays * a;
+  s.ok = reinterpret_cast<int*>(s.red + 4 * kCWarps * kCT * kCT);
+  return s;
+}
 
 // dx I + sx M at element (i, k) for the pair (mh, ml) of M there.
 __device__ __forceinline__ void xform_elem(float& mh, float& ml, int i, int k, float dxh,
@@ -212,35 +257,43 @@ __device__ __forceinline__ void xform_elem(float& mh, float& ml, int i, int k, f
   if (i == k && (dxh != 0.f || dxl != 0.f)) pair_add(mh, ml, dxh, dxl, mh, ml);
 }
 
-// Tile (i0, j0) of X' Y' in pair arithmetic (see tile_product, without the
-// symmetrisation); element (r, c) = (tid / 8, tid % 8) returned in (vh, vl)
-// for tid < 64.  The staging loads of up to four elements per operand are
-// issued before any of them is transformed and stored, so that one pass over
-// the rows and columns costs one load latency.
-__device__ void tile_product_df(ComposeDFSmem& sm, const float* X, float dxh, float dxl,
-                                float sxh, float sxl, const float* Y, float dyh, float dyl,
-                                float syh, float syl, int P, int i0, int j0, float& vh,
-                                float& vl) {
+// One work item on tile (i0, j0) of the P x P pair matrices (A, U, V at their
+// block's base; the coefficient pairs (dh, dl) = alpha_j, (sh, sl) = -beta_j):
+//   stage rows i0.. of A (raw into R when wantR, as Pm into P), columns j0.. of
+//   U (raw) when U, and columns j0.. of V as Pm when V -- the loads of one
+//   pass issued before any of them is transformed and stored;
+//   OU = P-rows x U-columns when U, OV = R-rows x V-columns when V (each K
+//   range cut into 8 interleaved slices, one per warp, added in warp order);
+//   OE (when given) = the tile of Pm itself (F_1 = Pm_0).
+__device__ void df_item(const DFSmem& sm, int P, int ld, const float* A, bool wantR,
+                        const float* U, const float* V, float dh, float dl, float sh, float sl,
+                        int i0, int j0, float* OU, float* OV, float* OE) {
   constexpr int kBatch = 4;
   const long long PP = (long long)P * P;
   const int total = kCT * P;
   for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kCThreads) {
-    float xh[kBatch], xl[kBatch], yh[kBatch], yl[kBatch];
+    float ah[kBatch], al[kBatch], uh[kBatch], ul[kBatch], vh[kBatch], vl[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * kCThreads;
-      xh[u] = xl[u] = yh[u] = yl[u] = 0.f;
+      ah[u] = al[u] = uh[u] = ul[u] = vh[u] = vl[u] = 0.f;
       if (e < total) {
-        // rows of X: element (r, k); columns of Y: element (k, c)
+        // rows: element (r, k); columns: element (k2, c)
         const int r = e / P, k = e - r * P, gi = i0 + r;
         if (gi < P) {
-          xh[u] = __ldcg(X + (long long)gi * P + k);
-          xl[u] = __ldcg(X + PP + (long long)gi * P + k);
+          ah[u] = __ldcg(A + (long long)gi * P + k);
+          al[u] = __ldcg(A + PP + (long long)gi * P + k);
         }
         const int k2 = e / kCT, c = e - k2 * kCT, gj = j0 + c;
         if (gj < P) {
-          yh[u] = __ldcg(Y + (long long)k2 * P + gj);
-          yl[u] = __ldcg(Y + PP + (long long)k2 * P + gj);
+          if (U) {
+            uh[u] = __ldcg(U + (long long)k2 * P + gj);
+            ul[u] = __ldcg(U + PP + (long long)k2 * P + gj);
+          }
+          if (V) {
+            vh[u] = __ldcg(V + (long long)k2 * P + gj);
+            vl[u] = __ldcg(V + PP + (long long)k2 * P + gj);
+          }
         }
       }
     }
@@ -249,81 +302,121 @@ __device__ void tile_product_df(ComposeDFSmem& sm, const float* X, float dxh, fl
       const int e = e0 + u * kCThreads;
       if (e < total) {
         const int r = e / P, k = e - r * P, gi = i0 + r;
-        if (gi < P) xform_elem(xh[u], xl[u], gi, k, dxh, dxl, sxh, sxl);
-        sm.Xh[r][k] = xh[u];
-        sm.Xl[r][k] = xl[u];
+        if (wantR) {
+          sm.Rh[r * ld + k] = ah[u];
+          sm.Rl[r * ld + k] = al[u];
+        }
+        if (gi < P) xform_elem(ah[u], al[u], gi, k, dh, dl, sh, sl);
+        sm.Ph[r * ld + k] = ah[u];
+        sm.Pl[r * ld + k] = al[u];
         const int k2 = e / kCT, c = e - k2 * kCT, gj = j0 + c;
-        if (gj < P) xform_elem(yh[u], yl[u], k2, gj, dyh, dyl, syh, syl);
-        sm.Yh[c][k2] = yh[u];
-        sm.Yl[c][k2] = yl[u];
+        if (U) {
+          sm.Uh[c * ld + k2] = uh[u];
+          sm.Ul[c * ld + k2] = ul[u];
+        }
+        if (V) {
+          if (gj < P) xform_elem(vh[u], vl[u], k2, gj, dh, dl, sh, sl);
+          sm.Vh[c * ld + k2] = vh[u];
+          sm.Vl[c * ld + k2] = vl[u];
+        }
       }
     }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = lane >> 2, j = (lane & 3) * 2;
-  float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+  float u0h = 0.f, u0l = 0.f, u1h = 0.f, u1l = 0.f;
+  float v0h = 0.f, v0l = 0.f, v1h = 0.f, v1l = 0.f;
   int n = 0;
   for (int k = warp; k < P; k += kCWarps) {
-    const float xh = sm.Xh[i][k], xl = sm.Xl[i][k];
-    pair_mac(xh, xl, sm.Yh[j][k], sm.Yl[j][k], a0h, a0l);
-    pair_mac(xh, xl, sm.Yh[j + 1][k], sm.Yl[j + 1][k], a1h, a1l);
+    if (U) {
+      const float xh = sm.Ph[i * ld + k], xl = sm.Pl[i * ld + k];
+      pair_mac(xh, xl, sm.Uh[j * ld + k], sm.Ul[j * ld + k], u0h, u0l);
+      pair_mac(xh, xl, sm.Uh[(j + 1) * ld + k], sm.Ul[(j + 1) * ld + k], u1h, u1l);
+    }
+    if (V) {
+      const float xh = sm.Rh[i * ld + k], xl = sm.Rl[i * ld + k];
+      pair_mac(xh, xl, sm.Vh[j * ld + k], sm.Vl[j * ld + k], v0h, v0l);
+      pair_mac(xh, xl, sm.Vh[(j + 1) * ld + k], sm.Vl[(j + 1) * ld + k], v1h, v1l);
+    }
     if (++n == 8) {
       n = 0;
-      pair_renorm(a0h, a0l);
-      pair_renorm(a1h, a1l);
+      pair_renorm(u0h, u0l);
+      pair_renorm(u1h, u1l);
+      pair_renorm(v0h, v0l);
+      pair_renorm(v1h, v1l);
     }
   }
-  sm.rh[warp][i * kCT + j] = a0h;
-  sm.rl[warp][i * kCT + j] = a0l;
-  sm.rh[warp][i * kCT + j + 1] = a1h;
-  sm.rl[warp][i * kCT + j + 1] = a1l;
+  constexpr int kT2 = kCT * kCT;
+  float* redU = sm.red;                       // [hi, lo][warp][64]
+  float* redV = sm.red + 2 * kCWarps * kT2;
+  const int o = i * kCT + j;
+  redU[warp * kT2 + o] = u0h;
+  redU[(kCWarps + warp) * kT2 + o] = u0l;
+  redU[warp * kT2 + o + 1] = u1h;
+  redU[(kCWarps + warp) * kT2 + o + 1] = u1l;
+  redV[warp * kT2 + o] = v0h;
+  redV[(kCWarps + warp) * kT2 + o] = v0l;
+  redV[warp * kT2 + o + 1] = v1h;
+  redV[(kCWarps + warp) * kT2 + o + 1] = v1l;
   __syncthreads();
-  vh = 0.f;
-  vl = 0.f;
-  if (threadIdx.x < kCT * kCT)
-    for (int w = 0; w < kCWarps; ++w)
-      pair_add(vh, vl, sm.rh[w][threadIdx.x], sm.rl[w][threadIdx.x], vh, vl);
-  __syncthreads();
-}
-
-__device__ __forceinline__ void store_tile_df(float* C, int P, int ti, int tj, float vh, float vl) {
-  if (threadIdx.x >= kCT * kCT) return;
-  const int gi = ti * kCT + threadIdx.x / kCT, gj = tj * kCT + threadIdx.x % kCT;
-  if (gi < P && gj < P) {
-    const long long PP = (long long)P * P;
-    __stcg(C + (long long)gi * P + gj, vh);
-    __stcg(C + PP + (long long)gi * P + gj, vl);
+  // threads 0..63 finish the first product's tile, 64..127 the second's,
+  // 128..191 copy the tile of Pm
+  const int t = threadIdx.x, q = t / kT2, e = t % kT2;
+  const int gi = i0 + e / kCT, gj = j0 + e % kCT;
+  if (q < 2 && gi < P && gj < P) {
+    float* out = q == 0 ? OU : OV;
+    if (out) {
+      const float* red = q == 0 ? redU : redV;
+      float rh = 0.f, rl = 0.f;
+      for (int w = 0; w < kCWarps; ++w)
+        pair_add(rh, rl, red[w * kT2 + e], red[(kCWarps + w) * kT2 + e], rh, rl);
+      __stcg(out + (long long)gi * P + gj, rh);
+      __stcg(out + PP + (long long)gi * P + gj, rl);
+    }
+  } else if (q == 2 && OE && gi < P && gj < P) {
+    __stcg(OE + (long long)gi * P + gj, sm.Ph[(e / kCT) * ld + gj]);
+    __stcg(OE + PP + (long long)gi * P + gj, sm.Pl[(e / kCT) * ld + gj]);
   }
 }
 
-
-__device__ bool grid_barrier_df(ComposeDFSmem& sm, unsigned* bar, unsigned target, int* err,
-                                int max_spin) {
-  __syncthreads();
+// Wait until *c0 >= t0 and (c1 null or) *c1 >= t1: thread 0 polls with
+// acquire loads, at most max_spin times; the CTA then continues.  Returns false
+// (and raises *err) when the wait expires or another CTA has raised *err.
+__device__ bool df_wait(const DFSmem& sm, const unsigned* c0, unsigned t0, const unsigned* c1,
+                        unsigned t1, int* err, int max_spin) {
   if (threadIdx.x == 0) {
-    // arrive with release semantics, poll with acquire semantics
-    int ok = 1;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-    int spins = 0;
+    int ok = 1, spins = 0;
     while (true) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if (v >= target) break;
+      unsigned v0, v1 = t1;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v0) : "l"(c0) : "memory");
+      if (c1) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v1) : "l"(c1) : "memory");
+      if (v0 >= t0 && v1 >= t1) break;
       if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
       if (++spins > max_spin) { atomicOr(err, 2); ok = 0; break; }
       __nanosleep(32);
     }
-    sm.ok = ok;
+    *sm.ok = ok;
   }
   __syncthreads();
-  return sm.ok != 0;
+  return *sm.ok != 0;
+}
+
+// The CTA's tile is stored: count it (release, after every thread's stores).
+__device__ __forceinline__ void df_signal(unsigned* c0, unsigned* c1) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c0) : "memory");
+    if (c1) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c1) : "memory");
+  }
 }
 
 __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const ComposeArgs a) {
-  __shared__ ComposeDFSmem sm;
-  const int P = a.P, ns = a.nsteps;
-  const int nt = (P + kCT - 1) / kCT, ntt = nt * nt;
+  extern __shared__ __align__(16) float df_dyn[];
+  const int P = a.P, ns = a.nsteps, NJ = a.NJ;
+  const int nt = (P + kCT - 1) / kCT, ntt = nt * nt, items = ntt * NJ;
+  const int ld = df_ld(P);
+  const DFSmem sm = df_carve(df_dyn, ld);
   const long long P2 = 2LL * P * P;               // floats per pair matrix
   float* A0 = reinterpret_cast<float*>(a.A0);
   float* A1 = reinterpret_cast<float*>(a.A1);
@@ -332,10 +425,15 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
   float* T = reinterpret_cast<float*>(a.T);
   // the previous block already left X X^T within its threshold of I: the
   // block is one Newton-Schulz step, applied by its FP32 correction instead
-  // (every CTA reads the same flag, so none reaches a grid barrier)
+  // (every CTA reads the same flag, so none waits for another)
   if (a.shortcut && *a.shortcut == 0) return;
+  unsigned* cT = a.cnt;
+  unsigned* rA = a.cnt + kComposeMaxTiles;
+  unsigned* cA = a.cnt + 2 * kComposeMaxTiles;
+  const unsigned per_block = (unsigned)(nt * NJ);   // items per row or column block and phase
+  const int max_spin = a.max_spin > 0 ? a.max_spin : kCMaxSpin;
+  // F_j lives in F when ns - j is even, else in S, so that F_ns ends in F
   auto Fbuf = [&](int j) { return ((ns - j) & 1) ? S : F; };
-  unsigned target = 0;
   for (int j = 0; j < ns; ++j) {
     float alh, all, mbh, mbl;
     split_d(a.alpha[j], alh, all);
@@ -343,49 +441,29 @@ __global__ void __launch_bounds__(kCThreads) polar_compose_df_kernel(const Compo
     const bool last = j + 1 == ns;
     const float* Aj = (j & 1) ? A1 : A0;
     float* An = (j & 1) ? A0 : A1;
+    const float* Fj = Fbuf(j);
     float* Fn = Fbuf(j + 1);
-    const int np = (j > 0 ? 1 : 0) + (last ? 0 : 1);
-    const int items1 = np * ntt * a.NJ;
-    for (int it = blockIdx.x; it < items1; it += gridDim.x) {
-      const int b = it / (np * ntt);
-      const int u = it % (np * ntt);
-      const bool isF = j > 0 && u < ntt;
-      const int ti = (u % ntt) / nt, tj = (u % ntt) % nt;
-      const float* Ab = Aj + b * P2;
-      float vh, vl;
-      if (isF)
-        tile_product_df(sm, Ab, alh, all, mbh, mbl, Fbuf(j) + b * P2, 0.f, 0.f, 1.f, 0.f, P,
-                        ti * kCT, tj * kCT, vh, vl);
-      else
-        tile_product_df(sm, Ab, 0.f, 0.f, 1.f, 0.f, Ab, alh, all, mbh, mbl, P, ti * kCT,
-                        tj * kCT, vh, vl);
-      store_tile_df((isF ? Fn : T) + b * P2, P, ti, tj, vh, vl);
-    }
-    if (j == 0) {
-      // F_1 = Pm_0, elementwise
-      const long long PP = (long long)P * P;
-      for (long long e = blockIdx.x * (long long)kCThreads + threadIdx.x; e < a.NJ * PP;
-           e += (long long)gridDim.x * kCThreads) {
-        const long long b = e / PP, r = e % PP;
-        float h = __ldcg(Aj + b * P2 + r), l = __ldcg(Aj + b * P2 + PP + r);
-        xform_elem(h, l, (int)(r / P), (int)(r % P), alh, all, mbh, mbl);
-        __stcg(Fn + b * P2 + r, h);
-        __stcg(Fn + b * P2 + PP + r, l);
-      }
+    // phase 1: F_{j+1} (F_1 = Pm_0 elementwise) and, before the last step, T
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      const int b = it / ntt, ti = (it % ntt) / nt, tj = it % nt;
+      if (j > 0 && !df_wait(sm, rA + ti, per_block * j, cA + tj, per_block * j, a.err, max_spin))
+        return;
+      df_item(sm, P, ld, Aj + b * P2, !last, j > 0 ? Fj + b * P2 : nullptr,
+              last ? nullptr : Aj + b * P2, alh, all, mbh, mbl, ti * kCT, tj * kCT,
+              j > 0 ? Fn + b * P2 : nullptr, last ? nullptr : T + b * P2,
+              j == 0 ? Fn + b * P2 : nullptr);
+      if (!last) df_signal(cT + tj, nullptr);
+      else __syncthreads();   // the staged rows are read by the stores above
     }
     if (last) break;
-    target += gridDim.x;
-    if (!grid_barrier_df(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
-    const int items2 = ntt * a.NJ;
-    for (int it = blockIdx.x; it < items2; it += gridDim.x) {
-      const int b = it / ntt, ti = (it % ntt) / nt, tj = (it % ntt) % nt;
-      float vh, vl;
-      tile_product_df(sm, Aj + b * P2, alh, all, mbh, mbl, T + b * P2, 0.f, 0.f, 1.f, 0.f, P,
-                      ti * kCT, tj * kCT, vh, vl);
-      store_tile_df(An + b * P2, P, ti, tj, vh, vl);
+    // phase 2: A_{j+1} = Pm_j T
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      const int b = it / ntt, ti = (it % ntt) / nt, tj = it % nt;
+      if (!df_wait(sm, cT + tj, per_block * (j + 1), nullptr, 0, a.err, max_spin)) return;
+      df_item(sm, P, ld, Aj + b * P2, false, T + b * P2, nullptr, alh, all, mbh, mbl, ti * kCT,
+              tj * kCT, An + b * P2, nullptr, nullptr);
+      df_signal(rA + ti, cA + tj);
     }
-    target += gridDim.x;
-    if (!grid_barrier_df(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kCMaxSpin)) return;
   }
 }
 
@@ -406,8 +484,13 @@ int compose_grid_cap(bool df) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, polar_compose_kernel, kCThreads, 0) !=
         cudaSuccess)
       return 0;
+    // the double-float kernel's shared memory is dynamic, sized by P
+    const int df_max = (int)compose_df_smem(kCMaxP);
+    if (cudaFuncSetAttribute(polar_compose_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             df_max) != cudaSuccess)
+      return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_df, polar_compose_df_kernel, kCThreads,
-                                                      0) != cudaSuccess)
+                                                      df_max) != cudaSuccess)
       return 0;
     g.sms = sms;
     g.per_sm = std::min(occ, 2);
@@ -565,12 +648,15 @@ int polar_compose(const ComposeArgs& a, cudaStream_t s, bool df) {
   if (cap <= 0) return -1;
   if (a.grid_share > 1) cap = std::max(1, cap / a.grid_share);
   const int nt = (a.P + kCT - 1) / kCT;
-  const int grid = std::max(1, std::min(cap, 2 * nt * nt * a.NJ));
-  cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
+  // the FP64 kernel's first phase holds two tiles per output tile, the
+  // double-float kernel's one item per output tile
+  const int grid = std::max(1, std::min(cap, (df ? 1 : 2) * nt * nt * a.NJ));
+  if (df) cudaMemsetAsync(a.cnt, 0, 3 * kComposeMaxTiles * sizeof(unsigned), s);
+  else cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kCThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = df ? compose_df_smem(a.P) : 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

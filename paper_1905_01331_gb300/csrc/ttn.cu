@@ -188,6 +188,7 @@ struct ttn_ctx {
   double *lz_opsp = nullptr, *lz_bp = nullptr, *lz_Yp = nullptr;
   int* iflags = nullptr;       // [0]=skip [1]=tdim [2]=conv [3]=nan [4]=wait expired
                                // [5]=grid-barrier counter of the polar composition
+                               // [6], [7]=top-solve flags; [8..]=composition tile counters
   SubStreams sub;              // of the current lane
   int lz_m = 48;
   double* E_hist = nullptr;    // device energies of the current ttn_sweep call
@@ -938,6 +939,7 @@ void compose_block(ttn_ctx* h, const PolarBlock& blk, int P, int NJ, bool df,
     a.beta[j] = blk.steps[j].second;
   }
   a.bar = reinterpret_cast<unsigned*>(h->iflags + 5);
+  a.cnt = reinterpret_cast<unsigned*>(h->iflags + 8);
   a.err = h->iflags + 4;
   a.max_spin = h->opt.wait_polls;
   a.grid_share = h->profiling ? 1 : (int)h->lanes.size();
@@ -1413,7 +1415,7 @@ void layout(ttn_ctx* h, Arena& ar) {
       h->lz_bp = ar.take((h->lz_m + 1) * c2_max);
       h->lz_Yp = ar.take(2 * K_max * c2_max);
     }
-    h->iflags = ar.take_int(8);
+    h->iflags = ar.take_int(8 + 3 * kComposeMaxTiles);
     h->partial = ar.take(h->partial_cap);
     const int ss = h->opt.stage_streams == 0 ? (h->lanes.size() == 1 ? kSubStreams : 1)
                                              : h->opt.stage_streams;
