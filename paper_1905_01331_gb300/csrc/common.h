@@ -276,9 +276,7 @@ struct LanczosArgs {
   int* flags;
   int c, K, m, restarts;
   double tol;
-  unsigned* bar;    // FP64 kernel: grid-barrier counter (zeroed by polar_compose)
-  // double-float kernel: 3 * kComposeMaxTiles tile counters (zeroed by polar_compose)
-  unsigned* cnt;
+  unsigned* bar;      // grid-barrier counter (zeroed by lanczos_launch)
   int* err;
   int max_spin;       // polls of a grid-barrier wait before it expires (<= 0: 2^21, ~1 s)
   // double-float matrix-vector products (mixed modes): df != 0 and pair
@@ -290,6 +288,9 @@ struct LanczosArgs {
   float* s1p;
   float* bp;
   float* Yp;
+  // set by lanczos_launch: the double-float matrix-vector phases stage all
+  // operand tiles of a phase at once (asynchronous copies into shared memory)
+  int wide = 0;
 };
 bool lanczos_supported(int c, int m);
 // CTAs of the launch for top dimension c when grid_share streams share the GPU.

@@ -42,7 +42,7 @@ constexpr int kLMaxC = 256;
 constexpr int kLMaxSpin = 1 << 21;       // ~1 s of polling, then the error flag
 constexpr int kLCheck = 8;               // steps between convergence checks within a cycle
 
-struct LzSmem {
+struct __align__(16) LzSmem {
   double L[kLT][kLMaxC + 1];             // left-operand rows of a tile
   double R[kLT][kLMaxC + 1];             // right-operand rows (or columns) of a tile
   double red[kLWarps][kLT * kLT];
@@ -488,6 +488,96 @@ __device__ void tile_store_p(LzSmem& sm, float a0h, float a0l, float a1h, float 
   __syncthreads();
 }
 
+// Wide staging (double-float mode, c <= kLWideMaxC, c a multiple of 8): every
+// operand tile of a matrix-vector phase is requested at once by 16-byte
+// asynchronous copies (cp.async.cg: L2 only, like the loads above) into
+// kLWideSlots slots of 16 rows of ldw = c + 4 floats (slots 0 and 1 reuse
+// sm.L and sm.R, the others are dynamic shared memory), so that a phase costs
+// one L2 latency instead of one per term.  A row tile holds rows [r0, r0+8)
+// of a pair matrix (hi rows 0-7, lo rows 8-15); a column tile holds columns
+// [c0, c0+8) untransposed (hi: c rows of 8 floats, then lo).  The products
+// below take the same operands in the same order as tile_fma_p, so both
+// stagings give the same bits.
+constexpr int kLWideMaxC = 128;
+constexpr int kLWideSlots = 8;
+
+__host__ __device__ __forceinline__ int lz_wide_ld(int c) { return c + 4; }
+
+size_t lz_wide_dyn_bytes(int c) {
+  return (size_t)(kLWideSlots - 2) * 2 * kLT * lz_wide_ld(c) * sizeof(float);
+}
+
+__device__ __forceinline__ float* wide_slot(LzSmem& sm, float* dyn, int s, int ldw) {
+  if (s == 0) return reinterpret_cast<float*>(&sm.L[0][0]);
+  if (s == 1) return reinterpret_cast<float*>(&sm.R[0][0]);
+  return dyn + (long long)(s - 2) * 2 * kLT * ldw;
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// rows [r0, r0+8) of the pair matrix M (hi at M, lo at M + n) into a row tile
+__device__ void wide_rows(float* dst, const float* M, long long n, int c, int r0, int ldw) {
+  const int q4 = c >> 2, per = kLT * q4;   // 16-byte chunks per half
+  for (int q = threadIdx.x; q < 2 * per; q += kLThreads) {
+    const int half = q >= per ? 1 : 0, qq = q - half * per;
+    const int r = qq / q4, k4 = (qq - r * q4) << 2;
+    cp_async16(dst + (half * kLT + r) * ldw + k4, M + half * n + (long long)(r0 + r) * c + k4);
+  }
+}
+// columns [c0, c0+8) of M into a column tile: dst[half][k][j] = M(half)[k][c0 + j]
+__device__ void wide_cols(float* dst, const float* M, long long n, int c, int c0) {
+  const int per = 2 * c;                   // two 16-byte chunks per row and half
+  for (int q = threadIdx.x; q < 2 * per; q += kLThreads) {
+    const int half = q >= per ? 1 : 0, qq = q - half * per;
+    const int k = qq >> 1, j4 = (qq & 1) << 2;
+    cp_async16(dst + half * kLT * c + k * kLT + j4, M + half * n + (long long)k * c + c0 + j4);
+  }
+}
+
+// acc += sum over this warp's K slice of L(i, k) R(j, k) in pair arithmetic:
+// L a row tile; R a row tile (R(j, k) = row j) or, with rcol, a column tile
+// (R(j, k) = M[k][c0 + j]).  Operand order, renormalisation and the final
+// renormalisation are those of tile_fma_p.
+__device__ __forceinline__ void wide_fma(const float* L, const float* R, bool rcol, int c, int ldw,
+                                         float& a0h, float& a0l, float& a1h, float& a1l) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane >> 2, j = (lane & 3) * 2;
+  const float* Lh = L + i * ldw;
+  const float* Ll = L + (kLT + i) * ldw;
+  int cnt = 0;
+  for (int k = warp; k < c; k += kLWarps) {
+    const float xh = Lh[k], xl = Ll[k];
+    float r0h, r0l, r1h, r1l;
+    if (rcol) {
+      const float* R0 = R + k * kLT + j;
+      r0h = R0[0];
+      r1h = R0[1];
+      r0l = R0[kLT * c];
+      r1l = R0[kLT * c + 1];
+    } else {
+      r0h = R[j * ldw + k];
+      r1h = R[(j + 1) * ldw + k];
+      r0l = R[(kLT + j) * ldw + k];
+      r1l = R[(kLT + j + 1) * ldw + k];
+    }
+    pair_mac(xh, xl, r0h, r0l, a0h, a0l);
+    pair_mac(xh, xl, r1h, r1l, a1h, a1l);
+    if (++cnt == 8) {
+      cnt = 0;
+      pair_renorm(a0h, a0l);
+      pair_renorm(a1h, a1l);
+    }
+  }
+  pair_renorm(a0h, a0l);
+  pair_renorm(a1h, a1l);
+}
+
 // FP64 value and its pair at index e of a vector (pair vector: hi at P, lo at P + n)
 __device__ __forceinline__ void store_both(double* D, float* P, long long n, long long e, double v) {
   __stcg(D + e, v);
@@ -607,6 +697,7 @@ __device__ void owned_combine(const LanczosArgs& a, const LzSmem& sm, int cnt, c
 
 __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs a) {
   __shared__ LzSmem sm;
+  extern __shared__ __align__(16) float lz_dyn[];
   const int c = a.c, K = a.K, m = a.m;
   const long long n = (long long)c * c;
   const int G = gridDim.x, bid = blockIdx.x;
@@ -620,6 +711,8 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
   unsigned target = 0;
 
   const bool df = a.df != 0;
+  const bool wide = df && a.wide != 0;
+  const int ldw = lz_wide_ld(c);
   float* bp0 = df ? a.bp : nullptr;          // pairs of basis_0
   // start: the operators as pairs (double-float mode), Vprev = V, basis_0 = V / |V|
   if (df) {
@@ -681,7 +774,28 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
       const double beta_j1 = j > 0 ? beta_prev : 0.0;
       // phase A: Y_b = Op_b x for the 2K operators A_k0, B_k0 (stored after o_0)
       const float* xp = df ? a.bp + 2 * (long long)j * n : nullptr;
-      for (int it = bid; it < 2 * K * ntiles; it += G) {
+      // wide staging: all 2K products of a tile by its CTA, the columns of x
+      // staged once, the operator rows two at a time
+      for (int t = bid; t < ntiles && wide; t += G) {
+        const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
+        for (int b0 = 0; b0 < 2 * K; b0 += 2) {
+          const int nb = min(2, 2 * K - b0);
+          if (b0 == 0) wide_cols(wide_slot(sm, lz_dyn, 0, ldw), xp, n, c, j0);
+          for (int u = 0; u < nb; ++u)
+            wide_rows(wide_slot(sm, lz_dyn, 1 + u, ldw), s0p + 2 * (long long)(1 + b0 + u) * n, n,
+                      c, i0, ldw);
+          cp_async_wait_all();
+          __syncthreads();
+          for (int u = 0; u < nb; ++u) {
+            float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+            wide_fma(wide_slot(sm, lz_dyn, 1 + u, ldw), wide_slot(sm, lz_dyn, 0, ldw), true, c, ldw,
+                     a0h, a0l, a1h, a1l);
+            tile_store_p(sm, a0h, a0l, a1h, a1l, a.Yp + 2 * (long long)(b0 + u) * n, nullptr, n, c,
+                         i0, j0);
+          }
+        }
+      }
+      for (int it = bid; it < 2 * K * ntiles && !wide; it += G) {
         const int b = it / ntiles, t = it % ntiles;
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
         if (df) {
@@ -703,7 +817,41 @@ __global__ void __launch_bounds__(kLThreads, 2) lanczos_kernel(const LanczosArgs
       if (!lz_barrier(sm, a.bar, target, a.err, a.max_spin > 0 ? a.max_spin : kLMaxSpin)) return;
       // phase B: w = o_0 x + x o_1^T + sum_k Y_k B_k1^T + Y_{K+k} A_k1^T on the
       // owned tiles, then their projections on basis_0..j and |w|^2
-      for (int t = bid; t < ntiles && df; t += G) {
+      // wide staging: the operand tiles of up to four terms in one round
+      for (int t = bid; t < ntiles && wide; t += G) {
+        const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
+        float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+        const int nterms = 2 + 2 * K;
+        for (int t0 = 0; t0 < nterms; t0 += kLWideSlots / 2) {
+          const int tn = min(kLWideSlots / 2, nterms - t0);
+          for (int u = 0; u < tn; ++u) {
+            const int term = t0 + u;
+            float* Ls = wide_slot(sm, lz_dyn, 2 * u, ldw);
+            float* Rs = wide_slot(sm, lz_dyn, 2 * u + 1, ldw);
+            if (term == 0) {
+              wide_rows(Ls, s0p, n, c, i0, ldw);
+              wide_cols(Rs, xp, n, c, j0);
+            } else if (term == 1) {
+              wide_rows(Ls, xp, n, c, i0, ldw);
+              wide_rows(Rs, s1p, n, c, j0, ldw);
+            } else {
+              const int q = term - 2;          // Y_q with q < K: B_{q,1}; else A_{q-K,1}
+              const long long rop = q < K ? (long long)(1 + K + q) : (long long)(1 + q - K);
+              wide_rows(Ls, a.Yp + 2 * (long long)q * n, n, c, i0, ldw);
+              wide_rows(Rs, s1p + 2 * rop * n, n, c, j0, ldw);
+            }
+          }
+          cp_async_wait_all();
+          __syncthreads();
+          for (int u = 0; u < tn; ++u)
+            wide_fma(wide_slot(sm, lz_dyn, 2 * u, ldw), wide_slot(sm, lz_dyn, 2 * u + 1, ldw),
+                     t0 + u == 0, c, ldw, a0h, a0l, a1h, a1l);
+          __syncthreads();
+        }
+        tile_store_p(sm, a0h, a0l, a1h, a1l, nullptr, a.w, n, c, i0, j0, x, sigma_j, xprev,
+                     beta_j1);
+      }
+      for (int t = bid; t < ntiles && df && !wide; t += G) {
         const int i0 = (t / nt) * kLT, j0 = (t % nt) * kLT;
         float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
         for (int term = 0; term < 2 + 2 * K; ++term) {
@@ -901,7 +1049,12 @@ int lanczos_grid_cap() {
   if (!g.sms) {
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_kernel, kLThreads, 0) !=
+    // (with the wide staging's dynamic shared memory at its largest)
+    const int dyn = (int)lz_wide_dyn_bytes(kLWideMaxC);
+    if (cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+        cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lanczos_kernel, kLThreads, dyn) !=
         cudaSuccess)
       return 0;
     g.sms = sms;
@@ -923,13 +1076,17 @@ int lanczos_grid(int c, int grid_share) {
   return (int)std::max<long long>(1, std::min<long long>(std::min(cap, kLMaxGrid), n / 64));
 }
 
-int lanczos_launch(const LanczosArgs& a, int grid, cudaStream_t s) {
-  if (!lanczos_supported(a.c, a.m) || grid < 1 || grid > kLMaxGrid) return -1;
+int lanczos_launch(const LanczosArgs& a0, int grid, cudaStream_t s) {
+  if (!lanczos_supported(a0.c, a0.m) || grid < 1 || grid > kLMaxGrid) return -1;
+  // the grid cap also sets the kernel's dynamic shared-memory limit
+  if (lanczos_grid_cap() <= 0) return -1;
+  LanczosArgs a = a0;
+  a.wide = a.df != 0 && a.c <= kLWideMaxC && a.c % 8 == 0 ? 1 : 0;
   cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kLThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.wide ? lz_wide_dyn_bytes(a.c) : 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
