@@ -309,10 +309,23 @@ int df_split(const double* x, float* hi, float* lo, long long n, cudaStream_t s)
 int df_gram_splits(int P, int n2);
 // Multiply-adds x 2 of the tiles df_gram computes (upper triangle only).
 double df_gram_flops(int P, long long n2);
+// The check_split pass over a Gram matrix, folded into the product's split-K
+// reduction: (ph, pl) = pair of a I - c C, flag |= 1 when max |C - I| > thr
+// (flag may be null), d32 = fl32(0.5 (I - C)) (may be null).
+struct GramCheck {
+  double a = 0.0, c = -1.0;
+  float* ph = nullptr;
+  float* pl = nullptr;
+  double thr = 0.0;
+  int* flag = nullptr;
+  float* d32 = nullptr;
+};
 // C (P x P, FP64) = X X^T for X (P x n2, row-major) given as (Xh, Xl).
 // run_if (device, may be null): when it points to 0 the launches return at once.
+// chk (may be null): also the check_split pass over C, with the same results
+// (one launch fewer when the product is split over K).
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-            cudaStream_t s, const int* run_if = nullptr);
+            cudaStream_t s, const int* run_if = nullptr, const GramCheck* chk = nullptr);
 // C (P x n2, FP64) = F X for F (P x P) given as (Fh, Fl) and X as (Xh, Xl);
 // with Ch, Cl also the normalised FP32 pair of C (the same as splitting C).
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,

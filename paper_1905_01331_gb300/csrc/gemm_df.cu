@@ -199,7 +199,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), MB) gemm_df_kernel(
 // in order (loads in flight together), warp 0 adds the eight sums in group
 // order (a fixed order of terms).
 __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, int tile, int sym,
-                                 double* C, long long ldc, const int* run_if) {
+                                 double* C, long long ldc, const int* run_if, GramCheck chk) {
   pdl_wait();
   pdl_trigger();
   if (run_if && *run_if == 0) return;
@@ -225,11 +225,21 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
     }
     gs[g][lane] = acc;
     __syncthreads();
+    int far = 0;
     if (g == 0 && e < MN) {
       double t = 0.0;
       for (int q = 0; q < 8; ++q) t += gs[q][lane];
       C[m * ldc + n] = t;
+      if (chk.ph) {
+        // the check_split pass (square C, element e = m N + n)
+        const double id = m == n ? 1.0 : 0.0;
+        if (chk.flag && !(fabs(t - id) <= chk.thr)) far = 1;
+        const double v = chk.c == -1.0 && chk.a == 0.0 ? t : (m == n ? chk.a : 0.0) - chk.c * t;
+        f64b::split(v, chk.ph[e], chk.pl[e]);
+        if (chk.d32) chk.d32[e] = f64b::to_f32(0.5 * (id - t));
+      }
     }
+    if (g == 0 && chk.flag && __any_sync(0xffffffffu, far) && lane == 0) atomicOr(chk.flag, 1);
     __syncthreads();
   }
 }
@@ -247,7 +257,7 @@ int gram_splits(int P, int n2, int GB, int target) {
 
 template <int GB, int GT, int MB>
 int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-                int splits, cudaStream_t s, const int* run_if) {
+                int splits, cudaStream_t s, const int* run_if, const GramCheck* chk) {
   const int nt = (P + GB - 1) / GB;
   dim3 grid(nt * (nt + 1) / 2, 1, splits);
   launch_k(gemm_df_kernel<GB, GB, GT, GT, true, MB>, grid, (GB / GT) * (GB / GT), 0, s,
@@ -255,8 +265,11 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
   int launches = 1;
   if (splits > 1) {
     launch_k(df_reduce_kernel, (int)std::min<long long>(((long long)P * P + 31) / 32, 8192), 256,
-             0, s, part, splits, P, P, GB, 1, C, P, run_if);
+             0, s, part, splits, P, P, GB, 1, C, P, run_if, chk ? *chk : GramCheck());
     ++launches;
+  } else if (chk) {
+    launches += check_split(C, P, chk->a, chk->c, chk->ph, chk->pl, chk->thr, chk->flag, s,
+                            chk->d32);
   }
   return launches;
 }
@@ -288,9 +301,9 @@ double df_gram_flops(int P, long long n2) {
 }
 
 int df_gram(const float* Xh, const float* Xl, int P, long long n2, double* C, double* part,
-            cudaStream_t s, const int* run_if) {
+            cudaStream_t s, const int* run_if, const GramCheck* chk) {
   return gram_launch<kGramB, kGramT, 2>(Xh, Xl, P, n2, C, part, df_gram_splits(P, (int)n2), s,
-                                        run_if);
+                                        run_if, chk);
 }
 
 int df_apply(const float* Fh, const float* Fl, const float* Xh, const float* Xl, int P,

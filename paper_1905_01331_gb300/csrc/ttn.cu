@@ -1059,9 +1059,25 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   for (size_t bi = 0; bi < sched.size(); ++bi) {
     const PolarBlock& blk = sched[bi];
     const bool df = df_ok && !h->measuring;
+    const bool kernel = (h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size());
     if (df) {
+      // with the composition kernel, the Gram product's reduction also writes
+      // A_0 as pairs for it; before the adaptive schedule's last block also
+      // the test max |X X^T - I| > kPolarNear (far: 1 into the flag, the
+      // block and the final step run in full) and D = 0.5 (I - X X^T) in FP32
+      // for the short path's correction
+      GramCheck chk;
+      chk.ph = reinterpret_cast<float*>(h->pP);
+      chk.pl = chk.ph + PP;
+      chk.thr = kPolarNear;
+      if (adaptive && bi + 1 == sched.size()) {
+        chk.flag = full;
+        chk.d32 = Dc;
+      }
       df_begin(h);
-      df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream), df_gram_flops(P, N));
+      df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, nullptr,
+                        kernel ? &chk : nullptr),
+             df_gram_flops(P, N));
     } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
@@ -1069,17 +1085,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     g.sym = 1;
     run(h, g, 0);
     }
-    const bool kernel = (h->opt.persistent & 1) && compose_supported(P, (int)blk.steps.size());
     if (kernel) {
-      // A_0 as pairs for the composition; before the adaptive schedule's last
-      // block also the test max |X X^T - I| > kPolarNear (far: 1 into the
-      // flag, the block and the final step run in full)
-      // (and D = 0.5 (I - X X^T) in FP32 for the short path's correction)
-      if (df)
-        h->launches += check_split(h->pA, P, 0.0, -1.0, reinterpret_cast<float*>(h->pP),
-                                   reinterpret_cast<float*>(h->pP) + PP, kPolarNear,
-                                   adaptive && bi + 1 == sched.size() ? full : nullptr, h->stream,
-                                   adaptive && bi + 1 == sched.size() ? Dc : nullptr);
       if (!h->measuring)
         compose_block(h, blk, P, NJ, df, adaptive && bi + 1 == sched.size() ? full : nullptr);
     } else {
@@ -1146,14 +1152,21 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   if (df_ok && !h->measuring) {
     // (cut short: these products return at once; the defect flag below then
     // reads the last block's Gram matrix, within kPolarNear of I)
+    // F = 1.5 I - 0.5 X X^T as pairs, from the Gram product's reduction; the
+    // final step converges quadratically only from |X X^T - I| << 1, so the
+    // same pass flags the instance when the blocks left it above 1e-5 (the
+    // isometry would then miss 1e-10).  Cut short, the pass is skipped with
+    // the product: the last block's Gram matrix is then within kPolarNear of I.
+    GramCheck fin;
+    fin.a = 1.5;
+    fin.c = 0.5;
+    fin.ph = Fh;
+    fin.pl = Fl;
+    fin.thr = 1e-5;
+    fin.flag = I.istat + 4;
     df_begin(h);
-    df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full), df_gram_flops(P, N),
-           full);
-    // F = 1.5 I - 0.5 X X^T as pairs; the final step converges quadratically
-    // only from |X X^T - I| << 1, so the same pass over the Gram matrix flags
-    // the instance when the blocks left it above 1e-5 (the isometry would then
-    // miss 1e-10)
-    h->launches += check_split(h->pA, P, 1.5, 0.5, Fh, Fl, 1e-5, I.istat + 4, h->stream);
+    df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full, &fin),
+           df_gram_flops(P, N), full);
     df_begin(h);
     df_end(h, df_apply(Fh, Fl, Xp, Xp + PN, P, N, X2, h->stream, full), 2.0 * P * P * (double)N,
            full);
