@@ -295,8 +295,7 @@ def run_gpu(args):
     s.sweep(args.warmup)
     stream = s.stream
     torch.cuda.synchronize()
-    # the state the timed sweeps start from, kept in pinned host memory for the
-    # end-to-end leg below
+    # pinned host buffers of the state for the end-to-end leg below
     import ctypes
     dp = ctypes.POINTER(ctypes.c_double)
     n_w = sum(int(np.prod(w.shape)) for w in ws)
@@ -304,8 +303,6 @@ def run_gpu(args):
     v_host = torch.empty(V.size, dtype=torch.float64).pin_memory()
     fp = ctypes.cast(flat_host.data_ptr(), dp)
     vp = ctypes.cast(v_host.data_ptr(), dp)
-    if s.lib.ttn_get_isometries(s.h, 0, fp, vp):
-        raise RuntimeError("reading the state back failed")
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -327,9 +324,15 @@ def run_gpu(args):
     prof = s.profile_sweep()
 
     # e2e through the C ABI with host buffers: upload the state, one sweep,
-    # read the energy back, every step.  The state uploaded is the one the
-    # timed sweeps started from (after the warm-up), so every e2e step is the
-    # first, and most expensive, sweep of the timed region plus the copies.
+    # read the energy back, every step.  The state uploaded is the one reached
+    # after the timed sweeps (and the profiling sweep), so every e2e step does
+    # the work of a steady-state sweep of the timed region plus the copies.
+    # (Repeating the first sweep after the warm-up instead would time the top
+    # solve of a transient state, which takes two or three restart cycles
+    # depending on the last bits of that state: the figure then moves by
+    # +-6 % with no change in the steady-state rate.)
+    if s.lib.ttn_get_isometries(s.h, 0, fp, vp):
+        raise RuntimeError("reading the state back failed")
     E_host = np.zeros(1)
     ep = E_host.ctypes.data_as(dp)
     e2e_steps = max(3, min(args.steps, 20))

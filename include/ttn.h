@@ -114,8 +114,17 @@ typedef struct {
                                final step is skipped (decided on the device),
                                else block 2 covers the worst case down to
                                min(mu / 4, 1e-10) and the final step runs;
+                               before it, a layer predicted well conditioned
+                               (on the device: its last try succeeded, or 16
+                               sweeps passed since it failed) first tries a
+                               short block for singular values above 1e-2;
+                               when that leaves max |X X^T - I| <= 1e-9, one
+                               Newton-Schulz step ends the factor and the
+                               schedule above does not run, else it runs from
+                               the same start;
                                3 = as 0 with the fixed double-float schedule
-                               (two long blocks and the final step always) */
+                               (two long blocks and the final step always);
+                               4 = as 0 without the first try */
   int double_float;         /* mixed modes, 1 (default): the polar factor's products
                                (Gram matrices, composition, apply, plus one final
                                Newton-Schulz step: isometry to ~1e-14) and the
@@ -227,7 +236,10 @@ int ttn_sweep_until(ttn_t h, double tol, int max_sweeps, int* n_done, double* ho
  * of the last sweep (mixed modes) was left more than 1e-5 from an isometry by
  * its Newton-Schulz blocks, else 0; with n_out >= 9, out[8] = the number of
  * isometry layers whose polar factor took the adaptive schedule's short path
- * in the last sweep (ttn_options.polar_blocks).  n_out >= 7.  Overwrites the context's
+ * in the last sweep (ttn_options.polar_blocks); with n_out >= 10, out[9] = the
+ * number of those layers whose short first block (polar_blocks 0: singular
+ * values above 1e-2 of |X|_F) already left an isometry, so that the full
+ * schedule did not run.  n_out >= 7.  Overwrites the context's
  * density matrices (a sweep recomputes them). */
 int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out);
 

@@ -210,10 +210,11 @@ class Sweeper:
     def diagnostics(self, inst=0):
         """Isometry defect, density-matrix traces and symmetry, norm of v,
         last energy change per spin, top-solve convergence (FP64, device)."""
-        out = np.zeros(9)
-        self._check(self.lib.ttn_diagnostics(self.h, inst, _ptr(out), 9), "diagnostics")
+        out = np.zeros(10)
+        self._check(self.lib.ttn_diagnostics(self.h, inst, _ptr(out), 10), "diagnostics")
         keys = ["isometry_defect", "trace_error", "asymmetry", "norm_error", "delta_e",
-                "top_converged", "krylov_dim", "polar_unconverged", "polar_short_layers"]
+                "top_converged", "krylov_dim", "polar_unconverged", "polar_short_layers",
+                "polar_first_try_layers"]
         return dict(zip(keys, out.tolist()))
 
     def energy(self, inst=0):

@@ -138,9 +138,11 @@ int dot_self_and_cross_partial(const double* x, const double* y, long long n, lo
 // zero (may be null): set to 0 by the launch (a flag that later kernels OR into).
 // With xh, xl (one batch only) X is written as FP32 pairs for the double-float
 // products instead (xh = fl32(X), xl = fl32(X - xh); X itself is not written).
+// With try_first (device, may be null): *run_full = (*try_first == 0).
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
                 int P, double mu, const double* part, cudaStream_t s, float* xh = nullptr,
-                float* xl = nullptr, int* zero = nullptr);
+                float* xl = nullptr, int* zero = nullptr, const int* try_first = nullptr,
+                int* run_full = nullptr);
 
 // For one P x P matrix A: (ph, pl) = FP32 pair of a I - c A (a = 0, c = -1:
 // of A itself, as df_split), with flag: flag |= 1 when max |A - I| > thr, and
@@ -158,10 +160,15 @@ int set_identity(double* F, int P, int nb, cudaStream_t s);
 // y = alpha * x + beta * y over n elements.
 int axpby(const double* x, double* y, long long n, double alpha, double beta, cudaStream_t s);
 // y = alpha * (*sel ? x1 : x0 + corr) over n elements (sel on the device; corr,
-// FP32, may be null); with y32 also its FP32 copy (as to_f32).
+// FP32, may be null); with y32 also its FP32 copy (as to_f32).  With pred
+// (device: try_first = pred[0], run_full = pred[pstride], count =
+// pred[2 pstride]) also the next prediction of the polar schedule: try_first
+// becomes 0 when this sweep's first try failed (run_full set), and 1 again
+// after `retry` sweeps.
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
                  double alpha, cudaStream_t s, float* y32 = nullptr,
-                 const float* corr = nullptr);
+                 const float* corr = nullptr, int* pred = nullptr, int pstride = 0,
+                 int retry = 0);
 
 // Symmetrise P x P blocks in place: A = (A + A^T) / 2.
 int symmetrize(double* A, int P, int nb, cudaStream_t s);

@@ -95,10 +95,14 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
                                    int P, double mu, const double* part, int nb, float* xh,
-                                   float* xl, int* zero) {
+                                   float* xl, int* zero, const int* try_first, int* run_full) {
   pdl_wait();
   pdl_trigger();
-  if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (zero) *zero = 0;
+    // the full schedule runs unless the layer is predicted well conditioned
+    if (run_full) *run_full = *try_first ? 0 : 1;
+  }
   const int b = blockIdx.y;
   // |G|^2 and <G, W> from the partial sums of dot2_partial_kernel, summed by
   // warp 0 of every CTA exactly as dot_final_kernel sums them (lane-strided,
@@ -167,9 +171,22 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
 }
 
 __global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
-                                    long long n, double alpha, float* y32, const float* corr) {
+                                    long long n, double alpha, float* y32, const float* corr,
+                                    int* pred, int pstride, int retry) {
   pdl_wait();
   pdl_trigger();
+  if (pred && blockIdx.x == 0 && threadIdx.x == 0) {
+    // next sweep's prediction: a failed first try switches the layer to the
+    // full schedule, which tries the first block again after `retry` sweeps
+    int& try_first = pred[0];
+    int& count = pred[2 * pstride];
+    if (try_first) {
+      if (pred[pstride]) { try_first = 0; count = 0; }
+    } else if (++count >= retry) {
+      try_first = 1;
+      count = 0;
+    }
+  }
   const bool one = *sel != 0;
   const double* x = one ? x1 : x0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -598,10 +615,12 @@ int dot_self_and_cross_partial(const double* x, const double* y, long long n, lo
 }
 
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
-                double mu, const double* part, cudaStream_t s, float* xh, float* xl, int* zero) {
+                double mu, const double* part, cudaStream_t s, float* xh, float* xl, int* zero,
+                const int* try_first, int* run_full) {
   if (nb != 1) xh = xl = nullptr;
+  if (!try_first) run_full = nullptr;
   launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P,
-           mu, part, nb, xh, xl, zero);
+           mu, part, nb, xh, xl, zero, try_first, run_full);
   return 1;
 }
 
@@ -629,8 +648,10 @@ int axpby(const double* x, double* y, long long n, double alpha, double beta, cu
 }
 
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
-                 double alpha, cudaStream_t s, float* y32, const float* corr) {
-  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32, corr);
+                 double alpha, cudaStream_t s, float* y32, const float* corr, int* pred,
+                 int pstride, int retry) {
+  launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32, corr, pred,
+           pstride, retry);
   return 1;
 }
 

@@ -85,6 +85,10 @@ struct Instance {
   // per isometry layer (mixed modes, adaptive polar schedule): 1 = the second
   // block ran in full and the final step ran, 0 = both were cut short
   int* pfull = nullptr;
+  // prediction of the adaptive polar schedule, per isometry layer t (stride
+  // max(T, 1)): [t] try the well-conditioned first block, [T + t] the full
+  // schedule runs in this sweep, [2T + t] sweeps since a failed first try
+  int* ppred = nullptr;
   // Identity part of the one-site operators, kept exactly in FP64: the true
   // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
   std::vector<double*> eoff;
@@ -197,6 +201,9 @@ struct ttn_ctx {
   // above kPolarTry, then either one Newton-Schulz step (when the first block
   // left an isometry) or a block for the worst case; empty if not applicable
   std::vector<PolarBlock> polar_adapt;
+  // adaptive schedule, layers predicted well conditioned: a first block that
+  // converges every singular value above kPolarFirst (empty if not applicable)
+  std::vector<PolarBlock> polar_first;
   bool measuring = false;      // plan pass: only size the partial buffer
   // plan pass over a fake base address: every operand's address range is
   // checked against the buffer it points into (no launch happens)
@@ -511,6 +518,14 @@ struct StageFork {
 // final step no longer removed.
 constexpr double kPolarTry = 1e-5;
 constexpr double kPolarNear = 1e-9;
+// Layers predicted well conditioned first try a block that converges every
+// singular value above kPolarFirst (10 steps instead of 17; growth <= 740,
+// so its rounding stays far below kPolarNear).  If it leaves X X^T within
+// kPolarNear of I, one Newton-Schulz step ends the factor as above;
+// otherwise the adaptive schedule runs in full from the same start, and the
+// layer skips the first try for kPolarRetry sweeps.
+constexpr double kPolarFirst = 1e-2;
+constexpr int kPolarRetry = 16;
 
 std::vector<PolarBlock> polar_schedule(double l0, double gmax, double final_tol, int max_block) {
   std::vector<PolarBlock> out;
@@ -982,7 +997,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // Newton-Schulz step (adaptive: the second composition and the final step
   // become one Newton-Schulz step when the first block already converged).
   const int pb = h->opt.polar_blocks;
-  const bool short_blocks = pb == 1 || ((pb == 0 || pb == 3) && (prec == 0 || P < 32));
+  const bool short_blocks = pb == 1 || ((pb == 0 || pb == 3 || pb == 4) && (prec == 0 || P < 32));
   const std::vector<PolarBlock>* schedp = short_blocks ? &h->polar_f64 : &h->polar_tc;
   // Mixed modes: every block's Gram and apply products in double-float
   // arithmetic on the FP32 pipes (~48 bits: the rounding amplified by a
@@ -991,16 +1006,24 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   // that takes the isometry defect from ~1e-11 to ~1e-14.  Operands in FP32
   // pairs, in the one-leg scratch Y and Yt (both free during the polar step).
   const bool df_ok = prec != 0 && h->opt.double_float && NJ == 1 && P >= 32 && schedp->size() > 1;
-  // Adaptive schedule (polar_blocks 0 in the mixed modes, double-float
+  // Adaptive schedule (polar_blocks 0 and 4 in the mixed modes, double-float
   // composition kernel): block 2 and the final step are cut short on the
   // device when block 1 already left an isometry (flag pfull[t] = 0).
-  const bool adaptive =
-      df_ok && !short_blocks && pb == 0 && h->polar_adapt.size() == 2 && (h->opt.persistent & 1) &&
-      compose_supported(P, (int)h->polar_adapt[0].steps.size()) &&
-      compose_supported(P, (int)h->polar_adapt[1].steps.size());
+  const bool adaptive = df_ok && !short_blocks && (pb == 0 || pb == 4) &&
+                        h->polar_adapt.size() == 2 && (h->opt.persistent & 1) &&
+                        compose_supported(P, (int)h->polar_adapt[0].steps.size()) &&
+                        compose_supported(P, (int)h->polar_adapt[1].steps.size());
   if (adaptive) schedp = &h->polar_adapt;
   const std::vector<PolarBlock>& sched = *schedp;
   int* full = I.pfull + t;
+  // polar_blocks 0: a layer predicted well conditioned first tries the short
+  // first block (kPolarFirst); the full adaptive schedule then runs only when
+  // that try did not leave an isometry (run_full, set on the device)
+  const bool try_first = adaptive && pb == 0 && !h->polar_first.empty() &&
+                         compose_supported(P, (int)h->polar_first[0].steps.size());
+  const int nT = std::max(I.T, 1);
+  int* try_flag = I.ppred + t;
+  int* run_full = try_first ? I.ppred + nT + t : nullptr;
   if (df_ok && !h->measuring && !adaptive)
     h->launches += store_ints(full, nullptr, 1, 1, h->stream);
   // X as FP32 pairs for the double-float products (hi at Xp, lo at Xp + PN),
@@ -1027,7 +1050,8 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     // block ORs 1 into it when that block and the final step must run)
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, h->red, h->stream,
                                df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr,
-                               adaptive ? full : nullptr);
+                               adaptive ? full : nullptr, try_first ? try_flag : nullptr,
+                               run_full);
   }
   // Mixed modes, layers with P < 32 (short blocks): the whole factor in one
   // CTA in pair arithmetic (small_polar) instead of a Gram, a composition and
@@ -1056,6 +1080,35 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   }
   if (df_ok && h->measuring)
     h->partial_cap = std::max<size_t>(h->partial_cap, (size_t)df_gram_splits(P, (int)N) * PP);
+  if (try_first && !h->measuring) {
+    // The first try (every launch returns at once unless *try_flag): Gram
+    // matrix of X_0 (its pairs for the composition), the short block's
+    // composition, X_A = F X_0 into X2 and Xp2 (X_0 stays in Xp for the full
+    // schedule), and the Gram matrix of X_A with the test max |X_A X_A^T -
+    // I| > kPolarNear (far: 1 into run_full) and D = 0.5 (I - X_A X_A^T) for
+    // the correction.  When the try succeeds, every launch of the full
+    // schedule below returns at once, block 1's swap leaves X_A where block
+    // 1's result would be, and the short path's correction and the final
+    // selection proceed as for a short path after block 1.
+    GramCheck g0;
+    g0.ph = reinterpret_cast<float*>(h->pP);
+    g0.pl = g0.ph + PP;
+    df_begin(h);
+    df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, try_flag, &g0),
+           df_gram_flops(P, N), try_flag);
+    compose_block(h, h->polar_first[0], P, NJ, true, try_flag);
+    const float* Fah = reinterpret_cast<const float*>(h->pF);
+    df_begin(h);
+    df_end(h, df_apply(Fah, Fah + PP, Xp, Xp + PN, P, N, X2, h->stream, try_flag, Xp2, Xp2 + PN),
+           2.0 * P * P * (double)N, try_flag);
+    GramCheck g1 = g0;
+    g1.thr = kPolarNear;
+    g1.flag = run_full;
+    g1.d32 = Dc;
+    df_begin(h);
+    df_end(h, df_gram(Xp2, Xp2 + PN, P, N, h->pA, h->partial, h->stream, try_flag, &g1),
+           df_gram_flops(P, N), try_flag);
+  }
   for (size_t bi = 0; bi < sched.size(); ++bi) {
     const PolarBlock& blk = sched[bi];
     const bool df = df_ok && !h->measuring;
@@ -1075,9 +1128,9 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
         chk.d32 = Dc;
       }
       df_begin(h);
-      df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, nullptr,
+      df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, run_full,
                         kernel ? &chk : nullptr),
-             df_gram_flops(P, N));
+             df_gram_flops(P, N), run_full);
     } else {
     // A = X X^T (symmetric product: upper tiles computed, mirrored)
     GemmDesc g = desc(P, P, 1, NJ, h->pA, P, 1, 0, PP);
@@ -1085,9 +1138,11 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     g.sym = 1;
     run(h, g, 0);
     }
+    // the flag that lets this block's launches run: run_full for block 1
+    // after a first try, full for the adaptive schedule's last block
+    const int* gate = adaptive && bi + 1 == sched.size() ? full : (bi == 0 ? run_full : nullptr);
     if (kernel) {
-      if (!h->measuring)
-        compose_block(h, blk, P, NJ, df, adaptive && bi + 1 == sched.size() ? full : nullptr);
+      if (!h->measuring) compose_block(h, blk, P, NJ, df, gate);
     } else {
     if (!h->measuring) h->launches += set_identity(h->pF, P, NJ, h->stream);
     for (size_t j = 0; j < blk.steps.size(); ++j) {
@@ -1126,7 +1181,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       }
       // the adaptive schedule's last block: the composed F (full == 1) or one
       // Newton-Schulz step from the Gram matrix still in pA (full == 0)
-      const int* cut = adaptive && bi + 1 == sched.size() ? full : nullptr;
+      const int* cut = gate;
       df_begin(h);
       df_end(h, df_apply(Fah, Fal, Xp, Xp + PN, P, N, X2, h->stream, cut, Xp2, Xp2 + PN),
              2.0 * P * P * (double)N, cut);
@@ -1178,7 +1233,8 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // final step's result (full == 1), or from the last block's input plus
       // the short path's correction (full == 0)
       h->launches += scale_select(adaptive ? X_short : X, X, full, W, NJ * PN, -1.0, h->stream,
-                                  I.w32[t], adaptive ? Corr : nullptr);
+                                  I.w32[t], adaptive ? Corr : nullptr,
+                                  try_first ? try_flag : nullptr, nT, kPolarRetry);
     } else {
       h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
       if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
@@ -1394,6 +1450,7 @@ void layout(ttn_ctx* h, Arena& ar) {
     I.dstat = ar.take(4);
     I.istat = ar.take_int(8);
     I.pfull = ar.take_int(std::max(I.T, 1));
+    I.ppred = ar.take_int(3 * std::max(I.T, 1));
     c2_max = std::max(c2_max, (size_t)c * c);
     K_max = std::max(K_max, I.K);
   }
@@ -1532,6 +1589,9 @@ void setup_schedules(ttn_ctx* h) {
         (int)second[0].steps.size() <= kMaxComposeSteps)
       h->polar_adapt = {first[0], second[0]};
   }
+  h->polar_first.clear();
+  const std::vector<PolarBlock> well = polar_schedule(kPolarFirst, 1e300, 1e-15, 1000);
+  if (well.size() == 1 && (int)well[0].steps.size() <= kMaxComposeSteps) h->polar_first = well;
 }
 
 }  // namespace
@@ -1634,8 +1694,8 @@ static int prepare(ttn_ctx* h, const ttn_problem* probs, int n, const ttn_option
   rc = build_instances(h, probs, n);
   if (rc) return rc;
   if (h->opt.streams < 1 || h->opt.streams > 64) return fail(h, TTN_EINVAL, "streams in [1,64]");
-  if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 3)
-    return fail(h, TTN_EINVAL, "polar_blocks is 0, 1, 2 or 3");
+  if (h->opt.polar_blocks < 0 || h->opt.polar_blocks > 4)
+    return fail(h, TTN_EINVAL, "polar_blocks is 0, 1, 2, 3 or 4");
   assign_lanes(h);
   setup_schedules(h);
   Arena a0;
@@ -1700,8 +1760,12 @@ int ttn_create(ttn_t* out, const ttn_problem* probs, int n, const ttn_options* o
     if (!rc)
       rc = check_cuda(h, cudaMemsetAsync(h->inst[i].dstat, 0, 4 * sizeof(double), h->stream), "status");
     if (!rc) {
-      // no polar block cut short yet
-      h->launches += store_ints(h->inst[i].pfull, nullptr, std::max(h->inst[i].T, 1), 1, h->stream);
+      // no polar block cut short yet; every layer first tries the
+      // well-conditioned first block
+      const int nT = std::max(h->inst[i].T, 1);
+      h->launches += store_ints(h->inst[i].pfull, nullptr, nT, 1, h->stream);
+      h->launches += store_ints(h->inst[i].ppred, nullptr, 2 * nT, 1, h->stream);
+      h->launches += store_ints(h->inst[i].ppred + 2 * nT, nullptr, nT, 0, h->stream);
       rc = check_cuda(h, cudaPeekAtLastError(), "status");
     }
   }
@@ -2007,7 +2071,7 @@ int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
   std::vector<double> r(3 * (2 * T + 1) + 1);
   double dst[4];
   int ist[8];
-  std::vector<int> pf(std::max(T, 1));
+  std::vector<int> pf(std::max(T, 1)), pr(std::max(T, 1));
   int rc = check_cuda(h, cudaMemcpyAsync(r.data(), res, r.size() * sizeof(double),
                                          cudaMemcpyDeviceToHost, h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaMemcpyAsync(dst, I.dstat, sizeof(dst), cudaMemcpyDeviceToHost,
@@ -2015,6 +2079,9 @@ int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
   if (!rc) rc = check_cuda(h, cudaMemcpyAsync(ist, I.istat, sizeof(ist), cudaMemcpyDeviceToHost,
                                               h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaMemcpyAsync(pf.data(), I.pfull, pf.size() * sizeof(int),
+                                              cudaMemcpyDeviceToHost, h->stream), "diagnostics");
+  // (run_full flags of the last sweep: 0 where the first try succeeded)
+  if (!rc) rc = check_cuda(h, cudaMemcpyAsync(pr.data(), I.ppred + pr.size(), pr.size() * sizeof(int),
                                               cudaMemcpyDeviceToHost, h->stream), "diagnostics");
   if (!rc) rc = check_cuda(h, cudaStreamSynchronize(h->stream), "diagnostics sync");
   if (rc) return rc;
@@ -2039,6 +2106,11 @@ int ttn_diagnostics(ttn_t h, int inst, double* out, int n_out) {
     int cut = 0;
     for (int t = 0; t < T; ++t) cut += pf[t] == 0;
     out[8] = cut;
+  }
+  if (n_out >= 10) {
+    int first = 0;
+    for (int t = 0; t < T; ++t) first += pr[t] == 0;
+    out[9] = first;
   }
   return TTN_OK;
 }
