@@ -45,7 +45,7 @@ METRIC = "TTN sweeps/s at chi=128 (TFIM L=1024)"
 TRAFFIC = {
     "tc_hbm": 15.47e6,   # gemm_tma_kernel: 121 launches, 1.87 GB
     "tc": 15.47e6,
-    "df": 8.55e6,        # gemm_df_kernel: 42 launches (10 cut short), 0.359 GB
+    "df": 5.71e6,        # gemm_df_kernel: 63 launches (39 return at once), 0.360 GB
 }
 
 
