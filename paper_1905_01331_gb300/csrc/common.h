@@ -80,6 +80,7 @@ struct GemmDesc {
   double* partial;   // splits * B0 * B1 * M * N doubles when splits > 1
   int prec;          // ttn_precision of the products
   const int* skip;   // if non-null and *skip != 0 the launch does nothing
+  int skip_when_zero;  // with skip: the launch does nothing when *skip == 0 instead
   int* err;          // device flag raised when a bounded wait of a kernel expires
   int sym;           // C = A A^T (symmetric, M == N): only tiles on or above the
                      // diagonal are computed and mirrored (FP64 engine)
@@ -94,6 +95,13 @@ struct GemmDesc {
 };
 // passed by value as a kernel parameter (limit 32764 bytes)
 static_assert(sizeof(GemmDesc) + 64 < 32764, "GemmDesc too large for a kernel parameter");
+
+#ifdef __CUDACC__
+// The device flag of a product says that its launches do nothing.
+__device__ __forceinline__ bool desc_skipped(const GemmDesc& d) {
+  return d.skip && ((*d.skip != 0) != (d.skip_when_zero != 0));
+}
+#endif
 
 // Launch one grouped product on `stream` (FP64 CUDA-core kernel or tcgen05
 // kernel by desc.prec).  Returns the number of kernel launches.
@@ -139,10 +147,11 @@ int dot_self_and_cross_partial(const double* x, const double* y, long long n, lo
 // With xh, xl (one batch only) X is written as FP32 pairs for the double-float
 // products instead (xh = fl32(X), xl = fl32(X - xh); X itself is not written).
 // With try_first (device, may be null): *run_full = (*try_first == 0).
+// zero2 (may be null): set to 0 as well.
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb,
                 int P, double mu, const double* part, cudaStream_t s, float* xh = nullptr,
                 float* xl = nullptr, int* zero = nullptr, const int* try_first = nullptr,
-                int* run_full = nullptr);
+                int* run_full = nullptr, int* zero2 = nullptr);
 
 // For one P x P matrix A: (ph, pl) = FP32 pair of a I - c A (a = 0, c = -1:
 // of A itself, as df_split), with flag: flag |= 1 when max |A - I| > thr, and
@@ -164,11 +173,12 @@ int axpby(const double* x, double* y, long long n, double alpha, double beta, cu
 // (device: try_first = pred[0], run_full = pred[pstride], count =
 // pred[2 pstride]) also the next prediction of the polar schedule: try_first
 // becomes 0 when this sweep's first try failed (run_full set), and 1 again
-// after `retry` sweeps.
+// after `retry` sweeps.  With sel2 (device, may be null), the *sel branch is
+// itself a choice: x2 when *sel2, else x1 + corr.
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
                  double alpha, cudaStream_t s, float* y32 = nullptr,
                  const float* corr = nullptr, int* pred = nullptr, int pstride = 0,
-                 int retry = 0);
+                 int retry = 0, const double* x2 = nullptr, const int* sel2 = nullptr);
 
 // Symmetrise P x P blocks in place: A = (A + A^T) / 2.
 int symmetrize(double* A, int P, int nb, cudaStream_t s);
@@ -326,6 +336,8 @@ struct GramCheck {
   double thr = 0.0;
   int* flag = nullptr;
   float* d32 = nullptr;
+  double thr2 = 0.0;     // flag2 |= 1 when max |C - I| > thr2 (flag2 may be null)
+  int* flag2 = nullptr;
 };
 // C (P x P, FP64) = X X^T for X (P x n2, row-major) given as (Xh, Xl).
 // run_if (device, may be null): when it points to 0 the launches return at once.

@@ -225,7 +225,7 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
     }
     gs[g][lane] = acc;
     __syncthreads();
-    int far = 0;
+    int far = 0, far2 = 0;
     if (g == 0 && e < MN) {
       double t = 0.0;
       for (int q = 0; q < 8; ++q) t += gs[q][lane];
@@ -234,12 +234,14 @@ __global__ void df_reduce_kernel(const double* part, int splits, int M, int N, i
         // the check_split pass (square C, element e = m N + n)
         const double id = m == n ? 1.0 : 0.0;
         if (chk.flag && !(fabs(t - id) <= chk.thr)) far = 1;
+        if (chk.flag2 && !(fabs(t - id) <= chk.thr2)) far2 = 1;
         const double v = chk.c == -1.0 && chk.a == 0.0 ? t : (m == n ? chk.a : 0.0) - chk.c * t;
         f64b::split(v, chk.ph[e], chk.pl[e]);
         if (chk.d32) chk.d32[e] = f64b::to_f32(0.5 * (id - t));
       }
     }
     if (g == 0 && chk.flag && __any_sync(0xffffffffu, far) && lane == 0) atomicOr(chk.flag, 1);
+    if (g == 0 && chk.flag2 && __any_sync(0xffffffffu, far2) && lane == 0) atomicOr(chk.flag2, 1);
     __syncthreads();
   }
 }
@@ -270,6 +272,8 @@ int gram_launch(const float* Xh, const float* Xl, int P, long long n2, double* C
   } else if (chk) {
     launches += check_split(C, P, chk->a, chk->c, chk->ph, chk->pl, chk->thr, chk->flag, s,
                             chk->d32);
+    if (chk->flag2)
+      launches += check_split(C, P, chk->a, chk->c, chk->ph, chk->pl, chk->thr2, chk->flag2, s);
   }
   return launches;
 }

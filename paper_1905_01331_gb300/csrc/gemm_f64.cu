@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
   pdl_wait();
   pdl_trigger();
   constexpr int TM = BM / 16, TN = BN / 16;
-  if (d.skip && *d.skip) return;
+  if (desc_skipped(d)) return;
   __shared__ double As[kBK][BM + 1];
   __shared__ double Bs[kBK][BN + 1];
 
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) gemm_f64_kernel(const GemmDesc d, in
 __global__ void splitk_reduce_kernel(const GemmDesc d) {
   pdl_wait();
   pdl_trigger();
-  if (d.skip && *d.skip) return;
+  if (desc_skipped(d)) return;
   __shared__ double gs[8][32];
   const long long MN = (long long)d.M * d.N;
   const long long total = MN * d.B0 * d.B1;

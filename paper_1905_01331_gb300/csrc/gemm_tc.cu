@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ uint32_t tmem_slot;
 
-  if (d.skip && *d.skip) return;
+  if (desc_skipped(d)) return;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_n = (d.N + BN - 1) / BN;
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) gemm_tc_kernel(const GemmDesc d
 __global__ void splitk_reduce_tc(const GemmDesc d) {
   pdl_wait();
   pdl_trigger();
-  if (d.skip && *d.skip) return;
+  if (desc_skipped(d)) return;
   __shared__ float gh[8][32], gl[8][32];
   const long long MN = static_cast<long long>(d.M) * d.N;
   const long long total = MN * d.B0 * d.B1;
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(kTThreads, kRing == kTSmem ? 1 : 2)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
-  if (d.skip && *d.skip) return;
+  if (desc_skipped(d)) return;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_n = (d.N + BN - 1) / BN;

@@ -95,11 +95,13 @@ __global__ void dot_final_kernel(const double* partial, int nb, double* out, con
 
 __global__ void polar_start_kernel(const double* G, const double* W, double* X, long long elems,
                                    int P, double mu, const double* part, int nb, float* xh,
-                                   float* xl, int* zero, const int* try_first, int* run_full) {
+                                   float* xl, int* zero, const int* try_first, int* run_full,
+                                   int* zero2) {
   pdl_wait();
   pdl_trigger();
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     if (zero) *zero = 0;
+    if (zero2) *zero2 = 0;
     // the full schedule runs unless the layer is predicted well conditioned
     if (run_full) *run_full = *try_first ? 0 : 1;
   }
@@ -172,7 +174,8 @@ __global__ void axpby_kernel(const double* x, double* y, long long n, double alp
 
 __global__ void scale_select_kernel(const double* x0, const double* x1, const int* sel, double* y,
                                     long long n, double alpha, float* y32, const float* corr,
-                                    int* pred, int pstride, int retry) {
+                                    int* pred, int pstride, int retry, const double* x2,
+                                    const int* sel2) {
   pdl_wait();
   pdl_trigger();
   if (pred && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -188,11 +191,14 @@ __global__ void scale_select_kernel(const double* x0, const double* x1, const in
     }
   }
   const bool one = *sel != 0;
-  const double* x = one ? x1 : x0;
+  // with sel2: the sel branch is x2 when *sel2, else x1 plus the correction
+  const bool two = one && sel2 && *sel2 != 0;
+  const bool add = corr && (!one || (sel2 && !two));
+  const double* x = two ? x2 : (one ? x1 : x0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     double xi = x[i];
-    if (!one && corr) xi += f64b::from_f32(corr[i]);
+    if (add) xi += f64b::from_f32(corr[i]);
     const double v = alpha * xi;
     y[i] = v;
     if (y32) y32[i] = f64b::to_f32(v);
@@ -616,11 +622,11 @@ int dot_self_and_cross_partial(const double* x, const double* y, long long n, lo
 
 int polar_start(const double* G, const double* W, double* X, long long elems, int nb, int P,
                 double mu, const double* part, cudaStream_t s, float* xh, float* xl, int* zero,
-                const int* try_first, int* run_full) {
+                const int* try_first, int* run_full, int* zero2) {
   if (nb != 1) xh = xl = nullptr;
   if (!try_first) run_full = nullptr;
   launch_k(polar_start_kernel, dim3(grid_for(elems, 256, 512), nb), 256, 0, s, G, W, X, elems, P,
-           mu, part, nb, xh, xl, zero, try_first, run_full);
+           mu, part, nb, xh, xl, zero, try_first, run_full, zero2);
   return 1;
 }
 
@@ -649,9 +655,9 @@ int axpby(const double* x, double* y, long long n, double alpha, double beta, cu
 
 int scale_select(const double* x0, const double* x1, const int* sel, double* y, long long n,
                  double alpha, cudaStream_t s, float* y32, const float* corr, int* pred,
-                 int pstride, int retry) {
+                 int pstride, int retry, const double* x2, const int* sel2) {
   launch_k(scale_select_kernel, grid_for(n), 256, 0, s, x0, x1, sel, y, n, alpha, y32, corr, pred,
-           pstride, retry);
+           pstride, retry, x2, sel2);
   return 1;
 }
 

@@ -89,6 +89,9 @@ struct Instance {
   // max(T, 1)): [t] try the well-conditioned first block, [T + t] the full
   // schedule runs in this sweep, [2T + t] sweeps since a failed first try
   int* ppred = nullptr;
+  // per isometry layer: the long path's block 2 left X X^T more than
+  // kPolarNear from I (the final Newton-Schulz step then runs in full)
+  int* pfar = nullptr;
   // Identity part of the one-site operators, kept exactly in FP64: the true
   // one-site term of site j at layer t is  ops[t][j][0] + eoff[t][j] * I.
   std::vector<double*> eoff;
@@ -1042,6 +1045,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
   float* Dc = reinterpret_cast<float*>(h->pT);
   float* Corr = Fh + 2 * PP;
   const double* X_short = X;
+  const double* X_block = X;   // the long path's block-2 result
   if (!h->measuring) {
     // |Gamma|^2 and <Gamma, W> from one pass over Gamma (partial sums, completed
     // inside the polar start)
@@ -1051,7 +1055,7 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     h->launches += polar_start(Gam, W, X, PN, NJ, P, h->opt.polar_damping, h->red, h->stream,
                                df_ok ? Xp : nullptr, df_ok ? Xp + PN : nullptr,
                                adaptive ? full : nullptr, try_first ? try_flag : nullptr,
-                               run_full);
+                               run_full, adaptive ? I.pfar + t : nullptr);
   }
   // Mixed modes, layers with P < 32 (short blocks): the whole factor in one
   // CTA in pair arithmetic (small_polar) instead of a Gram, a composition and
@@ -1219,12 +1223,32 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
     fin.pl = Fl;
     fin.thr = 1e-5;
     fin.flag = I.istat + 4;
+    // adaptive schedule: when block 2 left X X^T within kPolarNear of I (far
+    // stays 0), the final step is the same FP32 correction as the short
+    // path's, D X on the tensor cores with D = 0.5 (I - X X^T) from this pass;
+    // otherwise the double-float step runs
+    int* far = adaptive ? I.pfar + t : nullptr;
+    if (adaptive) {
+      fin.thr2 = kPolarNear;
+      fin.flag2 = far;
+      fin.d32 = Dc;
+    }
     df_begin(h);
     df_end(h, df_gram(Xp, Xp + PN, P, N, h->pA, h->partial, h->stream, full, &fin),
            df_gram_flops(P, N), full);
+    X_block = X;
+    if (adaptive) {
+      // (runs whenever the long path runs; unused when far is set)
+      GemmDesc c = desc(P, (int)N, 1, 1, TP{Corr, 1}, N, 1, 0, 0);
+      add(c, grp(op(TP{Dc, 1}, P, 1), op(TP{Xp, 1}, 1, N), P));
+      c.skip = full;
+      c.skip_when_zero = 1;
+      run(h, c, TTN_TF32X3);
+    }
+    const int* run_final = adaptive ? far : full;
     df_begin(h);
-    df_end(h, df_apply(Fh, Fl, Xp, Xp + PN, P, N, X2, h->stream, full), 2.0 * P * P * (double)N,
-           full);
+    df_end(h, df_apply(Fh, Fl, Xp, Xp + PN, P, N, X2, h->stream, run_final),
+           2.0 * P * P * (double)N, run_final);
     std::swap(X, X2);
   }
   if (!h->measuring) {
@@ -1232,9 +1256,12 @@ void polar(ttn_ctx* h, Instance& I, int t, int prec, const double* Gam) {
       // W and its FP32 copy for the tensor-core products in one pass: from the
       // final step's result (full == 1), or from the last block's input plus
       // the short path's correction (full == 0)
-      h->launches += scale_select(adaptive ? X_short : X, X, full, W, NJ * PN, -1.0, h->stream,
-                                  I.w32[t], adaptive ? Corr : nullptr,
-                                  try_first ? try_flag : nullptr, nT, kPolarRetry);
+      // (adaptive, long path: block 2's result plus the correction, or the
+      // double-float final step's result when block 2 was left far)
+      h->launches += scale_select(adaptive ? X_short : X, adaptive ? X_block : X, full, W,
+                                  NJ * PN, -1.0, h->stream, I.w32[t], adaptive ? Corr : nullptr,
+                                  try_first ? try_flag : nullptr, nT, kPolarRetry,
+                                  adaptive ? X : nullptr, adaptive ? I.pfar + t : nullptr);
     } else {
       h->launches += axpby(X, W, NJ * PN, -1.0, 0.0, h->stream);
       if (prec != 0) h->launches += to_f32(W, I.w32[t], NJ * PN, h->stream);
@@ -1451,6 +1478,7 @@ void layout(ttn_ctx* h, Arena& ar) {
     I.istat = ar.take_int(8);
     I.pfull = ar.take_int(std::max(I.T, 1));
     I.ppred = ar.take_int(3 * std::max(I.T, 1));
+    I.pfar = ar.take_int(std::max(I.T, 1));
     c2_max = std::max(c2_max, (size_t)c * c);
     K_max = std::max(K_max, I.K);
   }
