@@ -151,3 +151,26 @@ def test_tiles_blob_is_validated_at_planning(lib):
     entry = struct.pack("<Qiiiifi", 123, 1, 64, 2, 0, 1.0, 0)
     assert size_with(b"TTNT" + struct.pack("<III", 2, 1, 0) + entry) > 0
     assert size_with(b"TTNT" + struct.pack("<III", 2, 2, 0) + entry) == 0   # truncated
+
+
+def test_polar_schedule_option_is_validated_at_planning(lib):
+    """ttn_options.polar_blocks: 0 (adaptive with the first try), 1, 2, 3
+    (fixed two-block schedule) and 4 (adaptive without the first try) are
+    accepted; anything else is rejected before any device work."""
+    import numpy as np
+    from paper_1905_01331_gb300 import _abi
+    import ttn_inputs as ti
+    m = ti.tfim_chain(64, 1.0)
+    o, A, B = (np.ascontiguousarray(x) for x in (m.o, m.A, m.B))
+    dp = ctypes.POINTER(ctypes.c_double)
+    p = _abi.Problem(64, 1, 2, 16, 1, 0, o.ctypes.data_as(dp), A.ctypes.data_as(dp),
+                     B.ctypes.data_as(dp))
+
+    def size_with(pb):
+        opt = _abi.Options()
+        lib.ttn_default_options(ctypes.byref(opt))
+        opt.polar_blocks = pb
+        return lib.ttn_workspace_bytes(ctypes.byref(p), 1, ctypes.byref(opt))
+
+    assert all(size_with(pb) > 0 for pb in range(5))
+    assert size_with(5) == 0 and size_with(-1) == 0
